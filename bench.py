@@ -1,0 +1,444 @@
+#!/usr/bin/env python3
+"""Throughput of the BP1.0 / BP3.5 / BP3.0 hot path on GB300.
+
+One step = one pass of the whole path over the synthetic 32^3 jittered
+hex mesh (E = 32768, degree N = 7, lambda = 1):
+  geometric factors for BP1.0 (wJ at Gauss points), BP3.5 (7 planes at GLL
+  nodes) and BP3.0 (7 planes at Gauss points) from the element vertices,
+  then the BP1.0, BP3.5 and BP3.0 matvecs of one field q.
+The degree-N basis (a few KB of tables) is built once before timing.
+value = 3 E (N+1)^3 DOFs per step (one field through each operator) / time.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload.  Under torchrun every rank runs its own
+replica of the workload (the operators are block diagonal: no data-path
+collective); rank 0 reports the aggregate over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import fem_synth  # noqa: E402
+
+WORKLOAD = "BP1.0+BP3.5+BP3.0 FP64 with geometric factors, 32x32x32 jittered hex mesh (E=32768), N=7, lambda=1"
+METRIC = "GDOF/s (BP1.0+BP3.5+BP3.0 step, FP64, N=7, E=32768)"
+KERNELS = ["geofacs_bp1", "geofacs_bp35", "geofacs_bp30", "bp1", "bp35", "bp30"]
+
+# Measured DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) per
+# element at N = 7, with the sha256 of the kernel source it was taken from;
+# a kernel whose source changed since reports traffic null.
+NCU_TRAFFIC = {}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured", d
+    return 6800.0, "fallback", {}
+
+
+# FP64 issue rate of the GB300 SM: 2 FP64 FMA per clock per SM (the nominal
+# 1.25 TFLOP/s over 152 SMs at 2.07 GHz), 2 flops each.
+SMS = 152
+FP64_FLOP_PER_CLK_SM = 4
+
+
+def fp64_peak_tflops(sm_mhz: float) -> float:
+    return SMS * FP64_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12
+
+
+def alg_counts(N: int):
+    """Algorithmic FP64 flops (multiply-add = 2) and HBM bytes per element
+    of each kernel (bytes: Table 1 of the paper for the operators; the
+    geometric-factor kernels read 24 vertex doubles and write their planes)."""
+    n, m = N + 1, N + 2
+    n3, m3 = n ** 3, m ** 3
+    interp = 2 * (m * n3 + m * m * n * n + m3 * n)  # one of interpolate / project
+    flops = {
+        "geofacs_bp1": 22 * m3,
+        "geofacs_bp35": 70 * n3,
+        "geofacs_bp30": 70 * m3,
+        "bp1": 2 * interp + m3,
+        "bp35": 12 * n ** 4 + 18 * n3,
+        "bp30": 2 * interp + 12 * m ** 4 + 18 * m3,
+    }
+    byts = {
+        "geofacs_bp1": 8 * (24 + m3),
+        "geofacs_bp35": 8 * (24 + 7 * n3),
+        "geofacs_bp30": 8 * (24 + 7 * m3),
+        "bp1": 8 * (2 * n3 + m3),
+        "bp35": 8 * (9 * n3),
+        "bp30": 8 * (2 * n3 + 7 * m3),
+    }
+    return flops, byts
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during timing."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+                power.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Maximum of a per-rank float over all ranks (a timing reduction only)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int, device=None):
+    if world > 1:
+        import torch.distributed as dist
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def workload_arrays(N: int, E_side: int, rank: int):
+    verts = fem_synth.box_mesh(E_side)
+    E = verts.shape[0]
+    # each rank draws its own field (offset stream), same mesh recipe
+    q = fem_synth.field(fem_synth.SEED_Q, E, (N + 1) ** 3, offset=rank * E * (N + 1) ** 3)
+    return verts, q
+
+
+def _src_hash(name: str) -> str:
+    path = os.path.join(ROOT, "paper_1711_00903_gb300", "csrc", name)
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def cpu_oracle_rate(N: int, verts, q, lam: float, target_s: float, cores: int):
+    """Times the oracle's step (geometric factors + the three operators) on a
+    sample of elements sized for about target_s seconds; returns
+    (GDOF/s, elements in the sample, seconds, threads)."""
+    import oracle
+    threads = oracle.set_threads(cores)
+
+    def run(Es):
+        v, qq = verts[:Es], q[:Es]
+        t0 = time.perf_counter()
+        wJ, _ = oracle.geofacs(N, oracle.KIND_BP1, v)
+        G35, _ = oracle.geofacs(N, oracle.KIND_BP35, v)
+        G30, _ = oracle.geofacs(N, oracle.KIND_BP30, v)
+        oracle.bp1(N, wJ, qq)
+        oracle.bp35(N, G35, lam, qq)
+        oracle.bp30(N, G30, lam, qq)
+        return time.perf_counter() - t0
+
+    Es = min(64, verts.shape[0])
+    dt = run(Es)
+    Es = int(min(verts.shape[0], max(Es, Es * target_s / max(dt, 1e-6))))
+    dt = run(Es)
+    return 3 * Es * (N + 1) ** 3 / dt / 1e9, Es, dt, threads
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    N, lam = args.degree, 1.0
+    verts, q = workload_arrays(N, 32, 0)
+    cores = len(os.sched_getaffinity(0))
+    import oracle
+    oracle.set_threads(cores)
+    # size one step for about 1 s of CPU work so the whole run stays short
+    rate, Es, dt, threads = cpu_oracle_rate(N, verts, q, lam, 1.0, cores)
+    for _ in range(args.warmup):
+        cpu_oracle_rate_fixed(N, verts[:Es], q[:Es], lam)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cpu_oracle_rate_fixed(N, verts[:Es], q[:Es], lam)
+    T = time.perf_counter() - t0
+    value = args.steps * 3 * Es * (N + 1) ** 3 / T / 1e9
+    sample = f"first {Es} of 32768 elements per step (geometric factors + BP1.0 + BP3.5 + BP3.0, N={N})"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GDOF/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "E": 32768, "N": N, "lambda": lam, "sample_elements": Es},
+        "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": threads, "kind": "oracle",
+                          "sample": sample},
+        "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def cpu_oracle_rate_fixed(N, v, qq, lam):
+    import oracle
+    wJ, _ = oracle.geofacs(N, oracle.KIND_BP1, v)
+    G35, _ = oracle.geofacs(N, oracle.KIND_BP35, v)
+    G30, _ = oracle.geofacs(N, oracle.KIND_BP30, v)
+    oracle.bp1(N, wJ, qq)
+    oracle.bp35(N, G35, lam, qq)
+    oracle.bp30(N, G30, lam, qq)
+
+
+# ---------------------------------------------------------------- GPU path
+
+def run_ours(args):
+    import torch
+    import paper_1711_00903_gb300 as fem
+
+    world, rank, local = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU path)")
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+
+    N, lam = args.degree, 1.0
+    n, m = N + 1, N + 2
+    verts_h, q_h = workload_arrays(N, 32, rank)
+    E = verts_h.shape[0]
+    b = fem.fem_basis_setup(N)
+    stream = torch.cuda.current_stream(device)
+
+    verts = torch.from_numpy(verts_h).to(device)
+    q = torch.from_numpy(q_h).to(device)
+    wJ = torch.empty(fem.geo_shape(b, 1, E), dtype=torch.float64, device=device)
+    G35 = torch.empty(fem.geo_shape(b, 2, E), dtype=torch.float64, device=device)
+    G30 = torch.empty(fem.geo_shape(b, 3, E), dtype=torch.float64, device=device)
+    o1, o35, o30 = (torch.empty_like(q) for _ in range(3))
+
+    def step(ev=None):
+        def mark(i):
+            if ev is not None:
+                ev[i].record(stream)
+        mark(0)
+        fem.fem_mesh_geofacs(b, 1, verts, geo=wJ, stream=stream)
+        mark(1)
+        fem.fem_mesh_geofacs(b, 2, verts, geo=G35, stream=stream)
+        mark(2)
+        fem.fem_mesh_geofacs(b, 3, verts, geo=G30, stream=stream)
+        mark(3)
+        fem.fem_bp1_apply(b, wJ, q, out=o1, stream=stream)
+        mark(4)
+        fem.fem_bp35_apply(b, G35, lam, q, out=o35, stream=stream)
+        mark(5)
+        fem.fem_bp30_apply(b, G30, lam, q, out=o30, stream=stream)
+        mark(6)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(7)] for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world, device)
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        step(events[k])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world, device)
+    clocks = sampler.stop()
+    ms_local = t_start.elapsed_time(t_end)
+    ms = reduce_max(ms_local, world, device)
+    per_kernel = {name: statistics.fmean(events[k][i].elapsed_time(events[k][i + 1]) for k in range(args.steps))
+                  for i, name in enumerate(KERNELS)}
+
+    # end to end through the same calls: pinned host input -> device ->
+    # step -> host output, every step
+    verts_p = torch.from_numpy(verts_h).pin_memory()
+    q_p = torch.from_numpy(q_h).pin_memory()
+    outs_p = [torch.empty(q_h.shape, dtype=torch.float64).pin_memory() for _ in range(3)]
+    e2e_steps = max(3, min(args.steps, 20))
+
+    def e2e_step():
+        verts.copy_(verts_p, non_blocking=True)
+        q.copy_(q_p, non_blocking=True)
+        step()
+        for dst, src in zip(outs_p, (o1, o35, o30)):
+            dst.copy_(src, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier(world, device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = reduce_max(e0.elapsed_time(e1) / e2e_steps, world, device)
+
+    dofs = 3 * E * n ** 3
+    value = world * dofs * args.steps / (ms / 1e3) / 1e9
+    flops, byts = alg_counts(N)
+    hbm, hbm_src, _ = _peaks()
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    kern = {}
+    for name in KERNELS:
+        t = per_kernel[name] / 1e3
+        kern[name] = {
+            "ms": per_kernel[name],
+            "gdofs": E * n ** 3 / t / 1e9 if name in ("bp1", "bp35", "bp30") else None,
+            "alg_gbs": E * byts[name] / t / 1e9,
+            "hbm_frac": E * byts[name] / t / 1e9 / hbm,
+            "fp64_tflops": E * flops[name] / t / 1e12,
+            "fp64_frac": E * flops[name] / t / 1e12 / fp64_peak_tflops(2070.0),
+        }
+    dom = max(KERNELS, key=lambda k: per_kernel[k])
+    src_file = {"bp1": "bp1.cu", "bp35": "bp35.cu", "bp30": "bp30.cu"}.get(dom, "geofacs.cu")
+    tr = NCU_TRAFFIC.get(dom)
+    traffic = tr["bytes_per_elem"] * E if tr and tr["sha"] == _src_hash(src_file) and tr["N"] == N else None
+    peak_alu = fp64_peak_tflops(2070.0)
+    roofline = {
+        "kernel": dom, "bound": "alu", "unit": "TFLOP/s",
+        "achieved": kern[dom]["fp64_tflops"], "peak": peak_alu,
+        "frac": kern[dom]["fp64_tflops"] / peak_alu,
+        "peak_source": "FP64 issue rate derived from unit counts: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz",
+        "traffic": traffic,
+        "hbm": {"achieved_gbs": kern[dom]["alg_gbs"], "peak_gbs": hbm, "peak_source": hbm_src,
+                "frac": kern[dom]["hbm_frac"]},
+    }
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = len(os.sched_getaffinity(0))
+        rate, Es, dt, threads = cpu_oracle_rate(N, verts_h, q_h, lam, args.cpu_seconds, cores)
+        cpu = {"value": rate, "unit": "GDOF/s", "cores": threads, "kind": "oracle",
+               "sample": f"first {Es} of {E} elements, one step (geometric factors + BP1.0 + BP3.5 + BP3.0), "
+                         f"{dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "E": E, "N": N, "lambda": lam,
+                       "mesh": "32^3 unit cube, interior vertices jittered U[-0.1h,0.1h], trilinear",
+                       "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "e2e": {"value": world * dofs / (e2e_ms / 1e3) / 1e9, "unit": "GDOF/s",
+                    "h2d_bytes_per_step": int(verts_h.nbytes + q_h.nbytes),
+                    "d2h_bytes_per_step": int(3 * q_h.nbytes)},
+            "gpu_launches": 6 * args.steps,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "kernels": kern,
+        }
+        print(json.dumps(line))
+    b.free()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--degree", type=int, default=7)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be at least 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

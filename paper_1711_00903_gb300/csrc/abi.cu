@@ -1,0 +1,184 @@
+// C ABI entry points (include/fem.h): argument checks, basis handles and
+// dispatch to the kernels.
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "fem_internal.h"
+
+namespace {
+
+thread_local char g_cuda_err[256] = "";
+
+int cuda_fail(cudaError_t e) {
+    std::snprintf(g_cuda_err, sizeof g_cuda_err, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return (e == cudaErrorNoDevice || e == cudaErrorNoKernelImageForDevice || e == cudaErrorInsufficientDriver)
+               ? FEM_ENODEV
+               : FEM_ECUDA;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// True when [a, a+na) and [b, b+nb) (in doubles) overlap.
+bool overlap(const double *a, int64_t na, const double *b, int64_t nb) {
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(a), a1 = a0 + (uintptr_t)na * 8;
+    const uintptr_t b0 = reinterpret_cast<uintptr_t>(b), b1 = b0 + (uintptr_t)nb * 8;
+    return a0 < b1 && b0 < a1;
+}
+
+int64_t cube(int x) { return (int64_t)x * x * x; }
+
+// Common checks of an apply call; returns FEM_OK or FEM_EINVAL.
+int check_apply(const fem_basis *b, int64_t E, const double *geo, int64_t geo_per_elem,
+                const double *q, const double *out) {
+    if (!b || E < 0) return FEM_EINVAL;
+    if (E == 0) return FEM_OK;
+    if (!geo || !q || !out) return FEM_EINVAL;
+    if (!aligned16(geo) || !aligned16(q) || !aligned16(out)) return FEM_EINVAL;
+    const int64_t np = cube(b->host.n);
+    if (E > (INT64_MAX / 8) / (geo_per_elem > np ? geo_per_elem : np)) return FEM_EINVAL;
+    if (overlap(out, E * np, q, E * np) || overlap(out, E * np, geo, E * geo_per_elem)) return FEM_EINVAL;
+    if ((E + 1) > (int64_t)0x7fffffff) return FEM_EINVAL;  // grid size limit
+    return FEM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fem_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+const char *fem_strerror(int code) {
+    switch (code) {
+        case FEM_OK: return "FEM_OK";
+        case FEM_EINVAL: return "FEM_EINVAL: invalid argument";
+        case FEM_ECUDA: return "FEM_ECUDA: CUDA runtime or launch error";
+        case FEM_ENOMEM: return "FEM_ENOMEM: allocation failed";
+        case FEM_ENODEV: return "FEM_ENODEV: no usable CUDA device";
+        default: return "unknown fem error code";
+    }
+}
+
+const char *fem_last_cuda_error(void) { return g_cuda_err; }
+
+int fem_basis_setup(int N, fem_basis **out) {
+    if (!out || N < 1 || N > FEM_MAX_N) return FEM_EINVAL;
+    *out = nullptr;
+    fem_basis *b = new (std::nothrow) fem_basis();
+    if (!b) return FEM_ENOMEM;
+    if (!fem::compute_basis(N, &b->host)) {
+        delete b;
+        return FEM_EINVAL;
+    }
+    cudaError_t e = cudaGetDevice(&b->device);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(e);
+    }
+    const fem::HostBasis &h = b->host;
+    const fem::OpsLayout L{h.n, h.m};
+    double table[fem::OpsLayout{fem::kMaxQ - 1, fem::kMaxQ}.size()];
+    std::memset(table, 0, sizeof table);
+    std::memcpy(table + L.offI(), h.I, sizeof(double) * h.m * h.n);
+    std::memcpy(table + L.offD(), h.D, sizeof(double) * h.n * h.n);
+    std::memcpy(table + L.offDt(), h.Dt, sizeof(double) * h.m * h.m);
+    std::memcpy(table + L.offR(), h.r, sizeof(double) * h.n);
+    std::memcpy(table + L.offRt(), h.rt, sizeof(double) * h.m);
+    std::memcpy(table + L.offW(), h.w, sizeof(double) * h.n);
+    std::memcpy(table + L.offWt(), h.wt, sizeof(double) * h.m);
+    e = cudaMalloc(&b->d_ops, sizeof(double) * L.size());
+    if (e != cudaSuccess) {
+        delete b;
+        return e == cudaErrorMemoryAllocation ? FEM_ENOMEM : cuda_fail(e);
+    }
+    e = cudaMemcpy(b->d_ops, table, sizeof(double) * L.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = fem::prepare_bp1(N);
+    if (e == cudaSuccess) e = fem::prepare_bp35(N);
+    if (e == cudaSuccess) e = fem::prepare_bp30(N);
+    if (e == cudaSuccess) e = fem::prepare_geofacs(N);
+    if (e != cudaSuccess) {
+        cudaFree(b->d_ops);
+        delete b;
+        return cuda_fail(e);
+    }
+    *out = b;
+    return FEM_OK;
+}
+
+void fem_basis_free(fem_basis *b) {
+    if (!b) return;
+    if (b->d_ops) cudaFree(b->d_ops);
+    delete b;
+}
+
+int fem_basis_degree(const fem_basis *b) { return b ? b->host.N : FEM_EINVAL; }
+
+static void copy_tables(const fem::HostBasis &h, double *r, double *w, double *rt, double *wt,
+                        double *I, double *D, double *Dt) {
+    if (r) std::memcpy(r, h.r, sizeof(double) * h.n);
+    if (w) std::memcpy(w, h.w, sizeof(double) * h.n);
+    if (rt) std::memcpy(rt, h.rt, sizeof(double) * h.m);
+    if (wt) std::memcpy(wt, h.wt, sizeof(double) * h.m);
+    if (I) std::memcpy(I, h.I, sizeof(double) * h.m * h.n);
+    if (D) std::memcpy(D, h.D, sizeof(double) * h.n * h.n);
+    if (Dt) std::memcpy(Dt, h.Dt, sizeof(double) * h.m * h.m);
+}
+
+int fem_basis_tables(const fem_basis *b, double *r, double *w, double *rt, double *wt, double *I,
+                     double *D, double *Dt) {
+    if (!b) return FEM_EINVAL;
+    copy_tables(b->host, r, w, rt, wt, I, D, Dt);
+    return FEM_OK;
+}
+
+int fem_basis_host_tables(int N, double *r, double *w, double *rt, double *wt, double *I, double *D,
+                          double *Dt) {
+    fem::HostBasis h;
+    if (!fem::compute_basis(N, &h)) return FEM_EINVAL;
+    copy_tables(h, r, w, rt, wt, I, D, Dt);
+    return FEM_OK;
+}
+
+int fem_mesh_geofacs(const fem_basis *b, fem_geo_kind kind, int64_t E, const double *verts, double *geo,
+                     double *detJ_min, void *stream) {
+    if (!b || E < 0) return FEM_EINVAL;
+    if (kind != FEM_GEO_BP1 && kind != FEM_GEO_BP35 && kind != FEM_GEO_BP30) return FEM_EINVAL;
+    if (E == 0) return FEM_OK;
+    if (!verts || !geo || !aligned16(verts) || !aligned16(geo)) return FEM_EINVAL;
+    if (detJ_min && !aligned16(detJ_min)) return FEM_EINVAL;
+    if (E + 1 > (int64_t)0x7fffffff) return FEM_EINVAL;
+    const int q = (kind == FEM_GEO_BP35) ? b->host.n : b->host.m;
+    const int64_t per = (kind == FEM_GEO_BP1 ? 1 : 7) * cube(q);
+    if (overlap(geo, E * per, verts, E * 24)) return FEM_EINVAL;
+    if (detJ_min && (overlap(detJ_min, E, verts, E * 24) || overlap(detJ_min, E, geo, E * per)))
+        return FEM_EINVAL;
+    cudaError_t e = fem::launch_geofacs(b, kind, E, verts, geo, detJ_min, (cudaStream_t)stream);
+    return e == cudaSuccess ? FEM_OK : cuda_fail(e);
+}
+
+int fem_bp1_apply(const fem_basis *b, int64_t E, const double *wJ, const double *q, double *Mq,
+                  void *stream) {
+    const int c = check_apply(b, E, wJ, b ? cube(b->host.m) : 0, q, Mq);
+    if (c != FEM_OK || E == 0) return c;
+    cudaError_t e = fem::launch_bp1(b, E, wJ, q, Mq, (cudaStream_t)stream);
+    return e == cudaSuccess ? FEM_OK : cuda_fail(e);
+}
+
+int fem_bp35_apply(const fem_basis *b, int64_t E, const double *G, double lambda, const double *q,
+                   double *Aq, void *stream) {
+    const int c = check_apply(b, E, G, b ? 7 * cube(b->host.n) : 0, q, Aq);
+    if (c != FEM_OK || E == 0) return c;
+    cudaError_t e = fem::launch_bp35(b, E, G, lambda, q, Aq, (cudaStream_t)stream);
+    return e == cudaSuccess ? FEM_OK : cuda_fail(e);
+}
+
+int fem_bp30_apply(const fem_basis *b, int64_t E, const double *G, double lambda, const double *q,
+                   double *Aq, void *stream) {
+    const int c = check_apply(b, E, G, b ? 7 * cube(b->host.m) : 0, q, Aq);
+    if (c != FEM_OK || E == 0) return c;
+    cudaError_t e = fem::launch_bp30(b, E, G, lambda, q, Aq, (cudaStream_t)stream);
+    return e == cudaSuccess ? FEM_OK : cuda_fail(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+// Internal declarations of the GB300 library (not part of the public ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/fem.h"
+
+namespace fem {
+
+constexpr int kMaxN = FEM_MAX_N;
+constexpr int kMaxQ = kMaxN + 2;
+
+// Layout of the device table of one degree (all FP64, row-major):
+//   I  (m x n) at offI, D (n x n) at offD, Dt (m x m) at offDt,
+//   then GLL nodes r, Gauss nodes rt, GLL weights w, Gauss weights wt,
+//   kMaxQ slots each.
+struct OpsLayout {
+    int n, m;
+    __host__ __device__ constexpr int offI() const { return 0; }
+    __host__ __device__ constexpr int offD() const { return m * n; }
+    __host__ __device__ constexpr int offDt() const { return m * n + n * n; }
+    __host__ __device__ constexpr int total() const { return m * n + n * n + m * m; }
+    __host__ __device__ constexpr int offR() const { return total(); }
+    __host__ __device__ constexpr int offRt() const { return total() + kMaxQ; }
+    __host__ __device__ constexpr int offW() const { return total() + 2 * kMaxQ; }
+    __host__ __device__ constexpr int offWt() const { return total() + 3 * kMaxQ; }
+    __host__ __device__ constexpr int size() const { return total() + 4 * kMaxQ; }
+};
+
+// Host basis: nodes, weights and operator matrices of degree N.
+struct HostBasis {
+    int N, n, m;
+    double r[kMaxQ], w[kMaxQ], rt[kMaxQ], wt[kMaxQ];
+    double I[kMaxQ * kMaxQ], D[kMaxQ * kMaxQ], Dt[kMaxQ * kMaxQ];
+};
+
+// Computes the host basis (Golub-Welsch-type eigenvalue route + barycentric
+// Lagrange formulas).  Returns false on a bad degree.
+bool compute_basis(int N, HostBasis *hb);
+
+}  // namespace fem
+
+struct fem_basis {
+    fem::HostBasis host;
+    double *d_ops;  // device copy of I, D, Dt (fem::OpsLayout)
+    int device;
+};
+
+namespace fem {
+
+// Launchers (one per operator), dispatching on the degree at run time.
+cudaError_t launch_geofacs(const fem_basis *b, int kind, int64_t E, const double *verts,
+                           double *geo, double *detJ_min, cudaStream_t s);
+cudaError_t launch_bp1(const fem_basis *b, int64_t E, const double *wJ, const double *q,
+                       double *Mq, cudaStream_t s);
+cudaError_t launch_bp35(const fem_basis *b, int64_t E, const double *G, double lambda,
+                        const double *q, double *Aq, cudaStream_t s);
+cudaError_t launch_bp30(const fem_basis *b, int64_t E, const double *G, double lambda,
+                        const double *q, double *Aq, cudaStream_t s);
+
+// One-time per-degree kernel preparation (dynamic shared-memory limits).
+cudaError_t prepare_bp1(int N);
+cudaError_t prepare_bp35(int N);
+cudaError_t prepare_bp30(int N);
+cudaError_t prepare_geofacs(int N);
+
+}  // namespace fem
