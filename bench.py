@@ -41,7 +41,10 @@ KERNELS = ["geofacs_bp1", "geofacs_bp35", "geofacs_bp30", "bp1", "bp35", "bp30"]
 # Measured DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) per
 # element at N = 7, with the sha256 of the kernel source it was taken from;
 # a kernel whose source changed since reports traffic null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/bp30_f64_N7_E4096.md: 194.3 MB over 4096 elements
+    "bp30": {"N": 7, "bytes_per_elem": 47430, "sha": "6b3131ac7a833798"},
+}
 
 
 def _peaks():
@@ -194,27 +197,25 @@ def _src_hash(name: str) -> str:
 
 def cpu_oracle_rate(N: int, verts, q, lam: float, target_s: float, cores: int):
     """Times the oracle's step (geometric factors + the three operators) on a
-    sample of elements sized for about target_s seconds; returns
-    (GDOF/s, elements in the sample, seconds, threads)."""
+    sample of about target_s seconds: a prefix of the elements, or whole-mesh
+    passes repeated when one pass is shorter than that.  Returns
+    (GDOF/s, elements per pass, passes, seconds, threads)."""
     import oracle
     threads = oracle.set_threads(cores)
-
-    def run(Es):
-        v, qq = verts[:Es], q[:Es]
-        t0 = time.perf_counter()
-        wJ, _ = oracle.geofacs(N, oracle.KIND_BP1, v)
-        G35, _ = oracle.geofacs(N, oracle.KIND_BP35, v)
-        G30, _ = oracle.geofacs(N, oracle.KIND_BP30, v)
-        oracle.bp1(N, wJ, qq)
-        oracle.bp35(N, G35, lam, qq)
-        oracle.bp30(N, G30, lam, qq)
-        return time.perf_counter() - t0
-
-    Es = min(64, verts.shape[0])
-    dt = run(Es)
-    Es = int(min(verts.shape[0], max(Es, Es * target_s / max(dt, 1e-6))))
-    dt = run(Es)
-    return 3 * Es * (N + 1) ** 3 / dt / 1e9, Es, dt, threads
+    E = verts.shape[0]
+    Es = min(64, E)
+    t0 = time.perf_counter()
+    cpu_oracle_step(N, verts[:Es], q[:Es], lam)
+    dt = time.perf_counter() - t0
+    Es = int(min(E, max(Es, Es * target_s / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    cpu_oracle_step(N, verts[:Es], q[:Es], lam)
+    dt = time.perf_counter() - t0
+    reps = max(1, int(round(target_s / max(dt, 1e-6)))) if Es == E else 1
+    for _ in range(reps - 1):
+        cpu_oracle_step(N, verts[:Es], q[:Es], lam)
+    dt = time.perf_counter() - t0
+    return 3 * Es * reps * (N + 1) ** 3 / dt / 1e9, Es, reps, dt, threads
 
 
 def run_reference(args):
@@ -227,12 +228,12 @@ def run_reference(args):
     import oracle
     oracle.set_threads(cores)
     # size one step for about 1 s of CPU work so the whole run stays short
-    rate, Es, dt, threads = cpu_oracle_rate(N, verts, q, lam, 1.0, cores)
+    rate, Es, reps, dt, threads = cpu_oracle_rate(N, verts, q, lam, 1.0, cores)
     for _ in range(args.warmup):
-        cpu_oracle_rate_fixed(N, verts[:Es], q[:Es], lam)
+        cpu_oracle_step(N, verts[:Es], q[:Es], lam)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        cpu_oracle_rate_fixed(N, verts[:Es], q[:Es], lam)
+        cpu_oracle_step(N, verts[:Es], q[:Es], lam)
     T = time.perf_counter() - t0
     value = args.steps * 3 * Es * (N + 1) ** 3 / T / 1e9
     sample = f"first {Es} of 32768 elements per step (geometric factors + BP1.0 + BP3.5 + BP3.0, N={N})"
@@ -250,7 +251,7 @@ def run_reference(args):
     return 0
 
 
-def cpu_oracle_rate_fixed(N, v, qq, lam):
+def cpu_oracle_step(N, v, qq, lam):
     import oracle
     wJ, _ = oracle.geofacs(N, oracle.KIND_BP1, v)
     G35, _ = oracle.geofacs(N, oracle.KIND_BP35, v)
@@ -277,7 +278,7 @@ def run_ours(args):
 
     N, lam = args.degree, 1.0
     n, m = N + 1, N + 2
-    verts_h, q_h = workload_arrays(N, 32, rank)
+    verts_h, q_h = workload_arrays(N, args.mesh_side, rank)
     E = verts_h.shape[0]
     b = fem.fem_basis_setup(N)
     stream = torch.cuda.current_stream(device)
@@ -391,10 +392,10 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = len(os.sched_getaffinity(0))
-        rate, Es, dt, threads = cpu_oracle_rate(N, verts_h, q_h, lam, args.cpu_seconds, cores)
+        rate, Es, reps, dt, threads = cpu_oracle_rate(N, verts_h, q_h, lam, args.cpu_seconds, cores)
         cpu = {"value": rate, "unit": "GDOF/s", "cores": threads, "kind": "oracle",
-               "sample": f"first {Es} of {E} elements, one step (geometric factors + BP1.0 + BP3.5 + BP3.0), "
-                         f"{dt:.1f} s"}
+               "sample": f"{reps} pass(es) over the first {Es} of {E} elements (geometric factors + "
+                         f"BP1.0 + BP3.5 + BP3.0, N={N}), {dt:.1f} s"}
 
     if rank == 0:
         line = {
@@ -402,7 +403,8 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "E": E, "N": N, "lambda": lam,
+            "config": {"workload": WORKLOAD if E == 32768 else f"{WORKLOAD} [profiling size E={E}]",
+                       "E": E, "N": N, "lambda": lam,
                        "mesh": "32^3 unit cube, interior vertices jittered U[-0.1h,0.1h], trilinear",
                        "l2": "inputs larger than L2 (no flush)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -430,6 +432,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--degree", type=int, default=7)
+    ap.add_argument("--mesh-side", type=int, default=32,
+                    help="elements per side of the cube mesh (32 is the benchmark workload; "
+                         "smaller sides are for profiling captures)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args(argv)
