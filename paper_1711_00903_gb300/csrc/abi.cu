@@ -93,9 +93,9 @@ int fem_basis_setup(int N, fem_basis **out) {
         return e == cudaErrorMemoryAllocation ? FEM_ENOMEM : cuda_fail(e);
     }
     e = cudaMemcpy(b->d_ops, table, sizeof(double) * L.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = fem::prepare_bp1(N);
-    if (e == cudaSuccess) e = fem::prepare_bp35(N);
-    if (e == cudaSuccess) e = fem::prepare_bp30(N);
+    if (e == cudaSuccess) e = fem::prepare_bp1(N, fem::fold_table());
+    if (e == cudaSuccess) e = fem::prepare_bp35(N, fem::fold_table());
+    if (e == cudaSuccess) e = fem::prepare_bp30(N, fem::fold_table());
     if (e == cudaSuccess) e = fem::prepare_geofacs(N);
     if (e != cudaSuccess) {
         cudaFree(b->d_ops);

@@ -12,6 +12,8 @@
 // barycentric Lagrange formulas (Berrut & Trefethen, SIAM Review 46, 2004).
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <vector>
 
 #include "fem_internal.h"
 
@@ -217,6 +219,50 @@ bool compute_basis(int N, HostBasis *hb) {
     bary_diff(hb->n, hb->r, hb->D);
     bary_diff(hb->m, hb->rt, hb->Dt);
     return true;
+}
+
+}  // namespace fem
+
+// ---------------------------------------------------------------------------
+// Folded operator table (see eo.cuh).
+#include "fold_layout.h"
+
+namespace fem {
+
+void build_fold_block(int N, const double *I, const double *D, const double *Dt, double *out) {
+    const int n = N + 1, m = N + 2;
+    double IT[kMaxQ * kMaxQ], DT[kMaxQ * kMaxQ], DtT[kMaxQ * kMaxQ];
+    for (int a = 0; a < m; a++)
+        for (int i = 0; i < n; i++) IT[i * m + a] = I[a * n + i];
+    for (int a = 0; a < n; a++)
+        for (int i = 0; i < n; i++) DT[i * n + a] = D[a * n + i];
+    for (int a = 0; a < m; a++)
+        for (int b = 0; b < m; b++) DtT[b * m + a] = Dt[a * m + b];
+    const double *ops[kFoldCount] = {I, IT, D, DT, Dt, DtT};
+    double *p = out;
+    for (int op = 0; op < kFoldCount; op++) {
+        const int P = fold_rows(op, n, m), Q = fold_cols(op, n, m);
+        fold_matrix(P, Q, ops[op], p);
+        p += fold_size(P, Q);
+    }
+}
+
+}  // namespace fem
+
+namespace fem {
+
+const double *fold_table() {
+    static std::vector<double> table;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        table.assign(kFoldTotal, 0.0);
+        for (int N = 1; N <= kMaxN; N++) {
+            HostBasis hb;
+            compute_basis(N, &hb);
+            build_fold_block(N, hb.I, hb.D, hb.Dt, table.data() + fold_degree_offset(N));
+        }
+    });
+    return table.data();
 }
 
 }  // namespace fem

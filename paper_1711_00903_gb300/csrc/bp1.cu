@@ -3,135 +3,143 @@
 // interpolation GLL -> Gauss (Algorithm 1) and projection back (Algorithm 2)
 // as three one-dimensional contractions each.
 //
-// GB300 design.  The kernel is bound by FP64 instruction issue (FP64 runs at
-// about 1/64 of the FP32 rate on this part), so it keeps the FP64 work at
-// the sum-factorised count 2(m n^3 + m^2 n^2 + m^3 n) + m^3 per element and
-// uses shared memory and registers to remove everything else:
-//   * an m x m slab of threads per element (the 2D thread structure of
-//     Section 6), several elements per block;
-//   * the whole q^e in shared memory, so the six contractions need only
-//     three barriers (the fewest-barriers idea of Section 6, kernel 7);
-//   * the s-interpolation, t-interpolation, wJ scaling and t-projection of a
-//     thread's (a, b) column are fused in registers;
-//   * coalesced global loads of q and wJ and coalesced stores.
-#include "kernels_common.cuh"
+// GB300 design.  Bound by FP64 instruction issue (2 per clock per SM on this
+// part), so every one-dimensional contraction is one thread applying the
+// even-odd folded I or I^T (both centro-symmetric, the property the paper's
+// Section 6 kernel 8 exploits for shared-memory loads) to a whole line, with
+// the operator entries as constant-bank operands (eo.cuh):
+//   1. r-interpolation lines (j, k)          q box    -> X1 (m x n x n)
+//   2. s-interpolation lines (a, k)          X1       -> X2 (m x m x n)
+//   3. per column (a, b): t-interpolation, wJ scaling and t-projection in
+//      registers, back into X2 in place
+//   4. s-projection lines (a, k)             X2       -> X4 (m x n x n)
+//   5. r-projection lines (j, k)             X4       -> Mq (global)
+// Five barriers; tasks are packed densely onto the block's threads.
+#include "eo.cuh"
 
 namespace fem {
 namespace {
 
-template <int n>
+template <int N>
 struct Bp1Cfg {
-    static constexpr int m = n + 1;
+    static constexpr int n = N + 1, m = N + 2;
     static constexpr int NP = n * n * n, MP = m * m * m;
-    static constexpr int B0 = pad2(n * m * m);  // q (n^3), then the t-projected field (n m^2)
-    static constexpr int B1 = pad2(n * n * m);  // r-interpolated, then s-projected field
-    static constexpr int smem_elem = (B0 + B1) * 8;
-    static constexpr int EPB = pick_epb(m, smem_elem);
-    static constexpr int threads = m * m * EPB;
-    static constexpr int smem = (pad2(m * n) + EPB * (B0 + B1)) * 8;
+    using B0 = Box<n, n, n>;  // q
+    using B1 = Box<m, n, n>;  // r-interpolated / s-projected
+    using B2 = Box<m, m, n>;  // s-interpolated / t-projected
+    static constexpr int SA = (B0::size > B2::size) ? B0::size : B2::size;
+    static constexpr int SB = B1::size;
+    static constexpr int per = SA + SB;
+    static constexpr int EPB = pick_epb(m, per * 8);
+    static constexpr int threads = ((m * m * EPB + 31) / 32) * 32;
+    static constexpr int smem = EPB * per * 8;
+    static constexpr int oI = fold_offset(N, kFoldI), oIT = fold_offset(N, kFoldIT);
+    // two resident blocks per SM let one block's barriers overlap the other's
+    // FP64 work; above N = 8 the register cap would spill heavily
+    static constexpr int min_blocks = (N <= 8) ? 2 : 1;
 };
 
-template <int n>
-__global__ void __launch_bounds__(Bp1Cfg<n>::threads)
-bp1_f64_kernel(int64_t E, const double *__restrict__ ops, const double *__restrict__ wJ,
-               const double *__restrict__ q, double *__restrict__ Mq) {
-    using C = Bp1Cfg<n>;
-    constexpr int m = C::m, NP = C::NP, MP = C::MP, EPB = C::EPB, mm = m * m;
+template <int N>
+__global__ void __launch_bounds__(Bp1Cfg<N>::threads, Bp1Cfg<N>::min_blocks)
+bp1_f64_kernel(int64_t E, const double *__restrict__ wJ, const double *__restrict__ q, double *__restrict__ Mq) {
+    using C = Bp1Cfg<N>;
+    using B0 = typename C::B0;
+    using B1 = typename C::B1;
+    using B2 = typename C::B2;
+    constexpr int n = C::n, m = C::m, NP = C::NP, MP = C::MP, EPB = C::EPB, per = C::per;
     extern __shared__ double smem[];
-    double *sI = smem;  // I[a][i] at a*n + i
-    double *buf = sI + pad2(m * n);
-    const OpsLayout L{n, m};
-    block_copy(sI, ops + L.offI(), m * n);
 
-    // stage q of the block's elements (contiguous in memory) into shared
     const int64_t e0 = (int64_t)blockIdx.x * EPB;
-    const int64_t nel = (E - e0) < EPB ? (E - e0) : EPB;
-    for (int t = threadIdx.x; t < EPB * NP; t += blockDim.x) {
-        const int el = t / NP, p = t % NP;
-        buf[el * (C::B0 + C::B1) + p] = (el < nel) ? __ldg(q + (e0 + el) * NP + p) : 0.0;
-    }
-
-    const int el = threadIdx.x / mm, ab = threadIdx.x % mm;
-    const int a = ab % m, b = ab / m;
-    const int64_t e = e0 + el;
-    const bool valid = el < nel;
-    double *b0 = buf + el * (C::B0 + C::B1);  // q [k][j][i], later u [k][b][a]
-    double *b1 = b0 + C::B0;                  // t1 [k][j][a], later v [k][j][a]
-    __syncthreads();
-
-    // r-interpolation: t1[k][j][a] = sum_i I[a][i] q[k][j][i]  (threads with b < n act as j)
-    if (b < n) {
-#pragma unroll
-        for (int k = 0; k < n; k++) {
-            double s = 0.0;
-#pragma unroll
-            for (int i = 0; i < n; i++) s = fma(sI[a * n + i], b0[i + n * (b + n * k)], s);
-            b1[a + m * (b + n * k)] = s;
-        }
+    const int nel = (int)((E - e0) < EPB ? (E - e0) : EPB);
+    for (int t = threadIdx.x; t < nel * NP; t += blockDim.x) {
+        const int el = t / NP, p = t - el * NP;
+        smem[el * per + B0::at(p % n, (p / n) % n, p / (n * n))] = __ldg(q + e0 * NP + t);
     }
     __syncthreads();
 
-    // s- and t-interpolation, scaling and t-projection of column (a, b)
-    {
-        double t2[n];
+    // 1. r-interpolation: lines (j, k), n -> m
+    for_tasks<n * n, EPB>(nel, [&](int el, int r) {
+        const int j = r % n, k = r / n;
+        const double *X0 = smem + el * per;
+        double *X1 = smem + el * per + C::SA;
+        double x[n], y[m];
 #pragma unroll
-        for (int k = 0; k < n; k++) {
-            double s = 0.0;
+        for (int l = 0; l < n; l++) x[l] = X0[B0::at(l, j, k)];
+        eo_apply<m, n, 1, C::oI>(x, y);
 #pragma unroll
-            for (int jj = 0; jj < n; jj++) s = fma(sI[b * n + jj], b1[a + m * (jj + n * k)], s);
-            t2[k] = s;
-        }
-        const double *we = wJ + (valid ? e : 0) * MP + ab;
-        double u[n];
-#pragma unroll
-        for (int k = 0; k < n; k++) u[k] = 0.0;
-#pragma unroll
-        for (int c = 0; c < m; c++) {
-            double g = 0.0;
-#pragma unroll
-            for (int k = 0; k < n; k++) g = fma(sI[c * n + k], t2[k], g);
-            g *= valid ? __ldg(we + c * mm) : 0.0;
-#pragma unroll
-            for (int k = 0; k < n; k++) u[k] = fma(sI[c * n + k], g, u[k]);
-        }
-        // b0 (q) was last read before the previous barrier
-#pragma unroll
-        for (int k = 0; k < n; k++) b0[ab + mm * k] = u[k];
-    }
+        for (int l = 0; l < m; l++) X1[B1::at(l, j, k)] = y[l];
+    });
     __syncthreads();
 
-    // s-projection: v[k][j][a] = sum_b I[b][j] u[k][b][a]
-    if (b < n) {
+    // 2. s-interpolation: lines (a, k), n -> m
+    for_tasks<m * n, EPB>(nel, [&](int el, int r) {
+        const int a = r % m, k = r / m;
+        const double *X1 = smem + el * per + C::SA;
+        double *X2 = smem + el * per;
+        double x[n], y[m];
 #pragma unroll
-        for (int k = 0; k < n; k++) {
-            double s = 0.0;
+        for (int l = 0; l < n; l++) x[l] = X1[B1::at(a, l, k)];
+        eo_apply<m, n, 1, C::oI>(x, y);
 #pragma unroll
-            for (int bb = 0; bb < m; bb++) s = fma(sI[bb * n + b], b0[a + m * (bb + m * k)], s);
-            b1[a + m * (b + n * k)] = s;
-        }
-    }
+        for (int l = 0; l < m; l++) X2[B2::at(a, l, k)] = y[l];
+    });
     __syncthreads();
 
-    // r-projection: out[k][j][i] = sum_a I[a][i] v[k][j][a]
-    if (a < n && b < n && valid) {
-        double *oe = Mq + e * NP + a + n * b;
+    // 3. column (a, b): t-interpolation, scaling by wJ, t-projection
+    for_tasks<m * m, EPB>(nel, [&](int el, int r) {
+        const int a = r % m, b = r / m;
+        double *X2 = smem + el * per;
+        const double *we = wJ + (e0 + el) * MP + r;
+        double x[n], g[m], y[n];
 #pragma unroll
-        for (int k = 0; k < n; k++) {
-            double s = 0.0;
+        for (int l = 0; l < n; l++) x[l] = X2[B2::at(a, b, l)];
+        eo_apply<m, n, 1, C::oI>(x, g);
 #pragma unroll
-            for (int aa = 0; aa < m; aa++) s = fma(sI[aa * n + a], b1[aa + m * (b + n * k)], s);
-            oe[n * n * k] = s;
-        }
-    }
+        for (int c = 0; c < m; c++) g[c] *= __ldg(we + c * m * m);
+        eo_apply<n, m, 1, C::oIT>(g, y);
+#pragma unroll
+        for (int l = 0; l < n; l++) X2[B2::at(a, b, l)] = y[l];
+    });
+    __syncthreads();
+
+    // 4. s-projection: lines (a, k), m -> n
+    for_tasks<m * n, EPB>(nel, [&](int el, int r) {
+        const int a = r % m, k = r / m;
+        const double *X2 = smem + el * per;
+        double *X4 = smem + el * per + C::SA;
+        double x[m], y[n];
+#pragma unroll
+        for (int l = 0; l < m; l++) x[l] = X2[B2::at(a, l, k)];
+        eo_apply<n, m, 1, C::oIT>(x, y);
+#pragma unroll
+        for (int l = 0; l < n; l++) X4[B1::at(a, l, k)] = y[l];
+    });
+    __syncthreads();
+
+    // 5. r-projection: lines (j, k), m -> n, to global
+    for_tasks<n * n, EPB>(nel, [&](int el, int r) {
+        const int j = r % n, k = r / n;
+        const double *X4 = smem + el * per + C::SA;
+        double x[m], y[n];
+#pragma unroll
+        for (int l = 0; l < m; l++) x[l] = X4[B1::at(l, j, k)];
+        eo_apply<n, m, 1, C::oIT>(x, y);
+        double *o = Mq + (e0 + el) * NP + r * n;
+#pragma unroll
+        for (int l = 0; l < n; l++) o[l] = y[l];
+    });
 }
+
+FEM_DEFINE_FOLD_UPLOAD(upload_fold_bp1_tu)
 
 template <int N>
 struct Bp1Launch {
-    static cudaError_t run(const fem_basis *b, int64_t E, const double *wJ, const double *q,
-                           double *Mq, cudaStream_t s) {
-        using C = Bp1Cfg<N + 1>;
+    static cudaError_t run(const fem_basis *b, int64_t E, const double *wJ, const double *q, double *Mq,
+                           cudaStream_t s) {
+        using C = Bp1Cfg<N>;
+        (void)b;
         const int64_t blocks = (E + C::EPB - 1) / C::EPB;
-        bp1_f64_kernel<N + 1><<<(unsigned)blocks, C::threads, C::smem, s>>>(E, b->d_ops, wJ, q, Mq);
+        bp1_f64_kernel<N><<<(unsigned)blocks, C::threads, C::smem, s>>>(E, wJ, q, Mq);
         return cudaGetLastError();
     }
 };
@@ -139,19 +147,22 @@ struct Bp1Launch {
 template <int N>
 struct Bp1Prepare {
     static cudaError_t run() {
-        using C = Bp1Cfg<N + 1>;
-        return cudaFuncSetAttribute(bp1_f64_kernel<N + 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    C::smem);
+        return cudaFuncSetAttribute(bp1_f64_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    Bp1Cfg<N>::smem);
     }
 };
 
 }  // namespace
 
-cudaError_t launch_bp1(const fem_basis *b, int64_t E, const double *wJ, const double *q,
-                       double *Mq, cudaStream_t s) {
+cudaError_t launch_bp1(const fem_basis *b, int64_t E, const double *wJ, const double *q, double *Mq,
+                       cudaStream_t s) {
     return dispatch_degree<Bp1Launch>(b->host.N, b, E, wJ, q, Mq, s);
 }
 
-cudaError_t prepare_bp1(int N) { return dispatch_degree<Bp1Prepare>(N); }
+cudaError_t prepare_bp1(int N, const double *fold_table) {
+    cudaError_t e = upload_fold_bp1_tu(fold_table);
+    if (e != cudaSuccess) return e;
+    return dispatch_degree<Bp1Prepare>(N);
+}
 
 }  // namespace fem

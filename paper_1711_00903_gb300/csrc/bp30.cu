@@ -1,185 +1,235 @@
 // BP3.0 dealiased screened-Poisson matvec, IEEE FP64 (Algorithm 5):
 //   Aq = (I^T x I^T x I^T) [ Dt_r^T Rr + Dt_s^T Rs + Dt_t^T Rt + lambda wJ qg ],
 //   qg = (I x I x I) q,  [Rr Rs Rt] = G [Dt_r qg, Dt_s qg, Dt_t qg],
-// twelve one-dimensional contractions per element, all in one kernel with
-// no global intermediates (Section 8: a three-kernel split was no faster,
-// and removing global intermediates was the largest gain).
+// twelve one-dimensional contractions per element in one kernel with no
+// global intermediates (Section 8: a three-kernel split was no faster, and
+// removing global intermediates was the largest gain).
 //
-// GB300 design.  As for BP1.0 and BP3.5 the FP64 instruction count is the
-// bound on this part (FP64 at about 1/64 of the FP32 rate), so:
-//   * an m x m slab of threads per element, looping over the c slabs;
-//   * q^e staged in shared memory once; the interpolated field qg, and the
-//     r and s partial fluxes, kept whole in shared memory (3 m^3 doubles),
-//     five barriers per element;
-//   * the t-direction work of a thread's (a, b) column (t-interpolation,
-//     t-derivative, t-transpose as a register scatter, t-projection) stays in
-//     registers;
-//   * coalesced loads of q and of each geometric-factor plane.
-#include "kernels_common.cuh"
+// GB300 design.  Bound by FP64 instruction issue (2 per clock per SM), so
+// every contraction is one thread applying an even-odd folded operator to
+// a whole line with constant-bank operands (eo.cuh), and the element lives
+// in three m^3 shared-memory boxes:
+//   1. r-interpolation lines (j, k)               q      -> X1
+//   2. s-interpolation lines (a, k)               X1     -> X2
+//   3. t-interpolation columns (a, b)             X2     -> QG (m^3)
+//   4. r- and s-derivative lines                  QG     -> UR, US
+//   5. per column (a, b): t-derivative, chain rule with the 7 factors,
+//      t-transpose and the lambda wJ qg term, in registers (kept to step 7)
+//   6. r- and s-transpose lines, in place          UR, US
+//   7. per column: sum, t-projection               -> X3 (m x m x n)
+//   8. s-projection lines (a, k)                  X3     -> X4 (m x n x n)
+//   9. r-projection lines (j, k)                  X4     -> Aq (global)
+#include "eo.cuh"
 
 namespace fem {
 namespace {
 
-template <int n>
+template <int N>
 struct Bp30Cfg {
-    static constexpr int m = n + 1;
-    static constexpr int NP = n * n * n, MP = m * m * m;
-    static constexpr int SE = pad2(MP);  // one m^3 plane
-    static constexpr int smem_elem = 3 * SE * 8;
-    static constexpr int EPB = pick_epb(m, smem_elem);
-    static constexpr int threads = m * m * EPB;
-    static constexpr int smem = (pad2(m * n) + pad2(m * m) + EPB * 3 * SE) * 8;
+    static constexpr int n = N + 1, m = N + 2;
+    static constexpr int NP = n * n * n, MP = m * m * m, mm = m * m;
+    using B0 = Box<n, n, n>;
+    using B1 = Box<m, n, n>;
+    using B2 = Box<m, m, n>;
+    using B3 = Box<m, m, m>;
+    static constexpr int S = B3::size;  // every buffer holds one m^3 box
+    static constexpr int per = 3 * S;
+    static constexpr int EPB = pick_epb(m, per * 8);
+    static constexpr int threads = ((mm * EPB + 31) / 32) * 32;
+    static constexpr int smem = EPB * per * 8;
+    static constexpr int oI = fold_offset(N, kFoldI), oIT = fold_offset(N, kFoldIT);
+    static constexpr int oDt = fold_offset(N, kFoldDt), oDtT = fold_offset(N, kFoldDtT);
 };
 
-template <int n>
-__global__ void __launch_bounds__(Bp30Cfg<n>::threads)
-bp30_f64_kernel(int64_t E, const double *__restrict__ ops, const double *__restrict__ G,
-                double lambda, const double *__restrict__ q, double *__restrict__ Aq) {
-    using C = Bp30Cfg<n>;
-    constexpr int m = C::m, NP = C::NP, MP = C::MP, EPB = C::EPB, mm = m * m, SE = C::SE;
+template <int N>
+__global__ void __launch_bounds__(Bp30Cfg<N>::threads)
+bp30_f64_kernel(int64_t E, const double *__restrict__ G, double lambda, const double *__restrict__ q,
+                double *__restrict__ Aq) {
+    using C = Bp30Cfg<N>;
+    using B0 = typename C::B0;
+    using B1 = typename C::B1;
+    using B2 = typename C::B2;
+    using B3 = typename C::B3;
+    constexpr int n = C::n, m = C::m, NP = C::NP, MP = C::MP, mm = C::mm, EPB = C::EPB;
+    constexpr int S = C::S, per = C::per;
     extern __shared__ double smem[];
-    double *sI = smem;                  // I[a][i] at a*n + i
-    double *sDt = sI + pad2(m * n);     // Dt[a][d] at a*m + d
-    double *buf = sDt + pad2(m * m);
-    const OpsLayout L{n, m};
-    block_copy(sI, ops + L.offI(), m * n);
-    block_copy(sDt, ops + L.offDt(), m * m);
+    // per element: buffer A = smem + el*per, B = A + S, C = A + 2S
 
     const int64_t e0 = (int64_t)blockIdx.x * EPB;
-    const int64_t nel = (E - e0) < EPB ? (E - e0) : EPB;
-    // stage q into plane B of each element
-    for (int t = threadIdx.x; t < EPB * NP; t += blockDim.x) {
-        const int el = t / NP, p = t % NP;
-        buf[el * 3 * SE + SE + p] = (el < nel) ? __ldg(q + (e0 + el) * NP + p) : 0.0;
-    }
-
-    const int el = threadIdx.x / mm, ab = threadIdx.x % mm;
-    const int a = ab % m, b = ab / m;
-    const int64_t e = e0 + el;
-    const bool valid = el < nel;
-    double *pA = buf + el * 3 * SE;  // qg [c][b][a], later u [k][b][a]
-    double *pB = pA + SE;            // q, later Rr, later v [k][j][a]
-    double *pC = pB + SE;            // t1 [k][j][a], later Rs
-    __syncthreads();
-
-    // r-interpolation: t1[k][j][a] = sum_i I[a][i] q[k][j][i]
-    if (b < n) {
-#pragma unroll
-        for (int k = 0; k < n; k++) {
-            double s = 0.0;
-#pragma unroll
-            for (int i = 0; i < n; i++) s = fma(sI[a * n + i], pB[i + n * (b + n * k)], s);
-            pC[a + m * (b + n * k)] = s;
-        }
+    const int nel = (int)((E - e0) < EPB ? (E - e0) : EPB);
+    for (int t = threadIdx.x; t < nel * NP; t += blockDim.x) {
+        const int el = t / NP, p = t - el * NP;
+        smem[el * per + S + B0::at(p % n, (p / n) % n, p / (n * n))] = __ldg(q + e0 * NP + t);
     }
     __syncthreads();
 
-    // s- and t-interpolation of column (a, b) into registers and shared
-    double qg[m];
-    {
-        double t2[n];
+    // 1. r-interpolation (j, k): q (buffer B) -> X1 (buffer C)
+    for_tasks<n * n, EPB>(nel, [&](int el, int r) {
+        const int j = r % n, k = r / n;
+        const double *X0 = smem + el * per + S;
+        double *X1 = smem + el * per + 2 * S;
+        double x[n], y[m];
 #pragma unroll
-        for (int k = 0; k < n; k++) {
-            double s = 0.0;
+        for (int l = 0; l < n; l++) x[l] = X0[B0::at(l, j, k)];
+        eo_apply<m, n, 1, C::oI>(x, y);
 #pragma unroll
-            for (int jj = 0; jj < n; jj++) s = fma(sI[b * n + jj], pC[a + m * (jj + n * k)], s);
-            t2[k] = s;
-        }
-#pragma unroll
-        for (int c = 0; c < m; c++) {
-            double s = 0.0;
-#pragma unroll
-            for (int k = 0; k < n; k++) s = fma(sI[c * n + k], t2[k], s);
-            qg[c] = s;
-            pA[ab + mm * c] = s;
-        }
-    }
+        for (int l = 0; l < m; l++) X1[B1::at(l, j, k)] = y[l];
+    });
     __syncthreads();
 
-    // derivatives at the Gauss points, chain rule, t-transpose, mass term
+    // 2. s-interpolation (a, k): X1 (C) -> X2 (B)
+    for_tasks<m * n, EPB>(nel, [&](int el, int r) {
+        const int a = r % m, k = r / m;
+        const double *X1 = smem + el * per + 2 * S;
+        double *X2 = smem + el * per + S;
+        double x[n], y[m];
+#pragma unroll
+        for (int l = 0; l < n; l++) x[l] = X1[B1::at(a, l, k)];
+        eo_apply<m, n, 1, C::oI>(x, y);
+#pragma unroll
+        for (int l = 0; l < m; l++) X2[B2::at(a, l, k)] = y[l];
+    });
+    __syncthreads();
+
+    // 3. t-interpolation (a, b): X2 (B) -> QG (A)
+    for_tasks<mm, EPB>(nel, [&](int el, int r) {
+        const int a = r % m, b = r / m;
+        const double *X2 = smem + el * per + S;
+        double *QG = smem + el * per;
+        double x[n], y[m];
+#pragma unroll
+        for (int l = 0; l < n; l++) x[l] = X2[B2::at(a, b, l)];
+        eo_apply<m, n, 1, C::oI>(x, y);
+#pragma unroll
+        for (int l = 0; l < m; l++) QG[B3::at(a, b, l)] = y[l];
+    });
+    __syncthreads();
+
+    // 4. r-derivative lines (b=u, c=v) -> UR (B), s-derivative lines (a=u, c=v) -> US (C)
+    for_tasks<mm, EPB>(nel, [&](int el, int r) {
+        const int u = r % m, v = r / m;
+        const double *QG = smem + el * per;
+        double *UR = smem + el * per + S, *US = smem + el * per + 2 * S;
+        double x[m], y[m];
+#pragma unroll
+        for (int l = 0; l < m; l++) x[l] = QG[B3::at(l, u, v)];
+        eo_apply<m, m, -1, C::oDt>(x, y);
+#pragma unroll
+        for (int l = 0; l < m; l++) UR[B3::at(l, u, v)] = y[l];
+#pragma unroll
+        for (int l = 0; l < m; l++) x[l] = QG[B3::at(u, l, v)];
+        eo_apply<m, m, -1, C::oDt>(x, y);
+#pragma unroll
+        for (int l = 0; l < m; l++) US[B3::at(u, l, v)] = y[l];
+    });
+    __syncthreads();
+
+    // 5. column (a, b): t-derivative, chain rule, t-transpose, mass term.
+    // Each thread has at most one column task (threads >= m*m*EPB), so acc
+    // stays in its registers until step 7.
+    const int cel = threadIdx.x / mm, cr = threadIdx.x - cel * mm;
+    const int ca = cr % m, cb = cr / m;
+    const bool cact = cel < nel;
     double acc[m];
+    if (cact) {
+        const double *QG = smem + cel * per;
+        double *UR = smem + cel * per + S, *US = smem + cel * per + 2 * S;
+        double x[m], ut[m], Rt[m];
 #pragma unroll
-    for (int c = 0; c < m; c++) acc[c] = 0.0;
-    const double *Ge = G + (valid ? e : 0) * 7 * MP + ab;
-#pragma unroll
-    for (int c = 0; c < m; c++) {
-        const double *qc = pA + mm * c;
-        double ur = 0.0, us = 0.0, ut = 0.0;
-#pragma unroll
-        for (int d = 0; d < m; d++) {
-            ur = fma(sDt[a * m + d], qc[d + m * b], ur);
-            us = fma(sDt[b * m + d], qc[a + m * d], us);
-            ut = fma(sDt[c * m + d], qg[d], ut);
-        }
-        double g[7];
-#pragma unroll
-        for (int h = 0; h < 7; h++) g[h] = valid ? __ldg(Ge + h * MP + c * mm) : 0.0;
-        const double Rr = g[0] * ur + g[1] * us + g[2] * ut;
-        const double Rs = g[1] * ur + g[3] * us + g[4] * ut;
-        const double Rt = g[2] * ur + g[4] * us + g[5] * ut;
-        pB[ab + mm * c] = Rr;  // q in pB was last read before two barriers ago
-        pC[ab + mm * c] = Rs;  // t1 in pC was last read before the previous barrier
-#pragma unroll
-        for (int d = 0; d < m; d++) acc[d] = fma(sDt[c * m + d], Rt, acc[d]);
-        if (lambda != 0.0) acc[c] = fma(lambda * g[6], qg[c], acc[c]);
-    }
-    __syncthreads();
-
-    // r and s transposes, then t-projection into shared
-    {
+        for (int l = 0; l < m; l++) x[l] = QG[B3::at(ca, cb, l)];
+        eo_apply<m, m, -1, C::oDt>(x, ut);
+        const double *Ge = G + (e0 + cel) * 7 * MP + cr;
 #pragma unroll
         for (int c = 0; c < m; c++) {
-            const double *Rrc = pB + mm * c, *Rsc = pC + mm * c;
-            double s = acc[c];
+            const int s = B3::at(ca, cb, c);
+            const double ur = UR[s], us = US[s];
+            double g[7];
 #pragma unroll
-            for (int d = 0; d < m; d++) {
-                s = fma(sDt[d * m + a], Rrc[d + m * b], s);
-                s = fma(sDt[d * m + b], Rsc[a + m * d], s);
-            }
-            acc[c] = s;
+            for (int h = 0; h < 7; h++) g[h] = __ldg(Ge + h * MP + c * mm);
+            UR[s] = g[0] * ur + g[1] * us + g[2] * ut[c];
+            US[s] = g[1] * ur + g[3] * us + g[4] * ut[c];
+            Rt[c] = g[2] * ur + g[4] * us + g[5] * ut[c];
+            acc[c] = (lambda != 0.0) ? (lambda * g[6]) * x[c] : 0.0;
         }
+        double y[m];
+        eo_apply<m, m, -1, C::oDtT>(Rt, y);
 #pragma unroll
-        for (int k = 0; k < n; k++) {
-            double s = 0.0;
-#pragma unroll
-            for (int c = 0; c < m; c++) s = fma(sI[c * n + k], acc[c], s);
-            pA[ab + mm * k] = s;  // qg in pA was last read before the previous barrier
-        }
+        for (int c = 0; c < m; c++) acc[c] += y[c];
     }
     __syncthreads();
 
-    // s-projection: v[k][j][a] = sum_b I[b][j] u[k][b][a]
-    if (b < n) {
+    // 6. r- and s-transposes in place
+    for_tasks<mm, EPB>(nel, [&](int el, int r) {
+        const int u = r % m, v = r / m;
+        double *UR = smem + el * per + S, *US = smem + el * per + 2 * S;
+        double x[m], y[m];
 #pragma unroll
-        for (int k = 0; k < n; k++) {
-            double s = 0.0;
+        for (int l = 0; l < m; l++) x[l] = UR[B3::at(l, u, v)];
+        eo_apply<m, m, -1, C::oDtT>(x, y);
 #pragma unroll
-            for (int bb = 0; bb < m; bb++) s = fma(sI[bb * n + b], pA[a + m * (bb + m * k)], s);
-            pB[a + m * (b + n * k)] = s;  // Rr in pB was last read before the previous barrier
+        for (int l = 0; l < m; l++) UR[B3::at(l, u, v)] = y[l];
+#pragma unroll
+        for (int l = 0; l < m; l++) x[l] = US[B3::at(u, l, v)];
+        eo_apply<m, m, -1, C::oDtT>(x, y);
+#pragma unroll
+        for (int l = 0; l < m; l++) US[B3::at(u, l, v)] = y[l];
+    });
+    __syncthreads();
+
+    // 7. column (a, b): sum of the three directions, t-projection -> X3 (A)
+    if (cact) {
+        const double *UR = smem + cel * per + S, *US = smem + cel * per + 2 * S;
+        double *X3 = smem + cel * per;
+        double y[n];
+#pragma unroll
+        for (int c = 0; c < m; c++) {
+            const int s = B3::at(ca, cb, c);
+            acc[c] += UR[s] + US[s];
         }
+        eo_apply<n, m, 1, C::oIT>(acc, y);
+#pragma unroll
+        for (int l = 0; l < n; l++) X3[B2::at(ca, cb, l)] = y[l];
     }
     __syncthreads();
 
-    // r-projection and store
-    if (a < n && b < n && valid) {
-        double *oe = Aq + e * NP + a + n * b;
+    // 8. s-projection (a, k): X3 (A) -> X4 (B)
+    for_tasks<m * n, EPB>(nel, [&](int el, int r) {
+        const int a = r % m, k = r / m;
+        const double *X3 = smem + el * per;
+        double *X4 = smem + el * per + S;
+        double x[m], y[n];
 #pragma unroll
-        for (int k = 0; k < n; k++) {
-            double s = 0.0;
+        for (int l = 0; l < m; l++) x[l] = X3[B2::at(a, l, k)];
+        eo_apply<n, m, 1, C::oIT>(x, y);
 #pragma unroll
-            for (int aa = 0; aa < m; aa++) s = fma(sI[aa * n + a], pB[aa + m * (b + n * k)], s);
-            oe[n * n * k] = s;
-        }
-    }
+        for (int l = 0; l < n; l++) X4[B1::at(a, l, k)] = y[l];
+    });
+    __syncthreads();
+
+    // 9. r-projection (j, k): X4 (B) -> Aq
+    for_tasks<n * n, EPB>(nel, [&](int el, int r) {
+        const double *X4 = smem + el * per + S;
+        const int j = r % n, k = r / n;
+        double x[m], y[n];
+#pragma unroll
+        for (int l = 0; l < m; l++) x[l] = X4[B1::at(l, j, k)];
+        eo_apply<n, m, 1, C::oIT>(x, y);
+        double *o = Aq + (e0 + el) * NP + r * n;
+#pragma unroll
+        for (int l = 0; l < n; l++) o[l] = y[l];
+    });
 }
+
+FEM_DEFINE_FOLD_UPLOAD(upload_fold_bp30_tu)
 
 template <int N>
 struct Bp30Launch {
-    static cudaError_t run(const fem_basis *b, int64_t E, const double *G, double lambda,
-                           const double *q, double *Aq, cudaStream_t s) {
-        using C = Bp30Cfg<N + 1>;
+    static cudaError_t run(const fem_basis *b, int64_t E, const double *G, double lambda, const double *q,
+                           double *Aq, cudaStream_t s) {
+        using C = Bp30Cfg<N>;
+        (void)b;
         const int64_t blocks = (E + C::EPB - 1) / C::EPB;
-        bp30_f64_kernel<N + 1><<<(unsigned)blocks, C::threads, C::smem, s>>>(E, b->d_ops, G, lambda, q, Aq);
+        bp30_f64_kernel<N><<<(unsigned)blocks, C::threads, C::smem, s>>>(E, G, lambda, q, Aq);
         return cudaGetLastError();
     }
 };
@@ -187,19 +237,22 @@ struct Bp30Launch {
 template <int N>
 struct Bp30Prepare {
     static cudaError_t run() {
-        using C = Bp30Cfg<N + 1>;
-        return cudaFuncSetAttribute(bp30_f64_kernel<N + 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    C::smem);
+        return cudaFuncSetAttribute(bp30_f64_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    Bp30Cfg<N>::smem);
     }
 };
 
 }  // namespace
 
-cudaError_t launch_bp30(const fem_basis *b, int64_t E, const double *G, double lambda,
-                        const double *q, double *Aq, cudaStream_t s) {
+cudaError_t launch_bp30(const fem_basis *b, int64_t E, const double *G, double lambda, const double *q,
+                        double *Aq, cudaStream_t s) {
     return dispatch_degree<Bp30Launch>(b->host.N, b, E, G, lambda, q, Aq, s);
 }
 
-cudaError_t prepare_bp30(int N) { return dispatch_degree<Bp30Prepare>(N); }
+cudaError_t prepare_bp30(int N, const double *fold_table) {
+    cudaError_t e = upload_fold_bp30_tu(fold_table);
+    if (e != cudaSuccess) return e;
+    return dispatch_degree<Bp30Prepare>(N);
+}
 
 }  // namespace fem

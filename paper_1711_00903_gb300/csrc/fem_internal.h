@@ -59,10 +59,14 @@ cudaError_t launch_bp35(const fem_basis *b, int64_t E, const double *G, double l
 cudaError_t launch_bp30(const fem_basis *b, int64_t E, const double *G, double lambda,
                         const double *q, double *Aq, cudaStream_t s);
 
-// One-time per-degree kernel preparation (dynamic shared-memory limits).
-cudaError_t prepare_bp1(int N);
-cudaError_t prepare_bp35(int N);
-cudaError_t prepare_bp30(int N);
+// One-time per-degree kernel preparation: uploads the folded operator
+// table of every degree (fold_table()) and sets dynamic shared-memory limits.
+cudaError_t prepare_bp1(int N, const double *fold_table);
+cudaError_t prepare_bp35(int N, const double *fold_table);
+cudaError_t prepare_bp30(int N, const double *fold_table);
 cudaError_t prepare_geofacs(int N);
+
+// Host copy of the folded operator table of all degrees 1..15 (built once).
+const double *fold_table();
 
 }  // namespace fem

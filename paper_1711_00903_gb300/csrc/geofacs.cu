@@ -20,21 +20,35 @@ namespace {
 template <int qn>
 struct GeoCfg {
     static constexpr int QP = qn * qn * qn, qq = qn * qn;
-    static constexpr int smem_elem = (24 + 9 * qq + qq) * 8;
+    static constexpr int SD = (qq > 36) ? qq : 36;  // per-thread minima, or the 36 map coefficients
+    static constexpr int smem_elem = (24 + 9 * qq + SD) * 8;
     static constexpr int EPB = pick_epb(qn, smem_elem);
     static constexpr int threads = qq * EPB;
-    static constexpr int smem = (2 * pad2(qn) + EPB * pad2(24 + 9 * qq + qq)) * 8;
+    static constexpr int smem = (2 * pad2(qn) + EPB * pad2(24 + 9 * qq + SD)) * 8;
 };
 
-// kind: 1 = wJ only, otherwise 7 planes.
-template <int qn, int kind>
+// 1 / d in FP64: an FP32 reciprocal seed (24 bits) refined by two Newton
+// steps r <- r + r (1 - d r), each doubling the correct bits (48, then the
+// full 53).  Falls back to a division when d is outside the FP32 range.
+__device__ __forceinline__ double recip(double d) {
+    const float df = __double2float_rn(d);
+    if (!(fabsf(df) > 1e-37f && fabsf(df) < 1e37f)) return 1.0 / d;
+    double r = (double)__frcp_rn(df);
+    double e = fma(-d, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-d, r, 1.0);
+    return fma(r, e, r);
+}
+
+// kind: 1 = wJ only, otherwise 7 planes; MIN: also the per-element minimum |J|.
+template <int qn, int kind, bool MIN>
 __global__ void __launch_bounds__(GeoCfg<qn>::threads)
 geofacs_kernel(int64_t E, const double *__restrict__ nodes, const double *__restrict__ weights,
                const double *__restrict__ verts, double *__restrict__ geo,
                double *__restrict__ detJ_min) {
     using C = GeoCfg<qn>;
     constexpr int QP = C::QP, qq = C::qq, EPB = C::EPB;
-    constexpr int PER = pad2(24 + 9 * qq + qq);
+    constexpr int PER = pad2(24 + 9 * qq + C::SD);
     extern __shared__ double smem[];
     double *sx = smem, *sw = sx + pad2(qn);
     double *buf = sw + pad2(qn);
@@ -60,31 +74,52 @@ geofacs_kernel(int64_t E, const double *__restrict__ nodes, const double *__rest
     double *Xt = Xs + 3 * qq;              // dx/dt at (r_u, s_v)
     double *sdet = Xt + 3 * qq;            // per-thread minimum |J|
 
-    // tabulate the three column tables of X: with x = sum_c x_c phi_c,
-    // dx/dr = 1/8 sum_c x_c sr_c (1 + ss_c s)(1 + st_c t), etc.
-    {
-        const double p = sx[u], w2 = sx[v];
-        double cr[3] = {0, 0, 0}, cs[3] = {0, 0, 0}, ct[3] = {0, 0, 0};
-#pragma unroll
-        for (int c = 0; c < 8; c++) {
-            const double sr = (c & 1) ? 1.0 : -1.0, ss = (c & 2) ? 1.0 : -1.0, st = (c & 4) ? 1.0 : -1.0;
-            // X_r at (s = p, t = w2); X_s at (r = p, t = w2); X_t at (r = p, s = w2)
-            const double fr = sr * (1.0 + ss * p) * (1.0 + st * w2);
-            const double fs = ss * (1.0 + sr * p) * (1.0 + st * w2);
-            const double ft = st * (1.0 + sr * p) * (1.0 + ss * w2);
-#pragma unroll
-            for (int d = 0; d < 3; d++) {
-                const double xc = vx[c * 3 + d];
-                cr[d] = fma(xc, fr, cr[d]);
-                cs[d] = fma(xc, fs, cs[d]);
-                ct[d] = fma(xc, ft, ct[d]);
-            }
+    // tabulate the three column tables of X.  Along r the map's derivative is
+    // dx/dr(s, t) = 1/8 [ A (1-s)(1-t) + B (1+s)(1-t) + C (1-s)(1+t) + D (1+s)(1+t) ]
+    // with the r-edge vectors A = x1 - x0, B = x3 - x2, C = x5 - x4,
+    // D = x7 - x6, i.e. the bilinear form K0 + s K1 + t (K2 + s K3); the same
+    // holds along s and t with their own edges.  The 3 x 4 x 3 coefficients
+    // of an element are formed once (in shared memory), then each table entry
+    // costs three FMAs per component.
+    double *K = sdet;  // 36 coefficients, reused below for the minimum
+    for (int ci = ab; ci < 36; ci += qq) {
+        // K[(dir*4 + w)*3 + d]: dir 0 = r, 1 = s, 2 = t; w = coefficient
+        const int dir = ci / 12, w = (ci / 3) % 4, d = ci % 3;
+        // corner pairs (lower, upper) of the four edges along dir, in the
+        // order (-,-), (+,-), (-,+), (+,+) of the two other coordinates
+        const int stride = 1 << dir;
+        int base[4];
+        {
+            const int o1 = (dir == 0) ? 2 : 1, o2 = (dir == 2) ? 2 : 4;
+            base[0] = 0;
+            base[1] = o1;
+            base[2] = o2;
+            base[3] = o1 + o2;
         }
+        double ed[4];
+#pragma unroll
+        for (int h = 0; h < 4; h++) ed[h] = vx[(base[h] + stride) * 3 + d] - vx[base[h] * 3 + d];
+        // (1-p)(1-q) A + (1+p)(1-q) B + (1-p)(1+q) C + (1+p)(1+q) D
+        //   = (A+B+C+D) + p (B-A+D-C) + q (C+D-A-B) + p q (A-B-C+D)
+        double kv;
+        if (w == 0) kv = ed[0] + ed[1] + ed[2] + ed[3];
+        else if (w == 1) kv = (ed[1] - ed[0]) + (ed[3] - ed[2]);
+        else if (w == 2) kv = (ed[2] + ed[3]) - (ed[0] + ed[1]);
+        else kv = (ed[0] - ed[1]) - (ed[2] - ed[3]);
+        K[ci] = 0.125 * kv;
+    }
+    __syncthreads();
+    {
+        // entry (u, v): X_r at (s_u, t_v), X_s at (r_u, t_v), X_t at (r_u, s_v)
+        const double p = sx[u], w2 = sx[v];
 #pragma unroll
         for (int d = 0; d < 3; d++) {
-            Xr[ab * 3 + d] = 0.125 * cr[d];
-            Xs[ab * 3 + d] = 0.125 * cs[d];
-            Xt[ab * 3 + d] = 0.125 * ct[d];
+            Xr[ab * 3 + d] = fma(w2, fma(p, K[(0 * 4 + 3) * 3 + d], K[(0 * 4 + 2) * 3 + d]),
+                                 fma(p, K[(0 * 4 + 1) * 3 + d], K[(0 * 4 + 0) * 3 + d]));
+            Xs[ab * 3 + d] = fma(w2, fma(p, K[(1 * 4 + 3) * 3 + d], K[(1 * 4 + 2) * 3 + d]),
+                                 fma(p, K[(1 * 4 + 1) * 3 + d], K[(1 * 4 + 0) * 3 + d]));
+            Xt[ab * 3 + d] = fma(w2, fma(p, K[(2 * 4 + 3) * 3 + d], K[(2 * 4 + 2) * 3 + d]),
+                                 fma(p, K[(2 * 4 + 1) * 3 + d], K[(2 * 4 + 0) * 3 + d]));
         }
     }
     __syncthreads();
@@ -111,7 +146,7 @@ geofacs_kernel(int64_t E, const double *__restrict__ nodes, const double *__rest
         const double Cr2 = xs[0] * xt[1] - xs[1] * xt[0];
         const double det = xr[0] * Cr0 + xr[1] * Cr1 + xr[2] * Cr2;
         const double W = wab * sw[c];
-        mindet = fmin(mindet, det);
+        if (MIN) mindet = fmin(mindet, det);
         if (kind == 1) {
             if (valid) ge[c * qq] = W * det;
         } else {
@@ -121,7 +156,7 @@ geofacs_kernel(int64_t E, const double *__restrict__ nodes, const double *__rest
             const double Ct0 = xr[1] * xs[2] - xr[2] * xs[1];
             const double Ct1 = xr[2] * xs[0] - xr[0] * xs[2];
             const double Ct2 = xr[0] * xs[1] - xr[1] * xs[0];
-            const double f = W / det;
+            const double f = W * recip(det);
             if (valid) {
                 double *g = ge + c * qq;
                 g[0 * QP] = f * (Cr0 * Cr0 + Cr1 * Cr1 + Cr2 * Cr2);
@@ -134,7 +169,7 @@ geofacs_kernel(int64_t E, const double *__restrict__ nodes, const double *__rest
             }
         }
     }
-    if (detJ_min) {
+    if (MIN) {
         sdet[ab] = mindet;
         __syncthreads();
         for (int s = 1; s < qq; s *= 2) {
@@ -153,16 +188,16 @@ struct GeoLaunch {
         if (kind == FEM_GEO_BP35) {
             using C = GeoCfg<N + 1>;
             const int64_t blocks = (E + C::EPB - 1) / C::EPB;
-            geofacs_kernel<N + 1, 2><<<(unsigned)blocks, C::threads, C::smem, s>>>(
-                E, b->d_ops + L.offR(), b->d_ops + L.offW(), verts, geo, detJ_min);
+            auto k = detJ_min ? geofacs_kernel<N + 1, 2, true> : geofacs_kernel<N + 1, 2, false>;
+            k<<<(unsigned)blocks, C::threads, C::smem, s>>>(E, b->d_ops + L.offR(), b->d_ops + L.offW(), verts,
+                                                            geo, detJ_min);
         } else {
             using C = GeoCfg<N + 2>;
             const int64_t blocks = (E + C::EPB - 1) / C::EPB;
             const double *x = b->d_ops + L.offRt(), *w = b->d_ops + L.offWt();
-            if (kind == FEM_GEO_BP1)
-                geofacs_kernel<N + 2, 1><<<(unsigned)blocks, C::threads, C::smem, s>>>(E, x, w, verts, geo, detJ_min);
-            else
-                geofacs_kernel<N + 2, 3><<<(unsigned)blocks, C::threads, C::smem, s>>>(E, x, w, verts, geo, detJ_min);
+            auto k = (kind == FEM_GEO_BP1) ? (detJ_min ? geofacs_kernel<N + 2, 1, true> : geofacs_kernel<N + 2, 1, false>)
+                                           : (detJ_min ? geofacs_kernel<N + 2, 3, true> : geofacs_kernel<N + 2, 3, false>);
+            k<<<(unsigned)blocks, C::threads, C::smem, s>>>(E, x, w, verts, geo, detJ_min);
         }
         return cudaGetLastError();
     }
@@ -170,15 +205,20 @@ struct GeoLaunch {
 
 template <int N>
 struct GeoPrepare {
+    template <int qn, int kind, bool MIN>
+    static cudaError_t one() {
+        return cudaFuncSetAttribute(geofacs_kernel<qn, kind, MIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    GeoCfg<qn>::smem);
+    }
     static cudaError_t run() {
-        cudaError_t err = cudaFuncSetAttribute(geofacs_kernel<N + 1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               GeoCfg<N + 1>::smem);
-        if (err != cudaSuccess) return err;
-        err = cudaFuncSetAttribute(geofacs_kernel<N + 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   GeoCfg<N + 2>::smem);
-        if (err != cudaSuccess) return err;
-        return cudaFuncSetAttribute(geofacs_kernel<N + 2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    GeoCfg<N + 2>::smem);
+        cudaError_t e = cudaSuccess;
+        if (e == cudaSuccess) e = one<N + 1, 2, false>();
+        if (e == cudaSuccess) e = one<N + 1, 2, true>();
+        if (e == cudaSuccess) e = one<N + 2, 1, false>();
+        if (e == cudaSuccess) e = one<N + 2, 1, true>();
+        if (e == cudaSuccess) e = one<N + 2, 3, false>();
+        if (e == cudaSuccess) e = one<N + 2, 3, true>();
+        return e;
     }
 };
 
