@@ -72,6 +72,9 @@ def lib():
             L.or_bp35.argtypes = [i32, i64, _dp, dbl, _dp, _dp]
             L.or_bp30.argtypes = [i32, i64, _dp, dbl, _dp, _dp]
             L.or_dense_element.argtypes = [i32, i32, i32, dbl, _dp, _dp]
+            L.or_bp35_diag.argtypes = [i32, i64, _dp, dbl, _dp]
+            L.or_pcg_bp35.argtypes = [i32, i64, _dp, dbl, _dp, _dp, dbl, i32,
+                                      C.POINTER(C.c_double)]
             _lib = L
     return _lib
 
@@ -213,3 +216,45 @@ def dense_element(N: int, verts8: np.ndarray, rule: str, stiff: bool, lam: float
     assert lib().or_dense_element(N, 1 if rule == "gll" else 0, int(stiff), float(lam), v,
                                   A.reshape(-1)) == 0
     return A
+
+
+def bp35_diag(N: int, geo: np.ndarray, lam: float) -> np.ndarray:
+    """Closed-form diagonal of the BP3.5 operator (Algorithm 4's D^T G D +
+    lambda J), the Jacobi preconditioner."""
+    n = N + 1
+    E = geo.shape[0]
+    out = np.zeros((E, n ** 3))
+    assert lib().or_bp35_diag(N, E, _vec(geo, E, 7 * n ** 3), float(lam), out.reshape(-1)) == 0
+    return out
+
+
+def pcg_bp35(N: int, geo: np.ndarray, lam: float, b: np.ndarray, x0=None, tol=1e-10, maxit=10000):
+    """Jacobi-PCG (Saad, Algorithm 9.1) on the unassembled BP3.5 system
+    A x = b.  Returns (x, iterations, relative residual); raises on
+    breakdown."""
+    n = N + 1
+    E = b.shape[0]
+    x = np.zeros((E, n ** 3)) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    rel = C.c_double(0.0)
+    it = lib().or_pcg_bp35(N, E, _vec(geo, E, 7 * n ** 3), float(lam), _vec(b, E, n ** 3),
+                           x.reshape(-1), float(tol), int(maxit), C.byref(rel))
+    if it < 0:
+        raise RuntimeError(f"oracle PCG failed ({it})")
+    return x, it, rel.value
+
+
+def gll_node_coordinates(N: int, verts: np.ndarray) -> np.ndarray:
+    """Physical coordinates (E, n^3, 3) of every element's GLL nodes under
+    its trilinear map (used to build manufactured right-hand sides)."""
+    r, _ = gll(N)
+    n = N + 1
+    E = verts.shape[0]
+    out = np.zeros((E, n ** 3, 3))
+    for e in range(E):
+        p = 0
+        for k in range(n):
+            for j in range(n):
+                for i in range(n):
+                    out[e, p], _ = trilinear(verts[e], r[i], r[j], r[k])
+                    p += 1
+    return out

@@ -580,3 +580,104 @@ int or_dense_element(int N, int rule, int stiff, double lambda, const double *v,
     free(val);
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Jacobi-preconditioned conjugate gradients on the unassembled        */
+/* BP3.5 screened-Poisson system (block diagonal, Section 4)           */
+/* ------------------------------------------------------------------ */
+
+/* Diagonal of the BP3.5 operator D^T G D + lambda J (Algorithm 4) in
+ * closed form: entry (p,p) sums G_ab (D_a)_{node,p} (D_b)_{node,p} over the
+ * quadrature nodes; the D_r, D_s, D_t factors touch one line each, so
+ *   diag_ijk = sum_n (D_ni^2 Grr_njk + D_nj^2 Gss_ink + D_nk^2 Gtt_ijn)
+ *            + 2 (D_ii D_jj Grs + D_ii D_kk Grt + D_jj D_kk Gst)_ijk
+ *            + lambda wJ_ijk. */
+int or_bp35_diag(int N, int64_t E, const double *geo, double lambda, double *diag)
+{
+    if (N < 1 || N > OR_MAXN) return -1;
+    int n = N + 1;
+    int64_t np = (int64_t)n * n * n;
+    double D[OR_MAXQ * OR_MAXQ];
+    or_basis(N, NULL, NULL, NULL, NULL, NULL, D, NULL);
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < E; e++) {
+        const double *g = geo + e * 7 * np;
+        for (int k = 0; k < n; k++)
+            for (int j = 0; j < n; j++)
+                for (int i = 0; i < n; i++) {
+                    int64_t p = i + n * (j + n * k);
+                    double s = 0.0;
+                    for (int m2 = 0; m2 < n; m2++) {
+                        s += D[m2 * n + i] * D[m2 * n + i] * g[0 * np + m2 + n * (j + n * k)];
+                        s += D[m2 * n + j] * D[m2 * n + j] * g[3 * np + i + n * (m2 + n * k)];
+                        s += D[m2 * n + k] * D[m2 * n + k] * g[5 * np + i + n * (j + n * m2)];
+                    }
+                    double Dii = D[i * n + i], Djj = D[j * n + j], Dkk = D[k * n + k];
+                    s += 2.0 * (Dii * Djj * g[1 * np + p] + Dii * Dkk * g[2 * np + p] +
+                                Djj * Dkk * g[4 * np + p]);
+                    s += lambda * g[6 * np + p];
+                    diag[e * np + p] = s;
+                }
+    }
+    return 0;
+}
+
+static double dot(int64_t n, const double *a, const double *b)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < n; i++) s += a[i] * b[i];
+    return s;
+}
+
+/* Jacobi-preconditioned CG (Saad, Iterative Methods for Sparse Linear
+ * Systems, 2nd ed., Algorithm 9.1, with M = diag(A)) for A x = b, A the
+ * BP3.5 operator, starting from the x passed in.  Stops when
+ * ||r||_2 <= tol ||b||_2 or after maxit iterations.  Returns the number of
+ * iterations (>= 0), -1 on bad arguments, -2 on breakdown (p.Ap <= 0);
+ * *relres receives ||r||_2 / ||b||_2 of the recursively updated residual. */
+int or_pcg_bp35(int N, int64_t E, const double *geo, double lambda, const double *b, double *x,
+                double tol, int maxit, double *relres)
+{
+    if (N < 1 || N > OR_MAXN || E < 1) return -1;
+    int64_t len = E * (int64_t)(N + 1) * (N + 1) * (N + 1);
+    double *r = malloc(sizeof(double) * len), *z = malloc(sizeof(double) * len);
+    double *p = malloc(sizeof(double) * len), *Ap = malloc(sizeof(double) * len);
+    double *dg = malloc(sizeof(double) * len);
+    int it = 0, status = 0;
+    or_bp35_diag(N, E, geo, lambda, dg);
+    or_bp35(N, E, geo, lambda, x, Ap);
+    for (int64_t i = 0; i < len; i++) r[i] = b[i] - Ap[i];
+    double bn = sqrt(dot(len, b, b));
+    if (bn == 0.0) bn = 1.0;
+    for (int64_t i = 0; i < len; i++) z[i] = r[i] / dg[i];
+    for (int64_t i = 0; i < len; i++) p[i] = z[i];
+    double rz = dot(len, r, z);
+    double rn = sqrt(dot(len, r, r));
+    while (rn > tol * bn && it < maxit) {
+        or_bp35(N, E, geo, lambda, p, Ap);
+        double pAp = dot(len, p, Ap);
+        if (!(pAp > 0.0)) {
+            status = -2;
+            break;
+        }
+        double alpha = rz / pAp;
+        for (int64_t i = 0; i < len; i++) {
+            x[i] += alpha * p[i];
+            r[i] -= alpha * Ap[i];
+        }
+        for (int64_t i = 0; i < len; i++) z[i] = r[i] / dg[i];
+        double rz_new = dot(len, r, z);
+        double beta = rz_new / rz;
+        rz = rz_new;
+        for (int64_t i = 0; i < len; i++) p[i] = z[i] + beta * p[i];
+        rn = sqrt(dot(len, r, r));
+        it++;
+    }
+    if (relres) *relres = rn / bn;
+    free(r);
+    free(z);
+    free(p);
+    free(Ap);
+    free(dg);
+    return status ? status : it;
+}
