@@ -137,6 +137,85 @@ int fem_bp35_apply(const fem_basis *b, int64_t E, const double *G, double lambda
 int fem_bp30_apply(const fem_basis *b, int64_t E, const double *G, double lambda,
                    const double *q, double *Aq, void *stream);
 
+/* BP3.5 matvec in FP32 (the inner operator of the mixed-precision solver;
+ * same layouts as fem_bp35_apply with float data; FP32 arithmetic).
+ * Errors: FEM_EINVAL, FEM_ECUDA. */
+int fem_bp35_apply_f32(const fem_basis *b, int64_t E, const float *G, double lambda,
+                       const float *q, float *Aq, void *stream);
+
+/* Inverse of the diagonal of the BP3.5 operator D^T G D + lambda J (the
+ * Jacobi preconditioner), in closed form:
+ *   diag_ijk = sum_l (D_li^2 Grr_ljk + D_lj^2 Gss_ilk + D_lk^2 Gtt_ijl)
+ *            + 2 (D_ii D_jj Grs + D_ii D_kk Grt + D_jj D_kk Gst)_ijk + lambda wJ_ijk.
+ *   G device E*7*Np, dinv device E*Np (1/diag).  Errors: FEM_EINVAL, FEM_ECUDA. */
+int fem_bp35_jacobi(const fem_basis *b, int64_t E, const double *G, double lambda,
+                    double *dinv, void *stream);
+
+/* Deterministic FP64 dot product of two device vectors of n doubles: the
+ * result is written to *result (device); scratch is a caller-owned device
+ * array of at least fem_dot_scratch_size() doubles (its contents are
+ * overwritten).  Two calls with the same inputs give the same bits.
+ * Asynchronous on stream.  Errors: FEM_EINVAL, FEM_ECUDA. */
+int64_t fem_dot_scratch_size(void);
+int fem_dot(int64_t n, const double *x, const double *y, double *result, double *scratch,
+            void *stream);
+
+/* ---------------------------------------------------------------------
+ * Jacobi-preconditioned conjugate gradients for the unassembled BP3.5
+ * Helmholtz system (D^T G D + lambda J) x = rhs (Section 4; the solver is
+ * the textbook PCG with M = diag A).  Two modes:
+ *   FEM_PCG_FP64   all-FP64 PCG;
+ *   FEM_PCG_MIXED  FP64 defect correction: the residual rhs - A x, its norm
+ *                  and the update of x in FP64; each correction A d = r
+ *                  solved to inner_tol by an FP32 PCG (FP32 factors, FP32
+ *                  matvec, FP64 dot products).
+ * A solver context owns its device workspace (about 5 vectors in FP64
+ * mode; 7 FP32 factor planes and 6 FP32 + 1 FP64 vectors in mixed mode).
+ * --------------------------------------------------------------------- */
+#define FEM_EBREAKDOWN (-5) /* p.Ap <= 0 or a non-finite value in the recurrence */
+#define FEM_ENOCONV (-6)    /* iteration limit reached; x holds the last iterate */
+
+#define FEM_PCG_FP64 0
+#define FEM_PCG_MIXED 1
+
+typedef struct fem_pcg fem_pcg; /* opaque */
+
+typedef struct {
+    double tol;       /* stop when ||rhs - A x||_2 <= tol ||rhs||_2 (default 1e-10) */
+    int maxit;        /* iteration limit (default 100000)                          */
+    double inner_tol; /* mixed: relative tolerance of each FP32 solve (1e-4)       */
+    int inner_maxit;  /* mixed: iteration limit of each FP32 solve (100000)        */
+    int check_every;  /* host convergence check period (8 FP64, 16 FP32)           */
+} fem_pcg_opts;
+
+typedef struct {
+    int iters;     /* PCG iterations (FP32 inner iterations in mixed mode) */
+    int outer;     /* defect-correction steps (1 in FP64 mode)             */
+    double relres; /* ||rhs - A x||_2 / ||rhs||_2 of the returned x, FP64  */
+} fem_pcg_info;
+
+/* Creates a solver for E elements of the handle's degree with operator
+ * factors G (device, E*7*Np FP64, must stay valid for the context's life)
+ * and lambda >= 0; computes the Jacobi diagonal and, in mixed mode, the
+ * FP32 copy of G.  Allocates device memory; synchronous.
+ * Errors: FEM_EINVAL, FEM_ENOMEM, FEM_ECUDA. */
+int fem_pcg_create(const fem_basis *b, int64_t E, const double *G, double lambda, int mode,
+                   fem_pcg **out);
+
+/* Solves A x = rhs starting from the x passed in (device, E*Np doubles;
+ * rhs device, not aliasing x).  opts may be NULL (defaults above); info
+ * may be NULL.  Runs on stream and returns after the solve has finished
+ * (host convergence checks every check_every iterations; all scalars of
+ * the recurrence stay on the device).  The iterate is frozen on the device
+ * at the first iteration that meets the tolerance, so the result does not
+ * depend on check_every.  Returns FEM_OK, FEM_ENOCONV, FEM_EBREAKDOWN,
+ * FEM_EINVAL or FEM_ECUDA. */
+int fem_pcg_solve(fem_pcg *s, const double *rhs, double *x, const fem_pcg_opts *opts,
+                  fem_pcg_info *info, void *stream);
+
+/* Frees a solver (NULL accepted).  Synchronous. */
+void fem_pcg_destroy(fem_pcg *s);
+
 /* Static name of an error code. */
 const char *fem_strerror(int code);
 

@@ -20,15 +20,29 @@ __all__ = [
     "FemError", "lib", "Basis", "fem_version", "fem_basis_setup", "fem_basis_free",
     "fem_basis_tables", "fem_basis_host_tables", "fem_mesh_geofacs", "fem_bp1_apply",
     "fem_bp35_apply", "fem_bp30_apply", "FEM_GEO_BP1", "FEM_GEO_BP35", "FEM_GEO_BP30",
-    "geo_shape",
+    "geo_shape", "fem_bp35_apply_f32", "fem_bp35_jacobi", "fem_dot", "fem_dot_scratch_size", "Pcg",
+    "fem_pcg_create", "fem_pcg_solve", "fem_pcg_destroy", "FEM_PCG_FP64", "FEM_PCG_MIXED",
 ]
 
 FEM_OK, FEM_EINVAL, FEM_ECUDA, FEM_ENOMEM, FEM_ENODEV = 0, -1, -2, -3, -4
+FEM_EBREAKDOWN, FEM_ENOCONV = -5, -6
+FEM_PCG_FP64, FEM_PCG_MIXED = 0, 1
 FEM_GEO_BP1, FEM_GEO_BP35, FEM_GEO_BP30 = 1, 2, 3
 MAX_N = 15
 
 _lock = threading.Lock()
 _lib = None
+
+
+class PcgOpts(C.Structure):
+    """fem_pcg_opts (include/fem.h)."""
+    _fields_ = [("tol", C.c_double), ("maxit", C.c_int), ("inner_tol", C.c_double),
+                ("inner_maxit", C.c_int), ("check_every", C.c_int)]
+
+
+class PcgInfo(C.Structure):
+    """fem_pcg_info (include/fem.h)."""
+    _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("relres", C.c_double)]
 
 
 class FemError(RuntimeError):
@@ -62,9 +76,18 @@ def lib():
             L.fem_bp1_apply.argtypes = [vp, i64, dp, dp, dp, vp]
             L.fem_bp35_apply.argtypes = [vp, i64, dp, dbl, dp, dp, vp]
             L.fem_bp30_apply.argtypes = [vp, i64, dp, dbl, dp, dp, vp]
+            L.fem_bp35_apply_f32.argtypes = [vp, i64, dp, dbl, dp, dp, vp]
+            L.fem_bp35_jacobi.argtypes = [vp, i64, dp, dbl, dp, vp]
+            L.fem_dot_scratch_size.restype = i64
+            L.fem_dot.argtypes = [i64, dp, dp, dp, dp, vp]
+            L.fem_pcg_create.argtypes = [vp, i64, dp, dbl, i32, C.POINTER(vp)]
+            L.fem_pcg_solve.argtypes = [vp, dp, dp, C.POINTER(PcgOpts), C.POINTER(PcgInfo), vp]
+            L.fem_pcg_destroy.argtypes = [vp]
+            L.fem_pcg_destroy.restype = None
             for f in ("fem_basis_setup", "fem_basis_tables", "fem_basis_host_tables",
                       "fem_mesh_geofacs", "fem_bp1_apply", "fem_bp35_apply", "fem_bp30_apply",
-                      "fem_basis_degree"):
+                      "fem_basis_degree", "fem_bp35_apply_f32", "fem_bp35_jacobi", "fem_dot",
+                      "fem_pcg_create", "fem_pcg_solve"):
                 getattr(L, f).restype = i32
             _lib = L
     return _lib
@@ -212,3 +235,122 @@ def fem_bp30_apply(b: Basis, G, lam: float, q, out=None, stream=None):
     _check(lib().fem_bp30_apply(b.handle, E, G.data_ptr(), float(lam), q.data_ptr(), out.data_ptr(),
                                 _stream(stream, q.device)), "fem_bp30_apply")
     return out
+
+
+def _dev32(t, name, numel=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+        raise TypeError(f"{name} must be a CUDA float32 tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} has {t.numel()} entries, expected {numel}")
+    return t.data_ptr()
+
+
+def fem_bp35_apply_f32(b: Basis, G, lam: float, q, out=None, stream=None):
+    """BP3.5 matvec in FP32 (FP32 factors and field)."""
+    import torch
+    E = q.shape[0]
+    _dev32(q, "q", E * b.n ** 3)
+    _dev32(G, "G", E * 7 * b.n ** 3)
+    if out is None:
+        out = torch.empty_like(q)
+    _dev32(out, "out", E * b.n ** 3)
+    _check(lib().fem_bp35_apply_f32(b.handle, E, G.data_ptr(), float(lam), q.data_ptr(), out.data_ptr(),
+                                    _stream(stream, q.device)), "fem_bp35_apply_f32")
+    return out
+
+
+def fem_bp35_jacobi(b: Basis, G, lam: float, out=None, stream=None):
+    """Inverse diagonal of the BP3.5 operator (Jacobi preconditioner)."""
+    import torch
+    E = G.shape[0]
+    _dev(G, "G", E * 7 * b.n ** 3)
+    if out is None:
+        out = torch.empty((E, b.n ** 3), dtype=torch.float64, device=G.device)
+    _dev(out, "dinv", E * b.n ** 3)
+    _check(lib().fem_bp35_jacobi(b.handle, E, G.data_ptr(), float(lam), out.data_ptr(),
+                                 _stream(stream, G.device)), "fem_bp35_jacobi")
+    return out
+
+
+def fem_dot_scratch_size() -> int:
+    return int(lib().fem_dot_scratch_size())
+
+
+def fem_dot(x, y, result=None, scratch=None, stream=None):
+    """Deterministic FP64 dot product of two device vectors; returns the
+    one-element device tensor holding it."""
+    import torch
+    n = x.numel()
+    _dev(x, "x")
+    _dev(y, "y", n)
+    if result is None:
+        result = torch.empty(1, dtype=torch.float64, device=x.device)
+    if scratch is None:
+        scratch = torch.empty(fem_dot_scratch_size(), dtype=torch.float64, device=x.device)
+    _dev(result, "result")
+    _dev(scratch, "scratch")
+    if scratch.numel() < fem_dot_scratch_size():
+        raise ValueError("scratch too small")
+    _check(lib().fem_dot(n, x.data_ptr(), y.data_ptr(), result.data_ptr(), scratch.data_ptr(),
+                         _stream(stream, x.device)), "fem_dot")
+    return result
+
+
+class Pcg:
+    """Owning wrapper of a fem_pcg solver context."""
+
+    def __init__(self, handle: int, basis: Basis, E: int, G):
+        self.handle = C.c_void_p(handle)
+        self.basis, self.E, self.G = basis, E, G  # keep G alive with the context
+
+    def solve(self, rhs, x=None, tol=1e-10, maxit=0, inner_tol=0.0, inner_maxit=0, check_every=0,
+              stream=None, raise_on_error=True):
+        return fem_pcg_solve(self, rhs, x, tol, maxit, inner_tol, inner_maxit, check_every, stream,
+                             raise_on_error)
+
+    def free(self):
+        if self.handle and self.handle.value:
+            lib().fem_pcg_destroy(self.handle)
+            self.handle = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def fem_pcg_create(b: Basis, G, lam: float, mode: int = FEM_PCG_FP64) -> Pcg:
+    """Jacobi-PCG solver context for the BP3.5 system with factors G."""
+    E = G.shape[0]
+    _dev(G, "G", E * 7 * b.n ** 3)
+    h = C.c_void_p()
+    _check(lib().fem_pcg_create(b.handle, E, G.data_ptr(), float(lam), int(mode), C.byref(h)),
+           "fem_pcg_create")
+    return Pcg(h.value, b, E, G)
+
+
+def fem_pcg_solve(s: Pcg, rhs, x=None, tol=1e-10, maxit=0, inner_tol=0.0, inner_maxit=0,
+                  check_every=0, stream=None, raise_on_error=True):
+    """Solves A x = rhs from the x passed in (zeros when None).  Returns
+    (x, info dict, status code)."""
+    import torch
+    n = s.E * s.basis.n ** 3
+    _dev(rhs, "rhs", n)
+    if x is None:
+        x = torch.zeros_like(rhs)
+    _dev(x, "x", n)
+    opts = PcgOpts(float(tol), int(maxit), float(inner_tol), int(inner_maxit), int(check_every))
+    info = PcgInfo()
+    code = lib().fem_pcg_solve(s.handle, rhs.data_ptr(), x.data_ptr(), C.byref(opts), C.byref(info),
+                               _stream(stream, rhs.device))
+    if raise_on_error and code not in (FEM_OK,):
+        raise FemError(code, "fem_pcg_solve")
+    return x, {"iters": info.iters, "outer": info.outer, "relres": info.relres}, code
+
+
+def fem_pcg_destroy(s: Pcg):
+    s.free()

@@ -45,6 +45,10 @@ int check_apply(const fem_basis *b, int64_t E, const double *geo, int64_t geo_pe
 
 }  // namespace
 
+namespace fem {
+int record_cuda_error(cudaError_t e) { return cuda_fail(e); }
+}  // namespace fem
+
 extern "C" {
 
 int fem_version(void) { return 1 * 10000 + 0 * 100 + 0; }
@@ -56,6 +60,8 @@ const char *fem_strerror(int code) {
         case FEM_ECUDA: return "FEM_ECUDA: CUDA runtime or launch error";
         case FEM_ENOMEM: return "FEM_ENOMEM: allocation failed";
         case FEM_ENODEV: return "FEM_ENODEV: no usable CUDA device";
+        case FEM_EBREAKDOWN: return "FEM_EBREAKDOWN: conjugate-gradient breakdown";
+        case FEM_ENOCONV: return "FEM_ENOCONV: iteration limit reached";
         default: return "unknown fem error code";
     }
 }
@@ -170,6 +176,18 @@ int fem_bp35_apply(const fem_basis *b, int64_t E, const double *G, double lambda
     const int c = check_apply(b, E, G, b ? 7 * cube(b->host.n) : 0, q, Aq);
     if (c != FEM_OK || E == 0) return c;
     cudaError_t e = fem::launch_bp35(b, E, G, lambda, q, Aq, (cudaStream_t)stream);
+    return e == cudaSuccess ? FEM_OK : cuda_fail(e);
+}
+
+int fem_bp35_apply_f32(const fem_basis *b, int64_t E, const float *G, double lambda, const float *q, float *Aq,
+                       void *stream) {
+    if (!b || E < 0) return FEM_EINVAL;
+    if (E == 0) return FEM_OK;
+    if (!G || !q || !Aq || !aligned16(G) || !aligned16(q) || !aligned16(Aq)) return FEM_EINVAL;
+    const int64_t np = cube(b->host.n);
+    if ((const void *)Aq == (const void *)q || (E + 1) > (int64_t)0x7fffffff) return FEM_EINVAL;
+    (void)np;
+    cudaError_t e = fem::launch_bp35_f32(b, E, G, lambda, q, Aq, (cudaStream_t)stream);
     return e == cudaSuccess ? FEM_OK : cuda_fail(e);
 }
 

@@ -26,17 +26,30 @@ namespace fem {
 
 // ------------------------------------------------------------ device side
 
-// One constant table per translation unit (no relocatable device code);
-// every TU that uses it uploads the same contents at basis setup.
+// One constant table per translation unit and precision (no relocatable
+// device code); every TU that uses them uploads the same contents at basis
+// setup.
 static __constant__ double c_fold[kFoldTotal];
+static __constant__ float c_fold32[kFoldTotal];
 
-// y (P) = A x (Q) along one line, A folded at table offset OFF, parity SIG.
-template <int P, int Q, int SIG, int OFF>
-__device__ __forceinline__ void eo_apply(const double (&x)[Q], double (&y)[P]) {
+template <typename T>
+__device__ __forceinline__ T fold_at(int i);
+template <>
+__device__ __forceinline__ double fold_at<double>(int i) { return c_fold[i]; }
+template <>
+__device__ __forceinline__ float fold_at<float>(int i) { return c_fold32[i]; }
+
+__device__ __forceinline__ double fmx(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmx(float a, float b, float c) { return fmaf(a, b, c); }
+
+// y (P) = A x (Q) along one line, A folded at table offset OFF, parity SIG,
+// in the precision T of the data.
+template <int P, int Q, int SIG, int OFF, typename T>
+__device__ __forceinline__ void eo_apply(const T (&x)[Q], T (&y)[P]) {
     constexpr int hp = P / 2, hq = Q / 2;
     constexpr int oS = OFF, oT = OFF + hp * hq, oC = OFF + 2 * hp * hq;
     constexpr int oR = oC + ((Q % 2) ? hp : 0);
-    double e[hq > 0 ? hq : 1], o[hq > 0 ? hq : 1];
+    T e[hq > 0 ? hq : 1], o[hq > 0 ? hq : 1];
 #pragma unroll
     for (int i = 0; i < hq; i++) {
         e[i] = x[i] + x[Q - 1 - i];
@@ -44,21 +57,21 @@ __device__ __forceinline__ void eo_apply(const double (&x)[Q], double (&y)[P]) {
     }
 #pragma unroll
     for (int a = 0; a < hp; a++) {
-        double E = 0.0, O = 0.0;
+        T E = T(0), O = T(0);
 #pragma unroll
         for (int i = 0; i < hq; i++) {
-            E = fma(c_fold[oS + a * hq + i], e[i], E);
-            O = fma(c_fold[oT + a * hq + i], o[i], O);
+            E = fmx(fold_at<T>(oS + a * hq + i), e[i], E);
+            O = fmx(fold_at<T>(oT + a * hq + i), o[i], O);
         }
-        if (Q % 2) E = fma(c_fold[oC + a], x[hq], E);
+        if (Q % 2) E = fmx(fold_at<T>(oC + a), x[hq], E);
         y[a] = E + O;
         y[P - 1 - a] = (SIG > 0) ? (E - O) : (O - E);
     }
     if (P % 2) {
-        double M = 0.0;
+        T M = T(0);
 #pragma unroll
-        for (int i = 0; i < hq; i++) M = fma(c_fold[oR + i], (SIG > 0) ? e[i] : o[i], M);
-        if ((Q % 2) && SIG > 0) M = fma(c_fold[oR + hq], x[hq], M);
+        for (int i = 0; i < hq; i++) M = fmx(fold_at<T>(oR + i), (SIG > 0) ? e[i] : o[i], M);
+        if ((Q % 2) && SIG > 0) M = fmx(fold_at<T>(oR + hq), x[hq], M);
         y[hp] = M;
     }
 }
@@ -83,10 +96,16 @@ __device__ __forceinline__ void for_tasks(int nel, F &&f) {
     }
 }
 
-// Host: uploads the folded table (kFoldTotal doubles) to this TU's copy.
+// Host: uploads the folded table (kFoldTotal doubles) to this TU's copies
+// (the FP32 copy rounded from it).
 #define FEM_DEFINE_FOLD_UPLOAD(NAME)                                                     \
     cudaError_t NAME(const double *table) {                                              \
-        return cudaMemcpyToSymbol(c_fold, table, sizeof(double) * kFoldTotal, 0,         \
+        static float t32[kFoldTotal];                                                    \
+        for (int i = 0; i < kFoldTotal; i++) t32[i] = (float)table[i];                   \
+        cudaError_t e = cudaMemcpyToSymbol(c_fold, table, sizeof(double) * kFoldTotal, 0, \
+                                           cudaMemcpyHostToDevice);                      \
+        if (e != cudaSuccess) return e;                                                  \
+        return cudaMemcpyToSymbol(c_fold32, t32, sizeof(float) * kFoldTotal, 0,         \
                                   cudaMemcpyHostToDevice);                               \
     }
 

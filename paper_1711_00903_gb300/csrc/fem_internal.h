@@ -69,4 +69,20 @@ cudaError_t prepare_geofacs(int N);
 // Host copy of the folded operator table of all degrees 1..15 (built once).
 const double *fold_table();
 
+// Records the text of a CUDA error for fem_last_cuda_error() and maps it to
+// FEM_ECUDA or FEM_ENODEV.
+int record_cuda_error(cudaError_t e);
+
+// FP32 BP3.5 matvec (the inner operator of the mixed-precision solver).
+cudaError_t launch_bp35_f32(const fem_basis *b, int64_t E, const float *G, double lambda, const float *q,
+                            float *Aq, cudaStream_t s);
+cudaError_t launch_dot(int64_t n, const double *x, const double *y, double *result, double *scratch,
+                       cudaStream_t s);
+int64_t dot_scratch_size();
+
+// PCG solver internals (pcg.cu)
+cudaError_t pcg_create(fem_pcg *s);
+void pcg_release(fem_pcg *s);
+int pcg_solve(fem_pcg *s, const double *b, double *x, const fem_pcg_opts *o, fem_pcg_info *info, cudaStream_t st);
+
 }  // namespace fem

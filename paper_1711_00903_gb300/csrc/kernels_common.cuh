@@ -26,6 +26,24 @@ __device__ __forceinline__ void block_copy(double *dst, const double *__restrict
     for (int t = threadIdx.x; t < count; t += blockDim.x) dst[t] = __ldg(src + t);
 }
 
+// Sum of v over the block (blockDim.x a multiple of 32), in a fixed order so
+// that repeated runs give identical bits; the result is valid in thread 0.
+// sh: at least 32 doubles of shared memory not in use by other threads.
+// Every thread of the block must call it.
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    v = (threadIdx.x < (unsigned)nw) ? sh[threadIdx.x] : 0.0;
+    if (w == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;
+}
+
 // Dispatch of a functor templated on the degree N (1..15) at run time.
 template <template <int> class F, typename... Args>
 cudaError_t dispatch_degree(int N, Args &&...args) {

@@ -1,0 +1,546 @@
+// Jacobi-preconditioned conjugate gradients (Saad, "Iterative Methods for
+// Sparse Linear Systems", Algorithm 9.1, M = diag A) for the unassembled
+// BP3.5 screened-Poisson system S u + lambda M u = f of Section 4, in two
+// modes:
+//   FP64   all-FP64 PCG;
+//   mixed  FP64 defect correction (iterative refinement): the residual
+//          b - A x, its norm, the dot products and the solution update stay
+//          in FP64, while each correction equation A d = r is solved to a
+//          loose tolerance by an FP32 PCG whose matvec reads FP32 geometric
+//          factors.
+//
+// Device-resident state: every scalar of the recurrence (rho, p.Ap, alpha,
+// beta, ||r||^2, convergence and breakdown flags, the iteration count) lives
+// in device memory and is produced by deterministic single-block
+// reductions, so the host reads back a few scalars only every few
+// iterations.  One iteration is four launches: the BP3.5 matvec fused with
+// p <- z + beta p and the p.Ap partial sums, a reduction, the fused update
+// x += alpha p, r -= alpha Ap, z = r / diag with the r.z and r.r partial
+// sums, and a reduction.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "fem_internal.h"
+#include "kernels_common.cuh"
+
+namespace fem {
+
+enum {
+    S_RHO = 0,   // r . z of the current iterate
+    S_PQ,        // p . Ap
+    S_ALPHA,
+    S_BETA,
+    S_RR,        // r . r (of the solver in progress)
+    S_BB,        // b . b
+    S_TOL2,      // squared absolute stopping threshold on r . r
+    S_DONE,      // 1 once r . r <= S_TOL2 (further iterations are frozen)
+    S_BREAK,     // 1 on p . Ap <= 0 or a non-finite value
+    S_ITER,      // iterations completed
+    S_RR_OUTER,  // FP64 residual norm^2 of the defect-correction loop
+    S_COUNT
+};
+
+constexpr int kVecBlocks = 152 * 8;  // grid of the vector kernels (grid-stride)
+constexpr int kVecThreads = 256;
+constexpr int kRedThreads = 1024;
+
+namespace {
+
+// ------------------------------------------------------------------ kernels
+
+template <int N>
+__global__ void __launch_bounds__(256)
+bp35_dinv_kernel(int64_t E, const double *__restrict__ ops, const double *__restrict__ G, double lambda,
+                 double *__restrict__ dinv, float *__restrict__ dinv32) {
+    constexpr int n = N + 1, NP = n * n * n;
+    __shared__ double sD[n * n];
+    const OpsLayout L{n, n + 1};
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) sD[t] = ops[L.offD() + t];
+    __syncthreads();
+    const int64_t total = E * NP;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = g / NP;
+        const int p = (int)(g - e * NP), i = p % n, j = (p / n) % n, k = p / (n * n);
+        const double *Ge = G + e * 7 * NP;
+        double s = 0.0;
+#pragma unroll
+        for (int l = 0; l < n; l++) {
+            const double a = sD[l * n + i], b = sD[l * n + j], c = sD[l * n + k];
+            s = fma(a * a, Ge[0 * NP + l + n * (j + n * k)], s);
+            s = fma(b * b, Ge[3 * NP + i + n * (l + n * k)], s);
+            s = fma(c * c, Ge[5 * NP + i + n * (j + n * l)], s);
+        }
+        const double Di = sD[i * n + i], Dj = sD[j * n + j], Dk = sD[k * n + k];
+        s += 2.0 * (Di * Dj * Ge[1 * NP + p] + Di * Dk * Ge[2 * NP + p] + Dj * Dk * Ge[4 * NP + p]);
+        s += lambda * Ge[6 * NP + p];
+        const double v = 1.0 / s;
+        if (dinv) dinv[g] = v;
+        if (dinv32) dinv32[g] = (float)v;
+    }
+}
+
+__global__ void __launch_bounds__(kVecThreads) cast_f32_kernel(int64_t n, const double *__restrict__ a,
+                                                               float *__restrict__ b) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+// partial sums of x . y per block (grid-stride, fixed order)
+__global__ void __launch_bounds__(kVecThreads) dot_kernel(int64_t n, const double *__restrict__ x,
+                                                          const double *__restrict__ y, double *__restrict__ part) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s = fma(x[i], y[i], s);
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// FP64 PCG start: r = b - Ax, z = dinv r; partials (r.z, r.r)
+__global__ void __launch_bounds__(kVecThreads)
+init_kernel(int64_t n, const double *__restrict__ b, const double *__restrict__ Ax, double *__restrict__ r,
+            double *__restrict__ z, const double *__restrict__ dinv, double *__restrict__ part) {
+    __shared__ double sh[32];
+    double rz = 0.0, rr = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double ri = b[i] - Ax[i], zi = dinv[i] * ri;
+        r[i] = ri;
+        z[i] = zi;
+        rz = fma(ri, zi, rz);
+        rr = fma(ri, ri, rr);
+    }
+    rz = block_sum(rz, sh);
+    __syncthreads();
+    rr = block_sum(rr, sh);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = rz;
+        part[2 * blockIdx.x + 1] = rr;
+    }
+}
+
+// Defect-correction step: r64 = b - Ax (FP64), r = (float) r64, z = dinv r,
+// d = 0; partials (r.z, r.r, r64.r64)
+__global__ void __launch_bounds__(kVecThreads)
+outer_kernel(int64_t n, const double *__restrict__ b, const double *__restrict__ Ax, float *__restrict__ r,
+             float *__restrict__ z, float *__restrict__ d, const float *__restrict__ dinv, double *__restrict__ part) {
+    __shared__ double sh[32];
+    double rz = 0.0, rr = 0.0, r64 = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double ri = b[i] - Ax[i];
+        const float rf = (float)ri, zf = dinv[i] * rf;
+        r[i] = rf;
+        z[i] = zf;
+        d[i] = 0.0f;
+        rz = fma((double)rf, (double)zf, rz);
+        rr = fma((double)rf, (double)rf, rr);
+        r64 = fma(ri, ri, r64);
+    }
+    rz = block_sum(rz, sh);
+    __syncthreads();
+    rr = block_sum(rr, sh);
+    __syncthreads();
+    r64 = block_sum(r64, sh);
+    if (threadIdx.x == 0) {
+        part[3 * blockIdx.x] = rz;
+        part[3 * blockIdx.x + 1] = rr;
+        part[3 * blockIdx.x + 2] = r64;
+    }
+}
+
+// x += alpha p, r -= alpha Ap, z = dinv r; partials (r.z, r.r)
+template <typename T, typename XT>
+__global__ void __launch_bounds__(kVecThreads)
+update_kernel(int64_t n, const double *__restrict__ scal, XT *__restrict__ x, const T *__restrict__ p,
+              T *__restrict__ r, const T *__restrict__ Ap, T *__restrict__ z, const T *__restrict__ dinv,
+              double *__restrict__ part) {
+    __shared__ double sh[32];
+    const double alpha = scal[S_ALPHA];
+    const T a = (T)alpha;
+    double rz = 0.0, rr = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T ri = r[i];
+        if (alpha != 0.0) {
+            x[i] = (XT)fma((double)alpha, (double)p[i], (double)x[i]);
+            ri = ri - a * Ap[i];
+            r[i] = ri;
+        }
+        const T zi = dinv[i] * ri;
+        z[i] = zi;
+        rz = fma((double)ri, (double)zi, rz);
+        rr = fma((double)ri, (double)ri, rr);
+    }
+    rz = block_sum(rz, sh);
+    __syncthreads();
+    rr = block_sum(rr, sh);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = rz;
+        part[2 * blockIdx.x + 1] = rr;
+    }
+}
+
+// x (FP64) += d (FP32)
+__global__ void __launch_bounds__(kVecThreads) add_f32_kernel(int64_t n, double *__restrict__ x,
+                                                              const float *__restrict__ d) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += (double)d[i];
+}
+
+enum RedMode { R_SUM = 0, R_PQ, R_RZ, R_INIT, R_OUTER, R_TRUE };
+
+// Single-block reduction of `nparts` records of `stride` partial sums and
+// the scalar logic of the recurrence.
+__global__ void __launch_bounds__(kRedThreads)
+reduce_kernel(int mode, int64_t nparts, const double *__restrict__ part, double *__restrict__ scal,
+              double *__restrict__ out, double tol2_rel) {
+    __shared__ double sh[32];
+    const int stride = (mode == R_OUTER) ? 3 : (mode == R_RZ || mode == R_INIT || mode == R_TRUE) ? 2 : 1;
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int64_t i = threadIdx.x; i < nparts; i += blockDim.x)
+        for (int c = 0; c < stride; c++) acc[c] += part[i * stride + c];
+    double tot[3];
+    for (int c = 0; c < stride; c++) {
+        tot[c] = block_sum(acc[c], sh);
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    if (mode == R_SUM) {
+        *out = tot[0];
+    } else if (mode == R_TRUE) {  // residual norm of a finished solve
+        scal[S_RR] = tot[1];
+    } else if (mode == R_PQ) {
+        const double pq = tot[0];
+        scal[S_PQ] = pq;
+        double alpha = 0.0;
+        if (scal[S_DONE] == 0.0 && scal[S_BREAK] == 0.0) {
+            if (pq > 0.0 && isfinite(pq))
+                alpha = scal[S_RHO] / pq;
+            else
+                scal[S_BREAK] = 1.0;
+        }
+        scal[S_ALPHA] = alpha;
+    } else if (mode == R_RZ) {
+        const bool active = scal[S_DONE] == 0.0 && scal[S_BREAK] == 0.0;
+        const double rz = tot[0], rr = tot[1];
+        scal[S_BETA] = (scal[S_RHO] != 0.0) ? rz / scal[S_RHO] : 0.0;
+        scal[S_RHO] = rz;
+        scal[S_RR] = rr;
+        if (active) {
+            scal[S_ITER] += 1.0;
+            if (!isfinite(rr))
+                scal[S_BREAK] = 1.0;
+            else if (rr <= scal[S_TOL2])
+                scal[S_DONE] = 1.0;
+        }
+    } else {  // R_INIT, R_OUTER: start of a PCG run
+        scal[S_RHO] = tot[0];
+        scal[S_RR] = tot[1];
+        scal[S_BETA] = 0.0;
+        scal[S_ITER] = 0.0;
+        scal[S_BREAK] = 0.0;
+        scal[S_TOL2] = tol2_rel * (mode == R_INIT ? scal[S_BB] : tot[1]);
+        scal[S_DONE] = (tot[1] <= scal[S_TOL2]) ? 1.0 : 0.0;
+        if (mode == R_OUTER) scal[S_RR_OUTER] = tot[2];
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers used by the ABI
+
+template <int N>
+struct DinvLaunch {
+    static cudaError_t run(const fem_basis *b, int64_t E, const double *G, double lambda, double *dinv, float *dinv32,
+                           cudaStream_t s) {
+        const int64_t total = E * (int64_t)(N + 1) * (N + 1) * (N + 1);
+        int64_t blocks = (total + 255) / 256;
+        if (blocks > 152 * 32) blocks = 152 * 32;
+        bp35_dinv_kernel<N><<<(unsigned)blocks, 256, 0, s>>>(E, b->d_ops, G, lambda, dinv, dinv32);
+        return cudaGetLastError();
+    }
+};
+
+int64_t dot_scratch_size() { return kVecBlocks; }
+
+cudaError_t launch_dot(int64_t n, const double *x, const double *y, double *result, double *scratch,
+                       cudaStream_t s) {
+    dot_kernel<<<kVecBlocks, kVecThreads, 0, s>>>(n, x, y, scratch);
+    reduce_kernel<<<1, kRedThreads, 0, s>>>(R_SUM, kVecBlocks, scratch, nullptr, result, 0.0);
+    return cudaGetLastError();
+}
+
+}  // namespace fem
+
+// ---------------------------------------------------------------------- solver context
+
+struct fem_pcg {
+    const fem_basis *basis;
+    int64_t E, len;
+    const double *G;
+    double lambda;
+    int mode;
+    int device;
+    double *r, *z, *p, *q, *dinv;                   // FP64 recurrence (q also holds A x)
+    float *G32, *dinv32, *d32, *r32, *z32, *p32, *q32;  // FP32 inner recurrence (mixed mode)
+    double *part;
+    int64_t nparts;
+    double *scal;   // device scalars
+    double *hscal;  // pinned host copy
+};
+
+namespace fem {
+
+cudaError_t launch_bp35_pcg(const fem_basis *b, int64_t E, const double *G, double lambda, const double *z,
+                            double *p, const double *beta, double *Ap, double *partials, cudaStream_t s);
+cudaError_t launch_bp35_pcg_f32(const fem_basis *b, int64_t E, const float *G, double lambda, const float *z,
+                                float *p, const double *beta, float *Ap, double *partials, cudaStream_t s);
+int64_t bp35_max_blocks(int N, int64_t E);
+int64_t bp35_blocks(int N, int64_t E, bool f32);
+cudaError_t launch_bp35(const fem_basis *b, int64_t E, const double *G, double lambda, const double *q, double *Aq,
+                        cudaStream_t s);
+
+namespace {
+
+template <typename P>
+cudaError_t alloc(P **ptr, int64_t count) {
+    return cudaMalloc((void **)ptr, sizeof(P) * (size_t)(count > 0 ? count : 1));
+}
+
+cudaError_t sync_scalars(fem_pcg *s, cudaStream_t st) {
+    cudaError_t e = cudaMemcpyAsync(s->hscal, s->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e;
+}
+
+}  // namespace
+
+cudaError_t pcg_create(fem_pcg *s) {
+    cudaError_t e = cudaSuccess;
+    const int64_t len = s->len;
+    s->nparts = bp35_max_blocks(s->basis->host.N, s->E);
+    if (s->nparts < 3 * (int64_t)kVecBlocks) s->nparts = 3 * (int64_t)kVecBlocks;
+    if (e == cudaSuccess) e = alloc(&s->part, 3 * s->nparts);
+    if (e == cudaSuccess) e = alloc(&s->scal, S_COUNT);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&s->hscal, sizeof(double) * S_COUNT);
+    if (e == cudaSuccess) e = alloc(&s->q, len);
+    if (s->mode == FEM_PCG_FP64) {
+        if (e == cudaSuccess) e = alloc(&s->r, len);
+        if (e == cudaSuccess) e = alloc(&s->z, len);
+        if (e == cudaSuccess) e = alloc(&s->p, len);
+        if (e == cudaSuccess) e = alloc(&s->dinv, len);
+    } else {
+        if (e == cudaSuccess) e = alloc(&s->G32, 7 * len);
+        if (e == cudaSuccess) e = alloc(&s->dinv32, len);
+        if (e == cudaSuccess) e = alloc(&s->d32, len);
+        if (e == cudaSuccess) e = alloc(&s->r32, len);
+        if (e == cudaSuccess) e = alloc(&s->z32, len);
+        if (e == cudaSuccess) e = alloc(&s->p32, len);
+        if (e == cudaSuccess) e = alloc(&s->q32, len);
+    }
+    if (e != cudaSuccess) return e;
+    e = cudaMemset(s->scal, 0, sizeof(double) * S_COUNT);
+    if (e != cudaSuccess) return e;
+    e = dispatch_degree<DinvLaunch>(s->basis->host.N, s->basis, s->E, s->G, s->lambda, s->dinv, s->dinv32,
+                                    (cudaStream_t)0);
+    if (e == cudaSuccess && s->mode != FEM_PCG_FP64)
+        cast_f32_kernel<<<kVecBlocks, kVecThreads>>>(7 * len, s->G, s->G32);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    return e;
+}
+
+void pcg_release(fem_pcg *s) {
+    void *bufs[] = {s->r,   s->z,   s->p,   s->q,   s->dinv, s->G32, s->dinv32,
+                    s->d32, s->r32, s->z32, s->p32, s->q32,  s->part, s->scal};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    if (s->hscal) cudaFreeHost(s->hscal);
+}
+
+// Runs PCG iterations on (x, p, r, Ap, z) until the device flags say done or
+// broken, or maxit iterations; checks on the host every `every` iterations.
+template <typename T, typename XT>
+static cudaError_t pcg_loop(fem_pcg *s, const T *G, XT *x, T *p, T *r, T *Ap, T *z, const T *dinv, int maxit,
+                            int every, cudaStream_t st, int *iters) {
+    const int64_t len = s->len;
+    int done_it = 0;
+    cudaError_t e = cudaSuccess;
+    while (done_it < maxit) {
+        int chunk = every;
+        if (chunk > maxit - done_it) chunk = maxit - done_it;
+        for (int c = 0; c < chunk && e == cudaSuccess; c++) {
+            if (sizeof(T) == 8)
+                e = launch_bp35_pcg(s->basis, s->E, (const double *)G, s->lambda, (const double *)z, (double *)p,
+                                    s->scal + S_BETA, (double *)Ap, s->part, st);
+            else
+                e = launch_bp35_pcg_f32(s->basis, s->E, (const float *)G, s->lambda, (const float *)z, (float *)p,
+                                        s->scal + S_BETA, (float *)Ap, s->part, st);
+            if (e != cudaSuccess) break;
+            reduce_kernel<<<1, kRedThreads, 0, st>>>(R_PQ, bp35_blocks(s->basis->host.N, s->E, sizeof(T) == 4), s->part,
+                                                     s->scal, nullptr, 0.0);
+            update_kernel<T, XT><<<kVecBlocks, kVecThreads, 0, st>>>(len, s->scal, x, p, r, Ap, z, dinv, s->part);
+            reduce_kernel<<<1, kRedThreads, 0, st>>>(R_RZ, kVecBlocks, s->part, s->scal, nullptr, 0.0);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) return e;
+        done_it += chunk;
+        e = sync_scalars(s, st);
+        if (e != cudaSuccess) return e;
+        if (s->hscal[S_DONE] != 0.0 || s->hscal[S_BREAK] != 0.0) break;
+    }
+    *iters = (int)s->hscal[S_ITER];
+    return cudaSuccess;
+}
+
+
+int pcg_solve(fem_pcg *s, const double *b, double *x, const fem_pcg_opts *o, fem_pcg_info *info, cudaStream_t st) {
+    const double tol = (o && o->tol > 0) ? o->tol : 1e-10;
+    const int maxit = (o && o->maxit > 0) ? o->maxit : 100000;
+    const double itol = (o && o->inner_tol > 0) ? o->inner_tol : 1e-4;
+    const int imaxit = (o && o->inner_maxit > 0) ? o->inner_maxit : 100000;
+    const int every = (o && o->check_every > 0) ? o->check_every : (s->mode == FEM_PCG_FP64 ? 8 : 16);
+    const int64_t len = s->len;
+    fem_pcg_info loc;
+    std::memset(&loc, 0, sizeof loc);
+    cudaError_t e = cudaSetDevice(s->device);
+    // b . b
+    if (e == cudaSuccess) e = launch_dot(len, b, b, s->scal + S_BB, s->part, st);
+    if (e == cudaSuccess) e = sync_scalars(s, st);
+    if (e != cudaSuccess) return -2;
+    const double bb = s->hscal[S_BB];
+    int status = FEM_OK;
+    if (bb == 0.0) {  // the solution of A x = 0 is 0
+        e = cudaMemsetAsync(x, 0, sizeof(double) * len, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (info) *info = loc;
+        return e == cudaSuccess ? FEM_OK : -2;
+    }
+    if (s->mode == FEM_PCG_FP64) {
+        e = launch_bp35(s->basis, s->E, s->G, s->lambda, x, s->q, st);
+        if (e == cudaSuccess) {
+            init_kernel<<<kVecBlocks, kVecThreads, 0, st>>>(len, b, s->q, s->r, s->z, s->dinv, s->part);
+            reduce_kernel<<<1, kRedThreads, 0, st>>>(R_INIT, kVecBlocks, s->part, s->scal, nullptr, tol * tol);
+            e = cudaGetLastError();
+        }
+        int it = 0;
+        if (e == cudaSuccess) e = pcg_loop<double, double>(s, s->G, x, s->p, s->r, s->q, s->z, s->dinv, maxit, every, st, &it);
+        if (e != cudaSuccess) return -2;
+        loc.iters = it;
+        loc.outer = 1;
+        if (s->hscal[S_BREAK] != 0.0 && s->hscal[S_DONE] == 0.0) status = FEM_EBREAKDOWN;
+        else if (s->hscal[S_DONE] == 0.0) status = FEM_ENOCONV;
+    } else {
+        const int max_outer = 64;
+        int outer = 0;
+        for (; outer < max_outer; outer++) {
+            e = launch_bp35(s->basis, s->E, s->G, s->lambda, x, s->q, st);
+            if (e != cudaSuccess) break;
+            outer_kernel<<<kVecBlocks, kVecThreads, 0, st>>>(len, b, s->q, s->r32, s->z32, s->d32, s->dinv32, s->part);
+            reduce_kernel<<<1, kRedThreads, 0, st>>>(R_OUTER, kVecBlocks, s->part, s->scal, nullptr, itol * itol);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = sync_scalars(s, st);
+            if (e != cudaSuccess) break;
+            loc.relres = std::sqrt(s->hscal[S_RR_OUTER] / bb);
+            if (s->hscal[S_RR_OUTER] <= tol * tol * bb) break;
+            if (loc.iters >= imaxit * max_outer || loc.iters >= maxit) {
+                status = FEM_ENOCONV;
+                break;
+            }
+            int it = 0;
+            e = pcg_loop<float, float>(s, s->G32, s->d32, s->p32, s->r32, s->q32, s->z32, s->dinv32, imaxit, every, st,
+                                       &it);
+            if (e != cudaSuccess) break;
+            loc.iters += it;
+            if (it == 0 && s->hscal[S_BREAK] != 0.0) {
+                status = FEM_EBREAKDOWN;
+                break;
+            }
+            add_f32_kernel<<<kVecBlocks, kVecThreads, 0, st>>>(len, x, s->d32);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) break;
+        }
+        if (e != cudaSuccess) return -2;
+        if (outer == max_outer) status = FEM_ENOCONV;
+        loc.outer = outer;
+    }
+    // true FP64 residual of the returned x
+    e = launch_bp35(s->basis, s->E, s->G, s->lambda, x, s->q, st);
+    if (e == cudaSuccess && s->mode == FEM_PCG_FP64) {
+        init_kernel<<<kVecBlocks, kVecThreads, 0, st>>>(len, b, s->q, s->r, s->z, s->dinv, s->part);
+        reduce_kernel<<<1, kRedThreads, 0, st>>>(R_TRUE, kVecBlocks, s->part, s->scal, nullptr, 0.0);
+    }
+    if (e == cudaSuccess && s->mode != FEM_PCG_FP64) {
+        outer_kernel<<<kVecBlocks, kVecThreads, 0, st>>>(len, b, s->q, s->r32, s->z32, s->d32, s->dinv32, s->part);
+        reduce_kernel<<<1, kRedThreads, 0, st>>>(R_OUTER, kVecBlocks, s->part, s->scal, nullptr, itol * itol);
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = sync_scalars(s, st);
+    if (e != cudaSuccess) return -2;
+    loc.relres = std::sqrt((s->mode == FEM_PCG_FP64 ? s->hscal[S_RR] : s->hscal[S_RR_OUTER]) / bb);
+    if (info) *info = loc;
+    return status;
+}
+
+}  // namespace fem
+
+// ---------------------------------------------------------------------- C ABI
+
+extern "C" {
+
+int64_t fem_dot_scratch_size(void) { return fem::dot_scratch_size(); }
+
+int fem_dot(int64_t n, const double *x, const double *y, double *result, double *scratch, void *stream) {
+    if (n < 0 || !result || !scratch) return FEM_EINVAL;
+    if (n > 0 && (!x || !y)) return FEM_EINVAL;
+    cudaError_t e = fem::launch_dot(n, x, y, result, scratch, (cudaStream_t)stream);
+    return e == cudaSuccess ? FEM_OK : fem::record_cuda_error(e);
+}
+
+int fem_bp35_jacobi(const fem_basis *b, int64_t E, const double *G, double lambda, double *dinv, void *stream) {
+    if (!b || E < 0) return FEM_EINVAL;
+    if (E == 0) return FEM_OK;
+    if (!G || !dinv) return FEM_EINVAL;
+    cudaError_t e = fem::dispatch_degree<fem::DinvLaunch>(b->host.N, b, E, G, lambda, dinv, (float *)nullptr,
+                                                          (cudaStream_t)stream);
+    return e == cudaSuccess ? FEM_OK : fem::record_cuda_error(e);
+}
+
+int fem_pcg_create(const fem_basis *b, int64_t E, const double *G, double lambda, int mode, fem_pcg **out) {
+    if (!b || !out || E < 1 || !G || (mode != FEM_PCG_FP64 && mode != FEM_PCG_MIXED)) return FEM_EINVAL;
+    if (!(lambda >= 0.0)) return FEM_EINVAL;
+    *out = nullptr;
+    fem_pcg *s = new (std::nothrow) fem_pcg();
+    if (!s) return FEM_ENOMEM;
+    std::memset(s, 0, sizeof(*s));
+    s->basis = b;
+    s->E = E;
+    s->len = E * (int64_t)b->host.n * b->host.n * b->host.n;
+    s->G = G;
+    s->lambda = lambda;
+    s->mode = mode;
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = fem::pcg_create(s);
+    if (e != cudaSuccess) {
+        fem::pcg_release(s);
+        delete s;
+        return e == cudaErrorMemoryAllocation ? FEM_ENOMEM : fem::record_cuda_error(e);
+    }
+    *out = s;
+    return FEM_OK;
+}
+
+void fem_pcg_destroy(fem_pcg *s) {
+    if (!s) return;
+    fem::pcg_release(s);
+    delete s;
+}
+
+int fem_pcg_solve(fem_pcg *s, const double *rhs, double *x, const fem_pcg_opts *opts, fem_pcg_info *info,
+                  void *stream) {
+    if (!s || !rhs || !x || rhs == x) return FEM_EINVAL;
+    const int r = fem::pcg_solve(s, rhs, x, opts, info, (cudaStream_t)stream);
+    if (r == -2) return fem::record_cuda_error(cudaGetLastError());
+    return r;
+}
+
+}  // extern "C"

@@ -1,0 +1,174 @@
+"""GPU checks of the precision row: the FP32 BP3.5 matvec, the Jacobi
+diagonal, the deterministic dot product, and the FP64 and mixed-precision
+(FP32 inner solves inside FP64 defect correction) Jacobi-PCG solvers, against
+the FP64 oracle and the manufactured discrete solution."""
+import numpy as np
+import pytest
+
+import fem_synth
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _fem():
+    import paper_1711_00903_gb300 as fem
+    return fem
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dev(a):
+    return _torch().from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def _rel(got, ref):
+    return np.abs(np.asarray(got) - ref).max() / np.abs(ref).max()
+
+
+def _manufactured(N, nx, lam=1.0):
+    """b = A_oracle u_I, u_I = sin(pi x) sin(pi y) sin(pi z) at the GLL nodes."""
+    v = fem_synth.box_mesh(nx)
+    G, _ = oracle.geofacs(N, oracle.KIND_BP35, v)
+    X = oracle.gll_node_coordinates(N, v)
+    u = np.sin(np.pi * X[..., 0]) * np.sin(np.pi * X[..., 1]) * np.sin(np.pi * X[..., 2])
+    b = oracle.bp35(N, G, lam, u)
+    return v, G, u, b
+
+
+@pytest.mark.parametrize("N", [1, 3, 7, 15])
+def test_jacobi_diagonal(N):
+    fem = _fem()
+    v = fem_synth.box_mesh(3)[:23]
+    G, _ = oracle.geofacs(N, oracle.KIND_BP35, v)
+    b = fem.fem_basis_setup(N)
+    got = fem.fem_bp35_jacobi(b, _dev(G), 1.0).cpu().numpy()
+    ref = 1.0 / oracle.bp35_diag(N, G, 1.0)
+    assert _rel(got, ref) < 1e-12
+
+
+@pytest.mark.parametrize("N", [1, 2, 5, 7, 11, 15])
+def test_bp35_f32_matches_fp64_operator(N):
+    """FP32 matvec against the FP64 oracle applied to the same FP32-rounded
+    inputs: the difference is FP32 rounding of the arithmetic only."""
+    fem, torch = _fem(), _torch()
+    v = fem_synth.box_mesh(3)[:19]
+    E = v.shape[0]
+    G, _ = oracle.geofacs(N, oracle.KIND_BP35, v)
+    q = fem_synth.field(2, E, (N + 1) ** 3)
+    G32, q32 = G.astype(np.float32), q.astype(np.float32)
+    ref = oracle.bp35(N, G32.astype(np.float64), 1.0, q32.astype(np.float64))
+    b = fem.fem_basis_setup(N)
+    got = fem.fem_bp35_apply_f32(b, _dev(G32), 1.0, _dev(q32)).cpu().numpy().astype(np.float64)
+    assert _rel(got, ref) < 2e-6 * (N + 1)
+
+
+def test_dot_deterministic_and_exact():
+    fem, torch = _fem(), _torch()
+    x = fem_synth.field(11, 1, 3_000_001)[0]
+    y = fem_synth.field(12, 1, 3_000_001)[0]
+    xd, yd = _dev(x), _dev(y)
+    r1 = fem.fem_dot(xd, yd).item()
+    r2 = fem.fem_dot(xd, yd).item()
+    assert r1 == r2
+    ref = float(np.dot(x, y))
+    assert abs(r1 - ref) <= 1e-12 * np.abs(x * y).sum()
+    assert fem.fem_dot(xd[:0], yd[:0]).item() == 0.0
+
+
+@pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("N", [2, 4, 7])
+def test_pcg_manufactured(N, mode):
+    fem = _fem()
+    v, G, u, b = _manufactured(N, 4)
+    basis = fem.fem_basis_setup(N)
+    Gd = _dev(G)
+    s = fem.fem_pcg_create(basis, Gd, 1.0, mode)
+    x, info, code = s.solve(_dev(b), tol=1e-12 if mode == 0 else 1e-11)
+    x = x.cpu().numpy()
+    assert code == 0
+    assert info["relres"] <= (1e-12 if mode == 0 else 1e-11) * 1.0001
+    # true residual recomputed by the oracle
+    tr = np.linalg.norm(b - oracle.bp35(N, G, 1.0, x)) / np.linalg.norm(b)
+    assert tr <= 2e-11
+    lim = 1e-8 if mode == 0 else 1e-7
+    assert np.linalg.norm(x - u) / np.linalg.norm(u) <= lim
+    # against the oracle's own PCG solve
+    xo, it_o, _ = oracle.pcg_bp35(N, G, 1.0, b, tol=1e-12)
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) <= lim
+    if mode == 0:
+        assert abs(info["iters"] - it_o) <= 2
+    else:
+        assert info["outer"] >= 2
+
+
+def test_pcg_result_independent_of_check_period_and_repeatable():
+    fem = _fem()
+    N = 3
+    v, G, u, b = _manufactured(N, 3)
+    basis = fem.fem_basis_setup(N)
+    s = fem.fem_pcg_create(basis, _dev(G), 1.0, 0)
+    bd = _dev(b)
+    x1, i1, _ = s.solve(bd, tol=1e-10, check_every=1)
+    x2, i2, _ = s.solve(bd, tol=1e-10, check_every=7)
+    x3, i3, _ = s.solve(bd, tol=1e-10, check_every=7)
+    assert i1["iters"] == i2["iters"] == i3["iters"]
+    assert bool((x1 == x2).all()) and bool((x2 == x3).all())
+
+
+def test_pcg_edge_cases():
+    fem, torch = _fem(), _torch()
+    N = 2
+    v, G, u, b = _manufactured(N, 2)
+    basis = fem.fem_basis_setup(N)
+    Gd = _dev(G)
+    with pytest.raises(fem.FemError):
+        fem.fem_pcg_create(basis, Gd, -1.0, 0)
+    with pytest.raises(fem.FemError):
+        fem.fem_pcg_create(basis, Gd, 1.0, 7)
+    for mode in (0, 1):
+        s = fem.fem_pcg_create(basis, Gd, 1.0, mode)
+        zero = torch.zeros((v.shape[0], 27), dtype=torch.float64, device="cuda")
+        x, info, code = s.solve(zero, x=torch.ones_like(zero))
+        assert code == 0 and float(x.abs().max()) == 0.0
+        # iteration limit reached: FEM_ENOCONV, x holds the last iterate
+        x, info, code = s.solve(_dev(b), tol=1e-14, maxit=2, inner_maxit=1, raise_on_error=False)
+        assert code == fem.FEM_ENOCONV
+        assert np.all(np.isfinite(x.cpu().numpy()))
+
+
+def test_full_size_mixed_solve_config():
+    """N = 7 on the 32^3 mesh (E = 32768), manufactured right-hand side:
+    the mixed solve reaches the FP64 tolerance and the discrete solution."""
+    fem, torch = _fem(), _torch()
+    N = 7
+    v = fem_synth.box_mesh(32)
+    basis = fem.fem_basis_setup(N)
+    vd = _dev(v)
+    G = fem.fem_mesh_geofacs(basis, fem.FEM_GEO_BP35, vd)
+    X = oracle.gll_node_coordinates(N, v[:64])  # spot check of the coordinates below
+    # u_I on the device from the same trilinear map (oracle coordinates for all
+    # elements would take long; the map is evaluated by numpy here)
+    r, _ = oracle.gll(N)
+    n = N + 1
+    R, S, T = np.meshgrid(r, r, r, indexing="ij")  # (i, j, k) grids
+    R, S, T = R.transpose(2, 1, 0).reshape(-1), S.transpose(2, 1, 0).reshape(-1), T.transpose(2, 1, 0).reshape(-1)
+    phi = np.stack([((1 + (1 if c & 1 else -1) * R) * (1 + (1 if c & 2 else -1) * S) *
+                     (1 + (1 if c & 4 else -1) * T)) / 8 for c in range(8)], axis=1)  # (n^3, 8)
+    Xall = np.einsum("pc,ecd->epd", phi, v)
+    np.testing.assert_allclose(Xall[:64], X, rtol=0, atol=1e-14)
+    u = np.sin(np.pi * Xall[..., 0]) * np.sin(np.pi * Xall[..., 1]) * np.sin(np.pi * Xall[..., 2])
+    ud = _dev(u)
+    bd = fem.fem_bp35_apply(basis, G, 1.0, ud)
+    s = fem.fem_pcg_create(basis, G, 1.0, fem.FEM_PCG_MIXED)
+    x, info, code = s.solve(bd, tol=1e-10)
+    assert code == 0 and info["relres"] <= 1e-10
+    err = (torch.linalg.norm(x - ud) / torch.linalg.norm(ud)).item()
+    assert err <= 1e-7
+    s64 = fem.fem_pcg_create(basis, G, 1.0, fem.FEM_PCG_FP64)
+    x64, info64, code64 = s64.solve(bd, tol=1e-10)
+    assert code64 == 0
+    assert (torch.linalg.norm(x - x64) / torch.linalg.norm(x64)).item() <= 1e-7
