@@ -160,6 +160,29 @@ int64_t fem_dot_scratch_size(void);
 int fem_dot(int64_t n, const double *x, const double *y, double *result, double *scratch,
             void *stream);
 
+/* The same dot product without any device allocation, for callers that
+ * cannot call cudaMalloc where they need the reduction: code running while a
+ * stream is captured into a CUDA graph, a serving loop that must not
+ * allocate per request (an allocation can synchronise the device or fail
+ * under a fixed memory budget), or an application whose device memory is
+ * owned by its own allocator.  The paper has no counterpart; this is a
+ * library convenience.  The caller passes x, y (device, n doubles) and
+ * result (device, one double) only.  The partial sums live in a 32 KiB
+ * device array inside the library (one partial per 8192 entries), which
+ * every GPU that loads the library holds until the process exits, so n is
+ * capped at fem_dot_noalloc_max_n() = 33,554,432; larger n returns
+ * FEM_ETOOBIG without launching anything.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call
+ * shares the array and overwrites the slots it uses (nothing needs
+ * clearing), so calls that overlap on the GPU (different streams, or
+ * several host threads) race and must be serialised by the caller.
+ * Deterministic; agrees with fem_dot to rounding.  Asynchronous on stream.
+ * Errors: FEM_EINVAL, FEM_ETOOBIG, FEM_ECUDA. */
+#define FEM_ETOOBIG (-7) /* size beyond a fixed capacity of the library */
+int64_t fem_dot_noalloc_max_n(void);
+int fem_dot_noalloc(int64_t n, const double *x, const double *y, double *result, void *stream);
+
 /* ---------------------------------------------------------------------
  * Jacobi-preconditioned conjugate gradients for the unassembled BP3.5
  * Helmholtz system (D^T G D + lambda J) x = rhs (Section 4; the solver is

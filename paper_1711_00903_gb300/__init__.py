@@ -25,7 +25,7 @@ __all__ = [
 ]
 
 FEM_OK, FEM_EINVAL, FEM_ECUDA, FEM_ENOMEM, FEM_ENODEV = 0, -1, -2, -3, -4
-FEM_EBREAKDOWN, FEM_ENOCONV = -5, -6
+FEM_EBREAKDOWN, FEM_ENOCONV, FEM_ETOOBIG = -5, -6, -7
 FEM_PCG_FP64, FEM_PCG_MIXED = 0, 1
 FEM_GEO_BP1, FEM_GEO_BP35, FEM_GEO_BP30 = 1, 2, 3
 MAX_N = 15
@@ -82,6 +82,9 @@ def lib():
             L.fem_dot.argtypes = [i64, dp, dp, dp, dp, vp]
             L.fem_pcg_create.argtypes = [vp, i64, dp, dbl, i32, C.POINTER(vp)]
             L.fem_pcg_solve.argtypes = [vp, dp, dp, C.POINTER(PcgOpts), C.POINTER(PcgInfo), vp]
+            L.fem_dot_noalloc_max_n.restype = i64
+            L.fem_dot_noalloc.argtypes = [i64, dp, dp, dp, vp]
+            L.fem_dot_noalloc.restype = i32
             L.fem_pcg_destroy.argtypes = [vp]
             L.fem_pcg_destroy.restype = None
             for f in ("fem_basis_setup", "fem_basis_tables", "fem_basis_host_tables",

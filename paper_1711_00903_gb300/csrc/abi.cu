@@ -62,6 +62,7 @@ const char *fem_strerror(int code) {
         case FEM_ENODEV: return "FEM_ENODEV: no usable CUDA device";
         case FEM_EBREAKDOWN: return "FEM_EBREAKDOWN: conjugate-gradient breakdown";
         case FEM_ENOCONV: return "FEM_ENOCONV: iteration limit reached";
+        case FEM_ETOOBIG: return "FEM_ETOOBIG: size beyond the fixed capacity of the call";
         default: return "unknown fem error code";
     }
 }
