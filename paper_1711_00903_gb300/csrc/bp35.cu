@@ -28,12 +28,16 @@ template <typename T, int N>
 struct Bp35Cfg {
     static constexpr int n = N + 1, nn = n * n, NP = n * n * n;
     using B = Box<n, n, n>;
+    // FP32 is bound by HBM: at kernel start one thread asks the TMA engine
+    // to prefetch the block's factor planes (one contiguous range) into L2,
+    // so that the chain-rule phase finds them there.  FP64 is bound by FP64
+    // issue and reads the factors directly.
+    static constexpr bool PREFETCH = sizeof(T) == 4;
     static constexpr int smem_elem = 3 * B::size * (int)sizeof(T);
     static constexpr int EPB = pick_epb(n, smem_elem);
     static constexpr int threads = ((nn * EPB + 31) / 32) * 32;
-    static constexpr int smem = EPB * 3 * B::size * (int)sizeof(T) > threads * 8
-                                    ? EPB * 3 * B::size * (int)sizeof(T)
-                                    : threads * 8;
+    static constexpr int bytes = EPB * 3 * B::size * (int)sizeof(T);
+    static constexpr int smem = bytes > threads * 8 ? bytes : threads * 8;
     static constexpr int oD = fold_offset(N, kFoldD), oDT = fold_offset(N, kFoldDT);
 };
 
@@ -53,6 +57,8 @@ bp35_kernel(int64_t E, const T *__restrict__ G, double lambda, const T *__restri
 
     const int64_t e0 = (int64_t)blockIdx.x * EPB;
     const int nel = (int)((E - e0) < EPB ? (E - e0) : EPB);
+    if (C::PREFETCH && threadIdx.x == 0)
+        prefetch_l2(G + e0 * 7 * NP, (long long)nel * 7 * NP * (long long)sizeof(T));
 
     // stage the input field of the block's elements (contiguous in memory)
     if (PCG) {
@@ -138,7 +144,7 @@ bp35_kernel(int64_t E, const T *__restrict__ G, double lambda, const T *__restri
     }
     __syncthreads();
 
-    double dot = 0.0;
+    T dot = T(0);  // p . Ap of the thread's column, in the data's precision
     if (act) {
         T *Ae = Aq + (e0 + el) * NP + r;
 #pragma unroll
@@ -146,12 +152,12 @@ bp35_kernel(int64_t E, const T *__restrict__ G, double lambda, const T *__restri
             const int s = B::at(u, v, k);
             const T w = acc[k] + sR[s] + sS[s];
             Ae[k * nn] = w;
-            if (PCG) dot = fma((double)sQ[s], (double)w, dot);
+            if (PCG) dot = fmx(sQ[s], w, dot);
         }
     }
     if (PCG) {
         __syncthreads();  // the shared boxes are reused for the reduction
-        const double tot = block_sum(dot, reinterpret_cast<double *>(smem_raw));
+        const double tot = block_sum((double)dot, reinterpret_cast<double *>(smem_raw));
         if (threadIdx.x == 0) partials[blockIdx.x] = tot;
     }
 }

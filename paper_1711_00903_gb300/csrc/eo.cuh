@@ -39,8 +39,6 @@ __device__ __forceinline__ double fold_at<double>(int i) { return c_fold[i]; }
 template <>
 __device__ __forceinline__ float fold_at<float>(int i) { return c_fold32[i]; }
 
-__device__ __forceinline__ double fmx(double a, double b, double c) { return fma(a, b, c); }
-__device__ __forceinline__ float fmx(float a, float b, float c) { return fmaf(a, b, c); }
 
 // y (P) = A x (Q) along one line, A folded at table offset OFF, parity SIG,
 // in the precision T of the data.

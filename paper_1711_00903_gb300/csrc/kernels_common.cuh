@@ -21,6 +21,40 @@ __host__ __device__ constexpr int pick_epb(int q, int smem_per_elem) {
 // Rounds a count of doubles up to a multiple of 2 (16-byte alignment).
 __host__ __device__ constexpr int pad2(int x) { return (x + 1) & ~1; }
 
+// Asynchronous global -> shared copies (LDGSTS): the data lands in shared
+// memory without passing through registers; cp_async_wait_all() blocks the
+// issuing thread until its own copies have landed (a barrier then publishes
+// them to the block).  Both addresses must be aligned to the copy size.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// TMA bulk prefetch of [p, p + bytes) into L2, rounded inward to 16-byte
+// boundaries (a hint: nothing is prefetched outside the range).
+__device__ __forceinline__ void prefetch_l2(const void *p, long long bytes) {
+    const unsigned long long a = (unsigned long long)p, e = a + (unsigned long long)bytes;
+    const unsigned long long a16 = (a + 15) & ~15ull, e16 = e & ~15ull;
+    if (e16 <= a16) return;
+    unsigned long long off = a16;
+    while (off < e16) {  // a bulk prefetch moves at most 2^31 bytes; blocks use far less
+        unsigned long long sz = e16 - off;
+        if (sz > (1ull << 30)) sz = 1ull << 30;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(off), "r"((unsigned)sz) : "memory");
+        off += sz;
+    }
+}
+
+// Fused multiply-add in the precision of the operands.
+__device__ __forceinline__ double fmx(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmx(float a, float b, float c) { return fmaf(a, b, c); }
+
 // Copies `count` doubles from global to shared with all threads of the block.
 __device__ __forceinline__ void block_copy(double *dst, const double *__restrict__ src, int count) {
     for (int t = threadIdx.x; t < count; t += blockDim.x) dst[t] = __ldg(src + t);

@@ -148,7 +148,10 @@ outer_kernel(int64_t n, const double *__restrict__ b, const double *__restrict__
     }
 }
 
-// x += alpha p, r -= alpha Ap, z = dinv r; partials (r.z, r.r)
+// x += alpha p, r -= alpha Ap, z = dinv r; partials (r.z, r.r).  The
+// arithmetic is in the recurrence's own precision T (in FP32 the per-thread
+// partial sums too, so the FP32 inner solver issues no FP64 instruction per
+// entry); the per-block sums are FP64.
 template <typename T, typename XT>
 __global__ void __launch_bounds__(kVecThreads)
 update_kernel(int64_t n, const double *__restrict__ scal, XT *__restrict__ x, const T *__restrict__ p,
@@ -157,25 +160,60 @@ update_kernel(int64_t n, const double *__restrict__ scal, XT *__restrict__ x, co
     __shared__ double sh[32];
     const double alpha = scal[S_ALPHA];
     const T a = (T)alpha;
-    double rz = 0.0, rr = 0.0;
+    T rz = T(0), rr = T(0);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         T ri = r[i];
         if (alpha != 0.0) {
-            x[i] = (XT)fma((double)alpha, (double)p[i], (double)x[i]);
+            x[i] = fmx((XT)a, (XT)p[i], x[i]);
             ri = ri - a * Ap[i];
             r[i] = ri;
         }
         const T zi = dinv[i] * ri;
         z[i] = zi;
-        rz = fma((double)ri, (double)zi, rz);
-        rr = fma((double)ri, (double)ri, rr);
+        rz = fmx(ri, zi, rz);
+        rr = fmx(ri, ri, rr);
     }
-    rz = block_sum(rz, sh);
+    double drz = block_sum((double)rz, sh);
     __syncthreads();
-    rr = block_sum(rr, sh);
+    double drr = block_sum((double)rr, sh);
     if (threadIdx.x == 0) {
-        part[2 * blockIdx.x] = rz;
-        part[2 * blockIdx.x + 1] = rr;
+        part[2 * blockIdx.x] = drz;
+        part[2 * blockIdx.x + 1] = drr;
+    }
+}
+
+// The FP32 update with 16-byte vector accesses (n a multiple of 4, every
+// array 16-byte aligned): four entries per thread and iteration.
+__global__ void __launch_bounds__(kVecThreads)
+update_f32x4_kernel(int64_t n4, const double *__restrict__ scal, float4 *__restrict__ x, const float4 *__restrict__ p,
+                    float4 *__restrict__ r, const float4 *__restrict__ Ap, float4 *__restrict__ z,
+                    const float4 *__restrict__ dinv, double *__restrict__ part) {
+    __shared__ double sh[32];
+    const double alpha = scal[S_ALPHA];
+    const float a = (float)alpha;
+    float rz = 0.0f, rr = 0.0f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        float4 ri = r[i];
+        const float4 di = dinv[i];
+        if (alpha != 0.0) {
+            const float4 pi = p[i], qi = Ap[i];
+            float4 xi = x[i];
+            xi.x += a * pi.x; xi.y += a * pi.y; xi.z += a * pi.z; xi.w += a * pi.w;
+            x[i] = xi;
+            ri.x -= a * qi.x; ri.y -= a * qi.y; ri.z -= a * qi.z; ri.w -= a * qi.w;
+            r[i] = ri;
+        }
+        const float4 zi = make_float4(di.x * ri.x, di.y * ri.y, di.z * ri.z, di.w * ri.w);
+        z[i] = zi;
+        rz += ri.x * zi.x + ri.y * zi.y + ri.z * zi.z + ri.w * zi.w;
+        rr += ri.x * ri.x + ri.y * ri.y + ri.z * ri.z + ri.w * ri.w;
+    }
+    double drz = block_sum((double)rz, sh);
+    __syncthreads();
+    double drr = block_sum((double)rr, sh);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = drz;
+        part[2 * blockIdx.x + 1] = drr;
     }
 }
 
@@ -378,7 +416,12 @@ static cudaError_t pcg_loop(fem_pcg *s, const T *G, XT *x, T *p, T *r, T *Ap, T 
             if (e != cudaSuccess) break;
             reduce_kernel<<<1, kRedThreads, 0, st>>>(R_PQ, bp35_blocks(s->basis->host.N, s->E, sizeof(T) == 4), s->part,
                                                      s->scal, nullptr, 0.0);
-            update_kernel<T, XT><<<kVecBlocks, kVecThreads, 0, st>>>(len, s->scal, x, p, r, Ap, z, dinv, s->part);
+            if (sizeof(T) == 4 && sizeof(XT) == 4 && len % 4 == 0)
+                update_f32x4_kernel<<<kVecBlocks, kVecThreads, 0, st>>>(
+                    len / 4, s->scal, (float4 *)x, (const float4 *)p, (float4 *)r, (const float4 *)Ap, (float4 *)z,
+                    (const float4 *)dinv, s->part);
+            else
+                update_kernel<T, XT><<<kVecBlocks, kVecThreads, 0, st>>>(len, s->scal, x, p, r, Ap, z, dinv, s->part);
             reduce_kernel<<<1, kRedThreads, 0, st>>>(R_RZ, kVecBlocks, s->part, s->scal, nullptr, 0.0);
             e = cudaGetLastError();
         }
