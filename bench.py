@@ -426,6 +426,8 @@ def run_ours(args):
                 "frac": kern[dom]["hbm_frac"]},
     }
 
+    pcg = None if args.no_pcg else run_pcg(fem, torch, device, verts_h, args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = len(os.sched_getaffinity(0))
@@ -453,6 +455,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "clocks": clocks,
             "kernels": kern,
+            "pcg": pcg,
         }
         print(json.dumps(line))
     b.free()
@@ -460,6 +463,61 @@ def run_ours(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def manufactured_u(fem, basis, verts_h):
+    """u_I = sin(pi x) sin(pi y) sin(pi z) at every element's GLL nodes
+    (physical coordinates through the trilinear map, GLL nodes from the
+    library's basis tables)."""
+    N = basis.N
+    r = fem.fem_basis_tables(basis)["r"]
+    n = N + 1
+    R, S, T = np.meshgrid(r, r, r, indexing="ij")
+    R, S, T = (a.transpose(2, 1, 0).reshape(-1) for a in (R, S, T))
+    phi = np.stack([(1 + (1 if c & 1 else -1) * R) * (1 + (1 if c & 2 else -1) * S) *
+                    (1 + (1 if c & 4 else -1) * T) / 8 for c in range(8)], axis=1)
+    X = np.einsum("pc,ecd->epd", phi, verts_h)
+    return np.sin(np.pi * X[..., 0]) * np.sin(np.pi * X[..., 1]) * np.sin(np.pi * X[..., 2])
+
+
+def run_pcg(fem, torch, device, verts_h, args):
+    """Jacobi-PCG of the BP3.5 Helmholtz system (lambda = 1) with the
+    manufactured right-hand side b = A u_I: all-FP64 against FP32 inner
+    solves inside FP64 defect correction, both to ||r|| <= 1e-10 ||b||."""
+    N, lam, tol = args.degree, 1.0, 1e-10
+    basis = fem.fem_basis_setup(N)
+    vd = torch.from_numpy(verts_h).to(device)
+    G = fem.fem_mesh_geofacs(basis, fem.FEM_GEO_BP35, vd)
+    u = torch.from_numpy(manufactured_u(fem, basis, verts_h)).to(device)
+    b = fem.fem_bp35_apply(basis, G, lam, u)
+    out = {"workload": f"BP3.5 Helmholtz PCG (Jacobi), N={N}, E={verts_h.shape[0]}, lambda=1, "
+                       f"b = A u_I with u = sin(pi x) sin(pi y) sin(pi z), tol {tol:g}",
+           "error_reference": "u_I, the exact discrete solution (the oracle PCG agrees with the GPU "
+                              "solvers to 1e-8 on the smaller meshes of tests/test_pcg_gpu.py)"}
+    xs = {}
+    for name, mode, itol in (("fp64", fem.FEM_PCG_FP64, 0.0), ("mixed", fem.FEM_PCG_MIXED, 1e-3)):
+        s = fem.fem_pcg_create(basis, G, lam, mode)
+        x, info, code = s.solve(b, tol=tol, inner_tol=itol)  # warm-up
+        times = []
+        for _ in range(max(1, args.pcg_solves)):
+            x.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x, info, code = s.solve(b, x=x, tol=tol, inner_tol=itol)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        med = statistics.median(times)
+        err = (torch.linalg.norm(x - u) / torch.linalg.norm(u)).item()
+        out[name] = {"solves_per_s": 1.0 / med, "ms_per_solve": 1e3 * med, "iters": info["iters"],
+                     "outer": info["outer"], "relres": info["relres"], "status": code,
+                     "rel_err_vs_u_I": err}
+        xs[name] = x.clone()
+        s.free()
+    out["mixed"]["rel_diff_vs_fp64_solve"] = (torch.linalg.norm(xs["mixed"] - xs["fp64"]) /
+                                              torch.linalg.norm(xs["fp64"])).item()
+    out["mixed_speedup"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    basis.free()
+    return out
 
 
 def main(argv=None):
@@ -474,6 +532,8 @@ def main(argv=None):
                          "smaller sides are for profiling captures)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-pcg", action="store_true", help="skip the Helmholtz solve measurement")
+    ap.add_argument("--pcg-solves", type=int, default=3)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be at least 3")
