@@ -427,6 +427,7 @@ def run_ours(args):
     }
 
     pcg = None if args.no_pcg else run_pcg(fem, torch, device, verts_h, args)
+    batch = None if args.no_batch else run_batch(fem, torch, device, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -456,6 +457,7 @@ def run_ours(args):
             "clocks": clocks,
             "kernels": kern,
             "pcg": pcg,
+            "batch": batch,
         }
         print(json.dumps(line))
     b.free()
@@ -520,6 +522,58 @@ def run_pcg(fem, torch, device, verts_h, args):
     return out
 
 
+def run_batch(fem, torch, device, args):
+    """64 independent jittered meshes, N uniform in 2..10, E log-uniform in
+    64..8192, BP3.5 and BP3.0 (FP64, lambda = 1) on each: 128 separate launches
+    against one persistent launch (default and autotuned configuration) and
+    its CUDA-graph replay."""
+    w = fem_synth.batch_workload()
+    bases = {N: fem.fem_basis_setup(N) for N in sorted({s["N"] for s in w})}
+    items, dofs = [], 0
+    for s in w:
+        b = bases[s["N"]]
+        v = torch.from_numpy(fem_synth.box_mesh(s["nx"], s["ny"], s["nz"], jitter=0.1,
+                                                seed=s["mesh_seed"])).to(device)
+        q = torch.from_numpy(fem_synth.field(s["mesh_seed"] + 7, s["E"], (s["N"] + 1) ** 3)).to(device)
+        for op, kind in ((fem.FEM_OP_BP35, fem.FEM_GEO_BP35), (fem.FEM_OP_BP30, fem.FEM_GEO_BP30)):
+            g = fem.fem_mesh_geofacs(b, kind, v)
+            items.append((op, b, g, 1.0, q, torch.empty_like(q)))
+            dofs += q.numel()
+    batch = fem.Batch(items)
+
+    def timed(fn, reps=10):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def separate():
+        for op, b, g, lam, q, out in items:
+            (fem.fem_bp35_apply if op == fem.FEM_OP_BP35 else fem.fem_bp30_apply)(b, g, lam, q, out=out)
+
+    ms_sep = timed(separate)
+    ms_default = timed(batch.apply)
+    results = batch.tune(reps=5)
+    ms_tuned = timed(batch.apply)
+    ms_graph = timed(batch.graph_launch)
+    out = {"workload": "64 jittered meshes, N uniform 2..10, E log-uniform 64..8192 (108835 elements), "
+                       "BP3.5 and BP3.0 FP64 lambda=1 on each (128 matvecs)",
+           "dofs_per_pass": dofs,
+           "separate_launches": {"ms": ms_sep, "gdofs": dofs / ms_sep / 1e6},
+           "persistent_default": {"ms": ms_default, "gdofs": dofs / ms_default / 1e6},
+           "persistent_tuned": {"ms": ms_tuned, "gdofs": dofs / ms_tuned / 1e6, "config": batch.config},
+           "graph": {"ms": ms_graph, "gdofs": dofs / ms_graph / 1e6},
+           "tuner_candidates": len(results)}
+    batch.free()
+    return out
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -534,6 +588,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-pcg", action="store_true", help="skip the Helmholtz solve measurement")
     ap.add_argument("--pcg-solves", type=int, default=3)
+    ap.add_argument("--no-batch", action="store_true", help="skip the mixed-order batch measurement")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be at least 3")

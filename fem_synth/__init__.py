@@ -107,3 +107,22 @@ def field(seed: int, E: int, npts: int, lo: float = -1.0, hi: float = 1.0,
           offset: int = 0) -> np.ndarray:
     """Element-local field (E, npts) uniform in [lo, hi)."""
     return uniform(seed, E * npts, lo, hi, offset).reshape(E, npts)
+
+
+def batch_workload(count: int = 64, seed: int = SEED_BATCH, nmin: int = 2, nmax: int = 10,
+                   emin: int = 64, emax: int = 8192):
+    """Mixed-order batch recipe: `count` independent meshes, degree N uniform
+    in nmin..nmax, element count log-uniform in [emin, emax] rounded to a
+    near-cubic nx x ny x nz box of the unit cube, each jittered by its own
+    seed.  Returns a list of dicts (N, nx, ny, nz, E, mesh_seed)."""
+    u = uniform(seed, 2 * count)
+    out = []
+    for i in range(count):
+        N = nmin + min(int(u[2 * i] * (nmax - nmin + 1)), nmax - nmin)
+        target = float(np.exp(np.log(emin) + u[2 * i + 1] * (np.log(emax) - np.log(emin))))
+        nx = max(1, int(round(target ** (1.0 / 3.0))))
+        ny = max(1, int(round((target / nx) ** 0.5)))
+        nz = max(1, int(round(target / (nx * ny))))
+        out.append({"N": N, "nx": nx, "ny": ny, "nz": nz, "E": nx * ny * nz,
+                    "mesh_seed": seed * 1000 + i})
+    return out

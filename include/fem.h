@@ -239,6 +239,66 @@ int fem_pcg_solve(fem_pcg *s, const double *rhs, double *x, const fem_pcg_opts *
 /* Frees a solver (NULL accepted).  Synchronous. */
 void fem_pcg_destroy(fem_pcg *s);
 
+/* ---------------------------------------------------------------------
+ * Batched matvecs: many independent meshes of mixed degree (1..10), each
+ * with its own operator (BP3.5 or BP3.0, FP64), factors, lambda, input and
+ * output, applied in ONE persistent launch (Section 4: every element is
+ * independent, so meshes are just more elements).  Each element's result is
+ * bit-identical to the per-mesh fem_bp35_apply / fem_bp30_apply call.
+ * --------------------------------------------------------------------- */
+#define FEM_OP_BP35 2
+#define FEM_OP_BP30 3
+
+typedef struct {
+    int op;                  /* FEM_OP_BP35 or FEM_OP_BP30                       */
+    const fem_basis *basis;  /* degree 1..10 (the handle must outlive the batch) */
+    int64_t E;               /* elements (0 allowed)                            */
+    const double *geo;       /* device factors, as for the per-mesh call        */
+    double lambda;
+    const double *q;         /* device input, E*Np doubles                      */
+    double *out;             /* device output, E*Np doubles, not aliasing q/geo */
+} fem_batch_item;
+
+typedef struct {
+    int threads; /* threads per persistent block: 256 or 512              */
+    int group;   /* tasks taken per fetch of the shared counter, 1..64    */
+    int order;   /* 0: tasks by decreasing cost per element; 1: as given  */
+    float ms;    /* measured time of one launch (fem_batch_tune), or 0    */
+} fem_batch_config;
+
+typedef struct fem_batch fem_batch; /* opaque */
+
+/* Builds the task list of a batch (device copies of the descriptors; the
+ * pointers in the items must stay valid while the batch is used).
+ * Allocates device memory; synchronous.  Errors: FEM_EINVAL (bad op, degree
+ * above 10, NULL or aliased pointers), FEM_ENOMEM, FEM_ECUDA. */
+int fem_batch_create(const fem_batch_item *items, int count, fem_batch **out);
+
+/* One persistent launch over every mesh of the batch with the current
+ * configuration (a 4-byte counter reset, then the kernel), asynchronous on
+ * stream.  Errors: FEM_EINVAL, FEM_ECUDA. */
+int fem_batch_apply(fem_batch *b, void *stream);
+
+/* Autotuner: times every configuration (threads 256/512 x group 1/2/4/8 x
+ * both task orders, reps launches each after a warm-up) on the batch itself,
+ * keeps the fastest as the batch's configuration, and writes up to
+ * max_results timings to results (may be NULL) and their count to
+ * *nresults (may be NULL).  Synchronous.  Errors: FEM_EINVAL, FEM_ECUDA. */
+int fem_batch_tune(fem_batch *b, void *stream, int reps, fem_batch_config *results, int max_results,
+                   int *nresults);
+
+int fem_batch_get_config(const fem_batch *b, fem_batch_config *cfg);
+int fem_batch_set_config(fem_batch *b, const fem_batch_config *cfg);
+
+/* Captures the current configuration's launch (counter reset + kernel) into
+ * a CUDA graph on an internal stream the first time (and again after the
+ * configuration changes), then launches the graph on stream.
+ * Errors: FEM_EINVAL, FEM_ECUDA. */
+int fem_batch_graph_launch(fem_batch *b, void *stream);
+
+/* Frees a batch (NULL accepted).  Synchronous. */
+void fem_batch_destroy(fem_batch *b);
+
 /* Static name of an error code. */
 const char *fem_strerror(int code);
 

@@ -22,12 +22,14 @@ __all__ = [
     "fem_bp35_apply", "fem_bp30_apply", "FEM_GEO_BP1", "FEM_GEO_BP35", "FEM_GEO_BP30",
     "geo_shape", "fem_bp35_apply_f32", "fem_bp35_jacobi", "fem_dot", "fem_dot_scratch_size", "Pcg",
     "fem_pcg_create", "fem_pcg_solve", "fem_pcg_destroy", "FEM_PCG_FP64", "FEM_PCG_MIXED",
+    "Batch", "fem_batch_create", "FEM_OP_BP35", "FEM_OP_BP30",
 ]
 
 FEM_OK, FEM_EINVAL, FEM_ECUDA, FEM_ENOMEM, FEM_ENODEV = 0, -1, -2, -3, -4
 FEM_EBREAKDOWN, FEM_ENOCONV, FEM_ETOOBIG = -5, -6, -7
 FEM_PCG_FP64, FEM_PCG_MIXED = 0, 1
 FEM_GEO_BP1, FEM_GEO_BP35, FEM_GEO_BP30 = 1, 2, 3
+FEM_OP_BP35, FEM_OP_BP30 = 2, 3
 MAX_N = 15
 
 _lock = threading.Lock()
@@ -43,6 +45,17 @@ class PcgOpts(C.Structure):
 class PcgInfo(C.Structure):
     """fem_pcg_info (include/fem.h)."""
     _fields_ = [("iters", C.c_int), ("outer", C.c_int), ("relres", C.c_double)]
+
+
+class BatchItem(C.Structure):
+    """fem_batch_item (include/fem.h)."""
+    _fields_ = [("op", C.c_int), ("basis", C.c_void_p), ("E", C.c_int64), ("geo", C.c_void_p),
+                ("lam", C.c_double), ("q", C.c_void_p), ("out", C.c_void_p)]
+
+
+class BatchConfig(C.Structure):
+    """fem_batch_config (include/fem.h)."""
+    _fields_ = [("threads", C.c_int), ("group", C.c_int), ("order", C.c_int), ("ms", C.c_float)]
 
 
 class FemError(RuntimeError):
@@ -85,6 +98,17 @@ def lib():
             L.fem_dot_noalloc_max_n.restype = i64
             L.fem_dot_noalloc.argtypes = [i64, dp, dp, dp, vp]
             L.fem_dot_noalloc.restype = i32
+            L.fem_batch_create.argtypes = [C.POINTER(BatchItem), i32, C.POINTER(vp)]
+            L.fem_batch_apply.argtypes = [vp, vp]
+            L.fem_batch_tune.argtypes = [vp, vp, i32, C.POINTER(BatchConfig), i32, C.POINTER(i32)]
+            L.fem_batch_get_config.argtypes = [vp, C.POINTER(BatchConfig)]
+            L.fem_batch_set_config.argtypes = [vp, C.POINTER(BatchConfig)]
+            L.fem_batch_graph_launch.argtypes = [vp, vp]
+            L.fem_batch_destroy.argtypes = [vp]
+            L.fem_batch_destroy.restype = None
+            for f in ("fem_batch_create", "fem_batch_apply", "fem_batch_tune", "fem_batch_get_config",
+                      "fem_batch_set_config", "fem_batch_graph_launch"):
+                getattr(L, f).restype = i32
             L.fem_pcg_destroy.argtypes = [vp]
             L.fem_pcg_destroy.restype = None
             for f in ("fem_basis_setup", "fem_basis_tables", "fem_basis_host_tables",
@@ -357,3 +381,67 @@ def fem_pcg_solve(s: Pcg, rhs, x=None, tol=1e-10, maxit=0, inner_tol=0.0, inner_
 
 def fem_pcg_destroy(s: Pcg):
     s.free()
+
+
+class Batch:
+    """Owning wrapper of a fem_batch: many meshes of mixed degree applied in
+    one persistent launch.  items: list of (op, basis, geo, lam, q, out)."""
+
+    def __init__(self, items):
+        self.items = list(items)  # keeps every tensor and basis alive
+        arr = (BatchItem * max(1, len(self.items)))()
+        for k, (op, basis, geo, lam, q, out) in enumerate(self.items):
+            E = q.shape[0]
+            n, m = basis.n, basis.m
+            _dev(q, "q", E * n ** 3)
+            _dev(out, "out", E * n ** 3)
+            _dev(geo, "geo", E * 7 * (n ** 3 if op == FEM_OP_BP35 else m ** 3))
+            arr[k] = BatchItem(int(op), basis.handle.value, E, geo.data_ptr(), float(lam), q.data_ptr(),
+                               out.data_ptr())
+        h = C.c_void_p()
+        _check(lib().fem_batch_create(arr, len(self.items), C.byref(h)), "fem_batch_create")
+        self.handle = h
+
+    def apply(self, stream=None):
+        dev = self.items[0][4].device if self.items else None
+        _check(lib().fem_batch_apply(self.handle, _stream(stream, dev)), "fem_batch_apply")
+
+    def graph_launch(self, stream=None):
+        dev = self.items[0][4].device if self.items else None
+        _check(lib().fem_batch_graph_launch(self.handle, _stream(stream, dev)), "fem_batch_graph_launch")
+
+    def tune(self, reps=5, stream=None):
+        """Times every launch configuration; keeps the fastest.  Returns the
+        list of (threads, group, order, ms)."""
+        dev = self.items[0][4].device if self.items else None
+        res = (BatchConfig * 64)()
+        cnt = C.c_int(0)
+        _check(lib().fem_batch_tune(self.handle, _stream(stream, dev), int(reps), res, 64, C.byref(cnt)),
+               "fem_batch_tune")
+        return [(r.threads, r.group, r.order, r.ms) for r in res[:cnt.value]]
+
+    @property
+    def config(self):
+        c = BatchConfig()
+        _check(lib().fem_batch_get_config(self.handle, C.byref(c)), "fem_batch_get_config")
+        return {"threads": c.threads, "group": c.group, "order": c.order, "ms": c.ms}
+
+    @config.setter
+    def config(self, cfg):
+        c = BatchConfig(int(cfg["threads"]), int(cfg["group"]), int(cfg["order"]), 0.0)
+        _check(lib().fem_batch_set_config(self.handle, C.byref(c)), "fem_batch_set_config")
+
+    def free(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().fem_batch_destroy(self.handle)
+            self.handle = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def fem_batch_create(items) -> Batch:
+    return Batch(items)

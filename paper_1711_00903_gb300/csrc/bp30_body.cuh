@@ -1,0 +1,211 @@
+// Body of the FP64 BP3.0 kernel as a device function, shared by the
+// stand-alone kernel (bp30.cu) and the batched persistent kernel (batch.cu).
+// See bp30.cu for the algorithm and the GB300 design.
+#pragma once
+
+#include "eo.cuh"
+
+namespace fem {
+namespace {
+
+// Layout of one block of EPB elements (three m^3 shared boxes each).
+template <int N, int EPB_>
+struct Bp30Layout {
+    static constexpr int n = N + 1, m = N + 2;
+    static constexpr int NP = n * n * n, MP = m * m * m, mm = m * m;
+    using B0 = Box<n, n, n>;
+    using B1 = Box<m, n, n>;
+    using B2 = Box<m, m, n>;
+    using B3 = Box<m, m, m>;
+    static constexpr int S = B3::size;  // every buffer holds one m^3 box
+    static constexpr int per = 3 * S;
+    static constexpr int EPB = EPB_;
+    static constexpr int threads = ((mm * EPB + 31) / 32) * 32;  // the block needs at least this many
+    static constexpr int smem = EPB * per * 8;
+    static constexpr int oI = fold_offset(N, kFoldI), oIT = fold_offset(N, kFoldIT);
+    static constexpr int oDt = fold_offset(N, kFoldDt), oDtT = fold_offset(N, kFoldDtT);
+};
+
+// Elements per block of the stand-alone kernel: as many as fit 256 threads
+// under the shared-memory budget.
+template <int N>
+struct Bp30Cfg : Bp30Layout<N, pick_epb(N + 2, 3 * Box<N + 2, N + 2, N + 2>::size * 8)> {};
+
+// BP3.0 of elements [e0, e0 + nel) (nel <= EPB) by the whole block
+// (blockDim.x >= Layout::threads), shared memory at smem (Layout::smem bytes).
+template <int N, int EPB_>
+__device__ __forceinline__ void bp30_block(double *smem, int64_t e0, int nel, const double *__restrict__ G,
+                                           double lambda, const double *__restrict__ q, double *__restrict__ Aq) {
+    using C = Bp30Layout<N, EPB_>;
+    using B0 = typename C::B0;
+    using B1 = typename C::B1;
+    using B2 = typename C::B2;
+    using B3 = typename C::B3;
+    constexpr int n = C::n, m = C::m, NP = C::NP, MP = C::MP, mm = C::mm, EPB = C::EPB;
+    constexpr int S = C::S, per = C::per;
+    // per element: buffer A = smem + el*per, B = A + S, C = A + 2S
+    for (int t = threadIdx.x; t < nel * NP; t += blockDim.x) {
+        const int el = t / NP, p = t - el * NP;
+        smem[el * per + S + B0::at(p % n, (p / n) % n, p / (n * n))] = __ldg(q + e0 * NP + t);
+    }
+    __syncthreads();
+
+    // 1. r-interpolation (j, k): q (buffer B) -> X1 (buffer C)
+    for_tasks<n * n, EPB>(nel, [&](int el, int r) {
+        const int j = r % n, k = r / n;
+        const double *X0 = smem + el * per + S;
+        double *X1 = smem + el * per + 2 * S;
+        double x[n], y[m];
+#pragma unroll
+        for (int l = 0; l < n; l++) x[l] = X0[B0::at(l, j, k)];
+        eo_apply<m, n, 1, C::oI>(x, y);
+#pragma unroll
+        for (int l = 0; l < m; l++) X1[B1::at(l, j, k)] = y[l];
+    });
+    __syncthreads();
+
+    // 2. s-interpolation (a, k): X1 (C) -> X2 (B)
+    for_tasks<m * n, EPB>(nel, [&](int el, int r) {
+        const int a = r % m, k = r / m;
+        const double *X1 = smem + el * per + 2 * S;
+        double *X2 = smem + el * per + S;
+        double x[n], y[m];
+#pragma unroll
+        for (int l = 0; l < n; l++) x[l] = X1[B1::at(a, l, k)];
+        eo_apply<m, n, 1, C::oI>(x, y);
+#pragma unroll
+        for (int l = 0; l < m; l++) X2[B2::at(a, l, k)] = y[l];
+    });
+    __syncthreads();
+
+    // 3. t-interpolation (a, b): X2 (B) -> QG (A)
+    for_tasks<mm, EPB>(nel, [&](int el, int r) {
+        const int a = r % m, b = r / m;
+        const double *X2 = smem + el * per + S;
+        double *QG = smem + el * per;
+        double x[n], y[m];
+#pragma unroll
+        for (int l = 0; l < n; l++) x[l] = X2[B2::at(a, b, l)];
+        eo_apply<m, n, 1, C::oI>(x, y);
+#pragma unroll
+        for (int l = 0; l < m; l++) QG[B3::at(a, b, l)] = y[l];
+    });
+    __syncthreads();
+
+    // 4. r-derivative lines (b=u, c=v) -> UR (B), s-derivative lines (a=u, c=v) -> US (C)
+    for_tasks<mm, EPB>(nel, [&](int el, int r) {
+        const int u = r % m, v = r / m;
+        const double *QG = smem + el * per;
+        double *UR = smem + el * per + S, *US = smem + el * per + 2 * S;
+        double x[m], y[m];
+#pragma unroll
+        for (int l = 0; l < m; l++) x[l] = QG[B3::at(l, u, v)];
+        eo_apply<m, m, -1, C::oDt>(x, y);
+#pragma unroll
+        for (int l = 0; l < m; l++) UR[B3::at(l, u, v)] = y[l];
+#pragma unroll
+        for (int l = 0; l < m; l++) x[l] = QG[B3::at(u, l, v)];
+        eo_apply<m, m, -1, C::oDt>(x, y);
+#pragma unroll
+        for (int l = 0; l < m; l++) US[B3::at(u, l, v)] = y[l];
+    });
+    __syncthreads();
+
+    // 5. column (a, b): t-derivative, chain rule, t-transpose, mass term.
+    // Each thread has at most one column task (threads >= m*m*EPB), so acc
+    // stays in its registers until step 7.
+    const int cel = threadIdx.x / mm, cr = threadIdx.x - cel * mm;
+    const int ca = cr % m, cb = cr / m;
+    const bool cact = cel < nel;
+    double acc[m];
+    if (cact) {
+        const double *QG = smem + cel * per;
+        double *UR = smem + cel * per + S, *US = smem + cel * per + 2 * S;
+        double x[m], ut[m], Rt[m];
+#pragma unroll
+        for (int l = 0; l < m; l++) x[l] = QG[B3::at(ca, cb, l)];
+        eo_apply<m, m, -1, C::oDt>(x, ut);
+        const double *Ge = G + (e0 + cel) * 7 * MP + cr;
+#pragma unroll
+        for (int c = 0; c < m; c++) {
+            const int s = B3::at(ca, cb, c);
+            const double ur = UR[s], us = US[s];
+            double g[7];
+#pragma unroll
+            for (int h = 0; h < 7; h++) g[h] = __ldg(Ge + h * MP + c * mm);
+            UR[s] = g[0] * ur + g[1] * us + g[2] * ut[c];
+            US[s] = g[1] * ur + g[3] * us + g[4] * ut[c];
+            Rt[c] = g[2] * ur + g[4] * us + g[5] * ut[c];
+            acc[c] = (lambda != 0.0) ? (lambda * g[6]) * x[c] : 0.0;
+        }
+        double y[m];
+        eo_apply<m, m, -1, C::oDtT>(Rt, y);
+#pragma unroll
+        for (int c = 0; c < m; c++) acc[c] += y[c];
+    }
+    __syncthreads();
+
+    // 6. r- and s-transposes in place
+    for_tasks<mm, EPB>(nel, [&](int el, int r) {
+        const int u = r % m, v = r / m;
+        double *UR = smem + el * per + S, *US = smem + el * per + 2 * S;
+        double x[m], y[m];
+#pragma unroll
+        for (int l = 0; l < m; l++) x[l] = UR[B3::at(l, u, v)];
+        eo_apply<m, m, -1, C::oDtT>(x, y);
+#pragma unroll
+        for (int l = 0; l < m; l++) UR[B3::at(l, u, v)] = y[l];
+#pragma unroll
+        for (int l = 0; l < m; l++) x[l] = US[B3::at(u, l, v)];
+        eo_apply<m, m, -1, C::oDtT>(x, y);
+#pragma unroll
+        for (int l = 0; l < m; l++) US[B3::at(u, l, v)] = y[l];
+    });
+    __syncthreads();
+
+    // 7. column (a, b): sum of the three directions, t-projection -> X3 (A)
+    if (cact) {
+        const double *UR = smem + cel * per + S, *US = smem + cel * per + 2 * S;
+        double *X3 = smem + cel * per;
+        double y[n];
+#pragma unroll
+        for (int c = 0; c < m; c++) {
+            const int s = B3::at(ca, cb, c);
+            acc[c] += UR[s] + US[s];
+        }
+        eo_apply<n, m, 1, C::oIT>(acc, y);
+#pragma unroll
+        for (int l = 0; l < n; l++) X3[B2::at(ca, cb, l)] = y[l];
+    }
+    __syncthreads();
+
+    // 8. s-projection (a, k): X3 (A) -> X4 (B)
+    for_tasks<m * n, EPB>(nel, [&](int el, int r) {
+        const int a = r % m, k = r / m;
+        const double *X3 = smem + el * per;
+        double *X4 = smem + el * per + S;
+        double x[m], y[n];
+#pragma unroll
+        for (int l = 0; l < m; l++) x[l] = X3[B2::at(a, l, k)];
+        eo_apply<n, m, 1, C::oIT>(x, y);
+#pragma unroll
+        for (int l = 0; l < n; l++) X4[B1::at(a, l, k)] = y[l];
+    });
+    __syncthreads();
+
+    // 9. r-projection (j, k): X4 (B) -> Aq
+    for_tasks<n * n, EPB>(nel, [&](int el, int r) {
+        const double *X4 = smem + el * per + S;
+        const int j = r % n, k = r / n;
+        double x[m], y[n];
+#pragma unroll
+        for (int l = 0; l < m; l++) x[l] = X4[B1::at(l, j, k)];
+        eo_apply<n, m, 1, C::oIT>(x, y);
+        double *o = Aq + (e0 + el) * NP + r * n;
+#pragma unroll
+        for (int l = 0; l < n; l++) o[l] = y[l];
+    });
+}
+
+}  // namespace
+}  // namespace fem

@@ -1,0 +1,153 @@
+// Body of the BP3.5 kernels as a device function, shared by the stand-alone
+// kernels (bp35.cu) and the batched persistent kernel (batch.cu).  See
+// bp35.cu for the algorithm and the GB300 design.
+#pragma once
+
+#include "eo.cuh"
+
+namespace fem {
+namespace {
+
+// Layout of one block of EPB elements (three padded n^3 boxes each).
+template <typename T, int N, int EPB_>
+struct Bp35Layout {
+    static constexpr int n = N + 1, nn = n * n, NP = n * n * n;
+    using B = Box<n, n, n>;
+    // FP32 is bound by HBM: at kernel start one thread asks the TMA engine
+    // to prefetch the block's factor planes (one contiguous range) into L2,
+    // so that the chain-rule phase finds them there.  FP64 is bound by FP64
+    // issue and reads the factors directly.
+    static constexpr bool PREFETCH = sizeof(T) == 4;
+    static constexpr int EPB = EPB_;
+    static constexpr int threads = ((nn * EPB + 31) / 32) * 32;  // the block needs at least this many
+    static constexpr int bytes = EPB * 3 * B::size * (int)sizeof(T);
+    static constexpr int smem = bytes > threads * 8 ? bytes : threads * 8;
+    static constexpr int oD = fold_offset(N, kFoldD), oDT = fold_offset(N, kFoldDT);
+};
+
+// Elements per block of the stand-alone kernels: as many as fit 256 threads
+// under the shared-memory budget.
+template <typename T, int N>
+struct Bp35Cfg : Bp35Layout<T, N, pick_epb(N + 1, 3 * Box<N + 1, N + 1, N + 1>::size * (int)sizeof(T))> {};
+
+// BP3.5 of elements [e0, e0 + nel) (nel <= EPB) by the whole block
+// (blockDim.x >= Layout::threads), shared memory at smem_raw (Layout::smem
+// bytes).  PCG = true: the input field is p <- z + beta p (stored back to p;
+// beta read from *beta, p not read when beta is 0), and thread 0 writes the
+// block's p . Ap to *part_out.
+template <typename T, int N, int EPB_, bool PCG>
+__device__ __forceinline__ void bp35_block(unsigned char *smem_raw, int64_t e0, int nel, const T *__restrict__ G,
+                                           double lambda, const T *__restrict__ q, T *__restrict__ Aq,
+                                           const T *__restrict__ z, T *__restrict__ p,
+                                           const double *__restrict__ beta, double *__restrict__ part_out) {
+    using C = Bp35Layout<T, N, EPB_>;
+    using B = typename C::B;
+    constexpr int n = C::n, nn = C::nn, NP = C::NP;
+    T *smem = reinterpret_cast<T *>(smem_raw);
+    if (C::PREFETCH && threadIdx.x == 0)
+        prefetch_l2(G + e0 * 7 * NP, (long long)nel * 7 * NP * (long long)sizeof(T));
+
+    // stage the input field of the block's elements (contiguous in memory)
+    if (PCG) {
+        const T bt = (T)(*beta);
+        for (int t = threadIdx.x; t < nel * NP; t += blockDim.x) {
+            const int el = t / NP, s = t - el * NP;
+            const int64_t g = e0 * NP + t;
+            const T v = (bt == T(0)) ? z[g] : fmx(bt, p[g], z[g]);
+            p[g] = v;
+            smem[el * 3 * B::size + B::at(s % n, (s / n) % n, s / nn)] = v;
+        }
+    } else {
+        for (int t = threadIdx.x; t < nel * NP; t += blockDim.x) {
+            const int el = t / NP, s = t - el * NP;
+            smem[el * 3 * B::size + B::at(s % n, (s / n) % n, s / nn)] = __ldg(q + e0 * NP + t);
+        }
+    }
+    const int el = threadIdx.x / nn, r = threadIdx.x - el * nn;
+    const int u = r % n, v = r / n;
+    const bool act = el < nel;
+    T *sQ = smem + el * 3 * B::size, *sR = sQ + B::size, *sS = sR + B::size;
+    __syncthreads();
+
+    // derivatives: r-line at (j=u, k=v) and s-line at (i=u, k=v) to shared,
+    // t-line at (i=u, j=v) kept in registers
+    T qt[n];
+    if (act) {
+        T x[n], y[n];
+#pragma unroll
+        for (int l = 0; l < n; l++) x[l] = sQ[B::at(l, u, v)];
+        eo_apply<n, n, -1, C::oD>(x, y);
+#pragma unroll
+        for (int l = 0; l < n; l++) sR[B::at(l, u, v)] = y[l];
+#pragma unroll
+        for (int l = 0; l < n; l++) x[l] = sQ[B::at(u, l, v)];
+        eo_apply<n, n, -1, C::oD>(x, y);
+#pragma unroll
+        for (int l = 0; l < n; l++) sS[B::at(u, l, v)] = y[l];
+#pragma unroll
+        for (int l = 0; l < n; l++) x[l] = sQ[B::at(u, v, l)];
+        eo_apply<n, n, -1, C::oD>(x, qt);
+    }
+    __syncthreads();
+
+    // chain rule at the nodes of column (i=u, j=v), t-transpose in registers
+    T acc[n];
+    const T lam = (T)lambda;
+    if (act) {
+        const T *Ge = G + (e0 + el) * 7 * NP + r;
+        T Rt[n];
+#pragma unroll
+        for (int k = 0; k < n; k++) {
+            const int s = B::at(u, v, k);
+            const T qr = sR[s], qs = sS[s];
+            T g[7];
+#pragma unroll
+            for (int h = 0; h < 7; h++) g[h] = __ldg(Ge + h * NP + k * nn);
+            sR[s] = g[0] * qr + g[1] * qs + g[2] * qt[k];
+            sS[s] = g[1] * qr + g[3] * qs + g[4] * qt[k];
+            Rt[k] = g[2] * qr + g[4] * qs + g[5] * qt[k];
+            acc[k] = (lambda != 0.0) ? (lam * g[6]) * sQ[s] : T(0);
+        }
+        T y[n];
+        eo_apply<n, n, -1, C::oDT>(Rt, y);
+#pragma unroll
+        for (int k = 0; k < n; k++) acc[k] += y[k];
+    }
+    __syncthreads();
+
+    // r- and s-transposes, in place
+    if (act) {
+        T x[n], y[n];
+#pragma unroll
+        for (int l = 0; l < n; l++) x[l] = sR[B::at(l, u, v)];
+        eo_apply<n, n, -1, C::oDT>(x, y);
+#pragma unroll
+        for (int l = 0; l < n; l++) sR[B::at(l, u, v)] = y[l];
+#pragma unroll
+        for (int l = 0; l < n; l++) x[l] = sS[B::at(u, l, v)];
+        eo_apply<n, n, -1, C::oDT>(x, y);
+#pragma unroll
+        for (int l = 0; l < n; l++) sS[B::at(u, l, v)] = y[l];
+    }
+    __syncthreads();
+
+    T dot = T(0);  // p . Ap of the thread's column, in the data's precision
+    if (act) {
+        T *Ae = Aq + (e0 + el) * NP + r;
+#pragma unroll
+        for (int k = 0; k < n; k++) {
+            const int s = B::at(u, v, k);
+            const T w = acc[k] + sR[s] + sS[s];
+            Ae[k * nn] = w;
+            if (PCG) dot = fmx(sQ[s], w, dot);
+        }
+    }
+    if (PCG) {
+        __syncthreads();  // the shared boxes are reused for the reduction
+        const double tot = block_sum((double)dot, reinterpret_cast<double *>(smem_raw));
+        if (threadIdx.x == 0) *part_out = tot;
+    }
+}
+
+}  // namespace
+}  // namespace fem

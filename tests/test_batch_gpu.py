@@ -1,0 +1,119 @@
+"""Batched BP3.5 / BP3.0 over many meshes of mixed degree in one persistent
+launch: every element's result equals the per-mesh call bit for bit, and the
+per-mesh calls equal the oracle; the autotuner and the CUDA-graph replay give
+the same bits."""
+import numpy as np
+import pytest
+
+import fem_synth
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _fem():
+    import paper_1711_00903_gb300 as fem
+    return fem
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def _build(specs, bases):
+    """(items, per-mesh reference outputs) for specs [(op, N, nx, ny, nz, seed)]."""
+    import torch
+    fem = _fem()
+    items, refs = [], []
+    for op, N, nx, ny, nz, seed in specs:
+        b = bases[N]
+        v = fem_synth.box_mesh(nx, ny, nz, jitter=0.1, seed=seed)
+        E = v.shape[0]
+        kind = fem.FEM_GEO_BP35 if op == fem.FEM_OP_BP35 else fem.FEM_GEO_BP30
+        geo = fem.fem_mesh_geofacs(b, kind, _dev(v))
+        q = _dev(fem_synth.field(seed + 1, E, (N + 1) ** 3))
+        out = torch.full_like(q, float("nan"))
+        lam = 0.5 + (seed % 3)
+        ref = (fem.fem_bp35_apply if op == fem.FEM_OP_BP35 else fem.fem_bp30_apply)(b, geo, lam, q)
+        items.append((op, b, geo, lam, q, out))
+        refs.append((ref, v, lam))
+    return items, refs
+
+
+@pytest.fixture(scope="module")
+def bases():
+    fem = _fem()
+    return {N: fem.fem_basis_setup(N) for N in range(1, 11)}
+
+
+def test_mixed_batch_matches_per_mesh_calls_and_oracle(bases):
+    import torch
+    fem = _fem()
+    specs = []
+    for k, N in enumerate([1, 2, 3, 5, 7, 9, 10, 4]):
+        specs.append((fem.FEM_OP_BP35, N, 2, 2, 1 + k % 3, 100 + k))
+        specs.append((fem.FEM_OP_BP30, N, 1, 3, 2, 200 + k))
+    specs.append((fem.FEM_OP_BP35, 6, 1, 1, 1, 300))  # a single element
+    items, refs = _build(specs, bases)
+    batch = fem.Batch(items)
+    batch.apply()
+    torch.cuda.synchronize()
+    for (op, b, geo, lam, q, out), (ref, v, lam2), spec in zip(items, refs, specs):
+        assert torch.equal(out, ref), spec
+    # per-mesh calls against the oracle for a few of them
+    for (op, b, geo, lam, q, out), (ref, v, _), spec in list(zip(items, refs, specs))[:6]:
+        N = b.N
+        if op == fem.FEM_OP_BP35:
+            G, _ = oracle.geofacs(N, oracle.KIND_BP35, v)
+            o = oracle.bp35(N, G, lam, q.cpu().numpy())
+        else:
+            G, _ = oracle.geofacs(N, oracle.KIND_BP30, v)
+            o = oracle.bp30(N, G, lam, q.cpu().numpy())
+        assert np.abs(out.cpu().numpy() - o).max() / np.abs(o).max() < 1e-12
+
+
+def test_tuner_and_graph_replay_keep_the_bits(bases):
+    import torch
+    fem = _fem()
+    specs = [(fem.FEM_OP_BP35 if k % 2 else fem.FEM_OP_BP30, 2 + k % 9, 3, 3, 2, 400 + k) for k in range(12)]
+    items, refs = _build(specs, bases)
+    batch = fem.Batch(items)
+    results = batch.tune(reps=2)
+    assert len(results) == 16 and all(r[3] > 0 for r in results)
+    cfg = batch.config
+    assert cfg["ms"] == min(r[3] for r in results)
+    for _, _, _, _, _, out in items:
+        out.fill_(float("nan"))
+    batch.graph_launch()
+    batch.graph_launch()
+    torch.cuda.synchronize()
+    for (op, b, geo, lam, q, out), (ref, v, _) in zip(items, refs):
+        assert torch.equal(out, ref)
+    # every configuration gives the same bits
+    for threads in (256, 512):
+        for order in (0, 1):
+            batch.config = {"threads": threads, "group": 3, "order": order}
+            for _, _, _, _, _, out in items:
+                out.zero_()
+            batch.apply()
+            torch.cuda.synchronize()
+            for (op, b, geo, lam, q, out), (ref, v, _) in zip(items, refs):
+                assert torch.equal(out, ref)
+
+
+def test_batch_rejects_bad_items(bases):
+    import torch
+    fem = _fem()
+    b11 = fem.fem_basis_setup(11)
+    q = torch.zeros((1, 12 ** 3), dtype=torch.float64, device="cuda")
+    g = torch.zeros((1, 7, 12 ** 3), dtype=torch.float64, device="cuda")
+    with pytest.raises(fem.FemError):
+        fem.Batch([(fem.FEM_OP_BP35, b11, g, 1.0, q, torch.zeros_like(q))])
+    with pytest.raises(fem.FemError):  # output aliasing the input
+        b2 = bases[2]
+        q2 = torch.zeros((1, 27), dtype=torch.float64, device="cuda")
+        fem.Batch([(fem.FEM_OP_BP35, b2, torch.zeros((1, 7, 27), dtype=torch.float64, device="cuda"), 1.0, q2, q2)])
+    empty = fem.Batch([])
+    empty.apply()
+    torch.cuda.synchronize()
