@@ -151,6 +151,15 @@ int fem_bp35_apply_f32(const fem_basis *b, int64_t E, const float *G, double lam
 int fem_bp35_jacobi(const fem_basis *b, int64_t E, const double *G, double lambda,
                     double *dinv, void *stream);
 
+/* Inverse of the diagonal of the BP3.0 operator I^T (Dt^T G Dt + lambda J) I:
+ * with B = I and C = Dt I the gradient of basis function (i,j,k) at Gauss
+ * point (a,b,c) is (C_ai B_bj B_ck, B_ai C_bj B_ck, B_ai B_bj C_ck), and the
+ * diagonal sums g^T G g + lambda wJ (B_ai B_bj B_ck)^2 over the points
+ * (seven sum-factorised projections).  G device E*7*NpG, dinv device E*Np.
+ * Errors: FEM_EINVAL, FEM_ECUDA. */
+int fem_bp30_jacobi(const fem_basis *b, int64_t E, const double *G, double lambda,
+                    double *dinv, void *stream);
+
 /* Deterministic FP64 dot product of two device vectors of n doubles: the
  * result is written to *result (device); scratch is a caller-owned device
  * array of at least fem_dot_scratch_size() doubles (its contents are
@@ -184,9 +193,9 @@ int64_t fem_dot_noalloc_max_n(void);
 int fem_dot_noalloc(int64_t n, const double *x, const double *y, double *result, void *stream);
 
 /* ---------------------------------------------------------------------
- * Jacobi-preconditioned conjugate gradients for the unassembled BP3.5
- * Helmholtz system (D^T G D + lambda J) x = rhs (Section 4; the solver is
- * the textbook PCG with M = diag A).  Two modes:
+ * Jacobi-preconditioned conjugate gradients for the unassembled BP3.5 or
+ * BP3.0 Helmholtz system A x = rhs (Section 4; the solver is the textbook
+ * PCG with M = diag A).  Two modes:
  *   FEM_PCG_FP64   all-FP64 PCG;
  *   FEM_PCG_MIXED  FP64 defect correction: the residual rhs - A x, its norm
  *                  and the update of x in FP64; each correction A d = r
@@ -197,6 +206,9 @@ int fem_dot_noalloc(int64_t n, const double *x, const double *y, double *result,
  * --------------------------------------------------------------------- */
 #define FEM_EBREAKDOWN (-5) /* p.Ap <= 0 or a non-finite value in the recurrence */
 #define FEM_ENOCONV (-6)    /* iteration limit reached; x holds the last iterate */
+
+#define FEM_OP_BP35 2 /* operator selectors of the solver and of batches */
+#define FEM_OP_BP30 3
 
 #define FEM_PCG_FP64 0
 #define FEM_PCG_MIXED 1
@@ -217,12 +229,12 @@ typedef struct {
     double relres; /* ||rhs - A x||_2 / ||rhs||_2 of the returned x, FP64  */
 } fem_pcg_info;
 
-/* Creates a solver for E elements of the handle's degree with operator
- * factors G (device, E*7*Np FP64, must stay valid for the context's life)
- * and lambda >= 0; computes the Jacobi diagonal and, in mixed mode, the
- * FP32 copy of G.  Allocates device memory; synchronous.
- * Errors: FEM_EINVAL, FEM_ENOMEM, FEM_ECUDA. */
-int fem_pcg_create(const fem_basis *b, int64_t E, const double *G, double lambda, int mode,
+/* Creates a solver for E elements of the handle's degree: op FEM_OP_BP35
+ * (factors G device E*7*Np) or FEM_OP_BP30 (E*7*NpG), FP64, which must stay
+ * valid for the context's life, and lambda >= 0; computes the Jacobi
+ * diagonal and, in mixed mode, the FP32 copy of G.  Allocates device memory;
+ * synchronous.  Errors: FEM_EINVAL, FEM_ENOMEM, FEM_ECUDA. */
+int fem_pcg_create(const fem_basis *b, int op, int64_t E, const double *G, double lambda, int mode,
                    fem_pcg **out);
 
 /* Solves A x = rhs starting from the x passed in (device, E*Np doubles;
@@ -246,8 +258,6 @@ void fem_pcg_destroy(fem_pcg *s);
  * independent, so meshes are just more elements).  Each element's result is
  * bit-identical to the per-mesh fem_bp35_apply / fem_bp30_apply call.
  * --------------------------------------------------------------------- */
-#define FEM_OP_BP35 2
-#define FEM_OP_BP30 3
 
 typedef struct {
     int op;                  /* FEM_OP_BP35 or FEM_OP_BP30                       */

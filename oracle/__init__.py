@@ -75,6 +75,9 @@ def lib():
             L.or_bp35_diag.argtypes = [i32, i64, _dp, dbl, _dp]
             L.or_pcg_bp35.argtypes = [i32, i64, _dp, dbl, _dp, _dp, dbl, i32,
                                       C.POINTER(C.c_double)]
+            L.or_bp30_diag.argtypes = [i32, i64, _dp, dbl, _dp]
+            L.or_pcg_bp30.argtypes = [i32, i64, _dp, dbl, _dp, _dp, dbl, i32,
+                                      C.POINTER(C.c_double)]
             _lib = L
     return _lib
 
@@ -237,6 +240,30 @@ def pcg_bp35(N: int, geo: np.ndarray, lam: float, b: np.ndarray, x0=None, tol=1e
     x = np.zeros((E, n ** 3)) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     rel = C.c_double(0.0)
     it = lib().or_pcg_bp35(N, E, _vec(geo, E, 7 * n ** 3), float(lam), _vec(b, E, n ** 3),
+                           x.reshape(-1), float(tol), int(maxit), C.byref(rel))
+    if it < 0:
+        raise RuntimeError(f"oracle PCG failed ({it})")
+    return x, it, rel.value
+
+
+def bp30_diag(N: int, geo: np.ndarray, lam: float) -> np.ndarray:
+    """Diagonal of the BP3.0 operator (Algorithm 5's I^T (Dt^T G Dt +
+    lambda J) I), entry by entry from the gradients of the basis functions
+    at the Gauss points."""
+    n, m = N + 1, N + 2
+    E = geo.shape[0]
+    out = np.zeros((E, n ** 3))
+    assert lib().or_bp30_diag(N, E, _vec(geo, E, 7 * m ** 3), float(lam), out.reshape(-1)) == 0
+    return out
+
+
+def pcg_bp30(N: int, geo: np.ndarray, lam: float, b: np.ndarray, x0=None, tol=1e-10, maxit=10000):
+    """Jacobi-PCG (Saad, Algorithm 9.1) on the unassembled BP3.0 system."""
+    n, m = N + 1, N + 2
+    E = b.shape[0]
+    x = np.zeros((E, n ** 3)) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    rel = C.c_double(0.0)
+    it = lib().or_pcg_bp30(N, E, _vec(geo, E, 7 * m ** 3), float(lam), _vec(b, E, n ** 3),
                            x.reshape(-1), float(tol), int(maxit), C.byref(rel))
     if it < 0:
         raise RuntimeError(f"oracle PCG failed ({it})")

@@ -681,3 +681,94 @@ int or_pcg_bp35(int N, int64_t E, const double *geo, double lambda, const double
     free(dg);
     return status ? status : it;
 }
+
+/* Diagonal of the BP3.0 operator I^T (Dt^T G Dt + lambda J) I (Algorithm 5)
+ * entry by entry: with B = I (B_ai = l_i(rt_a)) and C = Dt I (C_ai =
+ * l_i'(rt_a)) the gradient of basis function (i,j,k) at Gauss point (a,b,c)
+ * is (C_ai B_bj B_ck, B_ai C_bj B_ck, B_ai B_bj C_ck), so
+ *   diag_ijk = sum_abc [ g^T G g + lambda wJ (B_ai B_bj B_ck)^2 ]. */
+int or_bp30_diag(int N, int64_t E, const double *geo, double lambda, double *diag)
+{
+    if (N < 1 || N > OR_MAXN) return -1;
+    int n = N + 1, m = N + 2;
+    int64_t np = (int64_t)n * n * n, mp = (int64_t)m * m * m;
+    double I[OR_MAXQ * OR_MAXQ], Dt[OR_MAXQ * OR_MAXQ], Cm[OR_MAXQ * OR_MAXQ];
+    or_basis(N, NULL, NULL, NULL, NULL, I, NULL, Dt);
+    for (int a = 0; a < m; a++)
+        for (int i = 0; i < n; i++) {
+            double s = 0.0;
+            for (int b = 0; b < m; b++) s += Dt[a * m + b] * I[b * n + i];
+            Cm[a * n + i] = s;
+        }
+#pragma omp parallel for schedule(static)
+    for (int64_t e = 0; e < E; e++) {
+        const double *g = geo + e * 7 * mp;
+        for (int k = 0; k < n; k++)
+            for (int j = 0; j < n; j++)
+                for (int i = 0; i < n; i++) {
+                    double s = 0.0;
+                    for (int c = 0; c < m; c++)
+                        for (int b = 0; b < m; b++)
+                            for (int a = 0; a < m; a++) {
+                                int64_t p = a + m * (b + m * c);
+                                double gr = Cm[a * n + i] * I[b * n + j] * I[c * n + k];
+                                double gs = I[a * n + i] * Cm[b * n + j] * I[c * n + k];
+                                double gt = I[a * n + i] * I[b * n + j] * Cm[c * n + k];
+                                double v = I[a * n + i] * I[b * n + j] * I[c * n + k];
+                                s += g[0 * mp + p] * gr * gr + g[3 * mp + p] * gs * gs + g[5 * mp + p] * gt * gt;
+                                s += 2.0 * (g[1 * mp + p] * gr * gs + g[2 * mp + p] * gr * gt + g[4 * mp + p] * gs * gt);
+                                s += lambda * g[6 * mp + p] * v * v;
+                            }
+                    diag[e * np + i + n * (j + n * k)] = s;
+                }
+    }
+    return 0;
+}
+
+/* Jacobi-preconditioned CG for the BP3.0 system, as or_pcg_bp35. */
+int or_pcg_bp30(int N, int64_t E, const double *geo, double lambda, const double *b, double *x,
+                double tol, int maxit, double *relres)
+{
+    if (N < 1 || N > OR_MAXN || E < 1) return -1;
+    int64_t len = E * (int64_t)(N + 1) * (N + 1) * (N + 1);
+    double *r = malloc(sizeof(double) * len), *z = malloc(sizeof(double) * len);
+    double *p = malloc(sizeof(double) * len), *Ap = malloc(sizeof(double) * len);
+    double *dg = malloc(sizeof(double) * len);
+    int it = 0, status = 0;
+    or_bp30_diag(N, E, geo, lambda, dg);
+    or_bp30(N, E, geo, lambda, x, Ap);
+    for (int64_t i = 0; i < len; i++) r[i] = b[i] - Ap[i];
+    double bn = sqrt(dot(len, b, b));
+    if (bn == 0.0) bn = 1.0;
+    for (int64_t i = 0; i < len; i++) z[i] = r[i] / dg[i];
+    for (int64_t i = 0; i < len; i++) p[i] = z[i];
+    double rz = dot(len, r, z);
+    double rn = sqrt(dot(len, r, r));
+    while (rn > tol * bn && it < maxit) {
+        or_bp30(N, E, geo, lambda, p, Ap);
+        double pAp = dot(len, p, Ap);
+        if (!(pAp > 0.0)) {
+            status = -2;
+            break;
+        }
+        double alpha = rz / pAp;
+        for (int64_t i = 0; i < len; i++) {
+            x[i] += alpha * p[i];
+            r[i] -= alpha * Ap[i];
+        }
+        for (int64_t i = 0; i < len; i++) z[i] = r[i] / dg[i];
+        double rz_new = dot(len, r, z);
+        double beta = rz_new / rz;
+        rz = rz_new;
+        for (int64_t i = 0; i < len; i++) p[i] = z[i] + beta * p[i];
+        rn = sqrt(dot(len, r, r));
+        it++;
+    }
+    if (relres) *relres = rn / bn;
+    free(r);
+    free(z);
+    free(p);
+    free(Ap);
+    free(dg);
+    return status ? status : it;
+}

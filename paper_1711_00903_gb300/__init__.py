@@ -20,7 +20,7 @@ __all__ = [
     "FemError", "lib", "Basis", "fem_version", "fem_basis_setup", "fem_basis_free",
     "fem_basis_tables", "fem_basis_host_tables", "fem_mesh_geofacs", "fem_bp1_apply",
     "fem_bp35_apply", "fem_bp30_apply", "FEM_GEO_BP1", "FEM_GEO_BP35", "FEM_GEO_BP30",
-    "geo_shape", "fem_bp35_apply_f32", "fem_bp35_jacobi", "fem_dot", "fem_dot_scratch_size", "Pcg",
+    "geo_shape", "fem_bp35_apply_f32", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot", "fem_dot_scratch_size", "Pcg",
     "fem_pcg_create", "fem_pcg_solve", "fem_pcg_destroy", "FEM_PCG_FP64", "FEM_PCG_MIXED",
     "Batch", "fem_batch_create", "FEM_OP_BP35", "FEM_OP_BP30",
 ]
@@ -93,7 +93,9 @@ def lib():
             L.fem_bp35_jacobi.argtypes = [vp, i64, dp, dbl, dp, vp]
             L.fem_dot_scratch_size.restype = i64
             L.fem_dot.argtypes = [i64, dp, dp, dp, dp, vp]
-            L.fem_pcg_create.argtypes = [vp, i64, dp, dbl, i32, C.POINTER(vp)]
+            L.fem_pcg_create.argtypes = [vp, i32, i64, dp, dbl, i32, C.POINTER(vp)]
+            L.fem_bp30_jacobi.argtypes = [vp, i64, dp, dbl, dp, vp]
+            L.fem_bp30_jacobi.restype = i32
             L.fem_pcg_solve.argtypes = [vp, dp, dp, C.POINTER(PcgOpts), C.POINTER(PcgInfo), vp]
             L.fem_dot_noalloc_max_n.restype = i64
             L.fem_dot_noalloc.argtypes = [i64, dp, dp, dp, vp]
@@ -113,7 +115,7 @@ def lib():
             L.fem_pcg_destroy.restype = None
             for f in ("fem_basis_setup", "fem_basis_tables", "fem_basis_host_tables",
                       "fem_mesh_geofacs", "fem_bp1_apply", "fem_bp35_apply", "fem_bp30_apply",
-                      "fem_basis_degree", "fem_bp35_apply_f32", "fem_bp35_jacobi", "fem_dot",
+                      "fem_basis_degree", "fem_bp35_apply_f32", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot",
                       "fem_pcg_create", "fem_pcg_solve"):
                 getattr(L, f).restype = i32
             _lib = L
@@ -289,6 +291,19 @@ def fem_bp35_apply_f32(b: Basis, G, lam: float, q, out=None, stream=None):
     return out
 
 
+def fem_bp30_jacobi(b: Basis, G, lam: float, out=None, stream=None):
+    """Inverse diagonal of the BP3.0 operator (Jacobi preconditioner)."""
+    import torch
+    E = G.shape[0]
+    _dev(G, "G", E * 7 * b.m ** 3)
+    if out is None:
+        out = torch.empty((E, b.n ** 3), dtype=torch.float64, device=G.device)
+    _dev(out, "dinv", E * b.n ** 3)
+    _check(lib().fem_bp30_jacobi(b.handle, E, G.data_ptr(), float(lam), out.data_ptr(),
+                                 _stream(stream, G.device)), "fem_bp30_jacobi")
+    return out
+
+
 def fem_bp35_jacobi(b: Basis, G, lam: float, out=None, stream=None):
     """Inverse diagonal of the BP3.5 operator (Jacobi preconditioner)."""
     import torch
@@ -350,12 +365,13 @@ class Pcg:
             pass
 
 
-def fem_pcg_create(b: Basis, G, lam: float, mode: int = FEM_PCG_FP64) -> Pcg:
-    """Jacobi-PCG solver context for the BP3.5 system with factors G."""
+def fem_pcg_create(b: Basis, G, lam: float, mode: int = FEM_PCG_FP64, op: int = FEM_OP_BP35) -> Pcg:
+    """Jacobi-PCG solver context for the BP3.5 (op FEM_OP_BP35) or BP3.0
+    (FEM_OP_BP30) system with factors G."""
     E = G.shape[0]
-    _dev(G, "G", E * 7 * b.n ** 3)
+    _dev(G, "G", E * 7 * (b.n ** 3 if op == FEM_OP_BP35 else b.m ** 3))
     h = C.c_void_p()
-    _check(lib().fem_pcg_create(b.handle, E, G.data_ptr(), float(lam), int(mode), C.byref(h)),
+    _check(lib().fem_pcg_create(b.handle, int(op), E, G.data_ptr(), float(lam), int(mode), C.byref(h)),
            "fem_pcg_create")
     return Pcg(h.value, b, E, G)
 

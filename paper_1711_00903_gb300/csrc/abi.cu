@@ -85,7 +85,7 @@ int fem_basis_setup(int N, fem_basis **out) {
     }
     const fem::HostBasis &h = b->host;
     const fem::OpsLayout L{h.n, h.m};
-    double table[fem::OpsLayout{fem::kMaxQ - 1, fem::kMaxQ}.size()];
+    double table[fem::OpsLayout{fem::kMaxQ - 1, fem::kMaxQ}.size() + 64];
     std::memset(table, 0, sizeof table);
     std::memcpy(table + L.offI(), h.I, sizeof(double) * h.m * h.n);
     std::memcpy(table + L.offD(), h.D, sizeof(double) * h.n * h.n);
@@ -94,6 +94,12 @@ int fem_basis_setup(int N, fem_basis **out) {
     std::memcpy(table + L.offRt(), h.rt, sizeof(double) * h.m);
     std::memcpy(table + L.offW(), h.w, sizeof(double) * h.n);
     std::memcpy(table + L.offWt(), h.wt, sizeof(double) * h.m);
+    for (int a2 = 0; a2 < h.m; a2++)  // C = Dt I
+        for (int i = 0; i < h.n; i++) {
+            double s = 0.0;
+            for (int c = 0; c < h.m; c++) s += h.Dt[a2 * h.m + c] * h.I[c * h.n + i];
+            table[L.offC() + a2 * h.n + i] = s;
+        }
     e = cudaMalloc(&b->d_ops, sizeof(double) * L.size());
     if (e != cudaSuccess) {
         delete b;

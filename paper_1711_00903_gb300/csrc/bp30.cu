@@ -24,36 +24,58 @@
 namespace fem {
 namespace {
 
-template <int N>
-__global__ void __launch_bounds__(Bp30Cfg<N>::threads)
-bp30_f64_kernel(int64_t E, const double *__restrict__ G, double lambda, const double *__restrict__ q,
-                double *__restrict__ Aq) {
-    using C = Bp30Cfg<N>;
-    extern __shared__ double smem[];
+template <typename T, int N, bool PCG>
+__global__ void __launch_bounds__(Bp30Cfg<N, T>::threads)
+bp30_kernel(int64_t E, const T *__restrict__ G, double lambda, const T *__restrict__ q, T *__restrict__ Aq,
+            const T *__restrict__ z, T *__restrict__ p, const double *__restrict__ beta,
+            double *__restrict__ partials) {
+    using C = Bp30Cfg<N, T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t e0 = (int64_t)blockIdx.x * C::EPB;
     const int nel = (int)((E - e0) < C::EPB ? (E - e0) : C::EPB);
-    bp30_block<N, C::EPB>(smem, e0, nel, G, lambda, q, Aq);
+    bp30_block<N, C::EPB, T, PCG>(reinterpret_cast<T *>(smem_raw), e0, nel, G, lambda, q, Aq, z, p, beta,
+                                  PCG ? partials + blockIdx.x : nullptr);
 }
 
 FEM_DEFINE_FOLD_UPLOAD(upload_fold_bp30_tu)
 
+template <typename T, bool PCG>
+struct Bp30LaunchT {
+    template <int N>
+    struct L {
+        static cudaError_t run(int64_t E, const T *G, double lambda, const T *q, T *Aq, const T *z, T *p,
+                               const double *beta, double *partials, cudaStream_t s) {
+            using C = Bp30Cfg<N, T>;
+            const int64_t blocks = (E + C::EPB - 1) / C::EPB;
+            bp30_kernel<T, N, PCG><<<(unsigned)blocks, C::threads, C::smem, s>>>(E, G, lambda, q, Aq, z, p, beta,
+                                                                                partials);
+            return cudaGetLastError();
+        }
+    };
+};
+
 template <int N>
-struct Bp30Launch {
-    static cudaError_t run(const fem_basis *b, int64_t E, const double *G, double lambda, const double *q,
-                           double *Aq, cudaStream_t s) {
-        using C = Bp30Cfg<N>;
-        (void)b;
-        const int64_t blocks = (E + C::EPB - 1) / C::EPB;
-        bp30_f64_kernel<N><<<(unsigned)blocks, C::threads, C::smem, s>>>(E, G, lambda, q, Aq);
-        return cudaGetLastError();
+struct Bp30Blocks {
+    static cudaError_t run(int64_t E, bool f32, int64_t *out) {
+        const int epb = f32 ? Bp30Cfg<N, float>::EPB : Bp30Cfg<N, double>::EPB;
+        *out = (E + epb - 1) / epb;
+        return cudaSuccess;
     }
 };
 
 template <int N>
 struct Bp30Prepare {
+    template <typename T, bool PCG>
+    static cudaError_t one() {
+        return cudaFuncSetAttribute(bp30_kernel<T, N, PCG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    Bp30Cfg<N, T>::smem);
+    }
     static cudaError_t run() {
-        return cudaFuncSetAttribute(bp30_f64_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    Bp30Cfg<N>::smem);
+        cudaError_t e = one<double, false>();
+        if (e == cudaSuccess) e = one<double, true>();
+        if (e == cudaSuccess) e = one<float, false>();
+        if (e == cudaSuccess) e = one<float, true>();
+        return e;
     }
 };
 
@@ -61,7 +83,34 @@ struct Bp30Prepare {
 
 cudaError_t launch_bp30(const fem_basis *b, int64_t E, const double *G, double lambda, const double *q,
                         double *Aq, cudaStream_t s) {
-    return dispatch_degree<Bp30Launch>(b->host.N, b, E, G, lambda, q, Aq, s);
+    return dispatch_degree<Bp30LaunchT<double, false>::L>(b->host.N, E, G, lambda, q, Aq, (const double *)nullptr,
+                                                           (double *)nullptr, (const double *)nullptr,
+                                                           (double *)nullptr, s);
+}
+
+cudaError_t launch_bp30_f32(const fem_basis *b, int64_t E, const float *G, double lambda, const float *q,
+                            float *Aq, cudaStream_t s) {
+    return dispatch_degree<Bp30LaunchT<float, false>::L>(b->host.N, E, G, lambda, q, Aq, (const float *)nullptr,
+                                                          (float *)nullptr, (const double *)nullptr,
+                                                          (double *)nullptr, s);
+}
+
+cudaError_t launch_bp30_pcg(const fem_basis *b, int64_t E, const double *G, double lambda, const double *z,
+                            double *p, const double *beta, double *Ap, double *partials, cudaStream_t s) {
+    return dispatch_degree<Bp30LaunchT<double, true>::L>(b->host.N, E, G, lambda, (const double *)nullptr, Ap, z, p,
+                                                          beta, partials, s);
+}
+
+cudaError_t launch_bp30_pcg_f32(const fem_basis *b, int64_t E, const float *G, double lambda, const float *z,
+                                float *p, const double *beta, float *Ap, double *partials, cudaStream_t s) {
+    return dispatch_degree<Bp30LaunchT<float, true>::L>(b->host.N, E, G, lambda, (const float *)nullptr, Ap, z, p,
+                                                         beta, partials, s);
+}
+
+int64_t bp30_blocks(int N, int64_t E, bool f32) {
+    int64_t out = 0;
+    dispatch_degree<Bp30Blocks>(N, E, f32, &out);
+    return out;
 }
 
 cudaError_t prepare_bp30(int N, const double *fold_table) {

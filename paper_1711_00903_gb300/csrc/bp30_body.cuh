@@ -8,8 +8,10 @@
 namespace fem {
 namespace {
 
-// Layout of one block of EPB elements (three m^3 shared boxes each).
-template <int N, int EPB_>
+// Layout of one block of EPB elements (three m^3 shared boxes each), data
+// type T (double for the paper's FP64 operator, float for the inner operator
+// of the mixed-precision solver).
+template <int N, int EPB_, typename T = double>
 struct Bp30Layout {
     static constexpr int n = N + 1, m = N + 2;
     static constexpr int NP = n * n * n, MP = m * m * m, mm = m * m;
@@ -21,22 +23,30 @@ struct Bp30Layout {
     static constexpr int per = 3 * S;
     static constexpr int EPB = EPB_;
     static constexpr int threads = ((mm * EPB + 31) / 32) * 32;  // the block needs at least this many
-    static constexpr int smem = EPB * per * 8;
+    static constexpr int bytes = EPB * per * (int)sizeof(T);
+    static constexpr int smem = bytes > threads * 8 ? bytes : threads * 8;
+    static constexpr bool PREFETCH = sizeof(T) == 4;  // see bp35_body.cuh
     static constexpr int oI = fold_offset(N, kFoldI), oIT = fold_offset(N, kFoldIT);
     static constexpr int oDt = fold_offset(N, kFoldDt), oDtT = fold_offset(N, kFoldDtT);
 };
 
 // Elements per block of the stand-alone kernel: as many as fit 256 threads
 // under the shared-memory budget.
-template <int N>
-struct Bp30Cfg : Bp30Layout<N, pick_epb(N + 2, 3 * Box<N + 2, N + 2, N + 2>::size * 8)> {};
+template <int N, typename T = double>
+struct Bp30Cfg : Bp30Layout<N, pick_epb(N + 2, 3 * Box<N + 2, N + 2, N + 2>::size * (int)sizeof(T)), T> {};
 
 // BP3.0 of elements [e0, e0 + nel) (nel <= EPB) by the whole block
-// (blockDim.x >= Layout::threads), shared memory at smem (Layout::smem bytes).
-template <int N, int EPB_>
-__device__ __forceinline__ void bp30_block(double *smem, int64_t e0, int nel, const double *__restrict__ G,
-                                           double lambda, const double *__restrict__ q, double *__restrict__ Aq) {
-    using C = Bp30Layout<N, EPB_>;
+// (blockDim.x >= Layout::threads), shared memory at smem (Layout::smem
+// bytes).  PCG = true: the input field is p <- z + beta p (stored back to p;
+// beta read from *beta, p not read when beta is 0), and thread 0 writes the
+// block's p . Ap to *part_out.
+template <int N, int EPB_, typename T = double, bool PCG = false>
+__device__ __forceinline__ void bp30_block(T *smem, int64_t e0, int nel, const T *__restrict__ G, double lambda,
+                                           const T *__restrict__ q, T *__restrict__ Aq,
+                                           const T *__restrict__ z = nullptr, T *__restrict__ p = nullptr,
+                                           const double *__restrict__ beta = nullptr,
+                                           double *__restrict__ part_out = nullptr) {
+    using C = Bp30Layout<N, EPB_, T>;
     using B0 = typename C::B0;
     using B1 = typename C::B1;
     using B2 = typename C::B2;
@@ -44,18 +54,31 @@ __device__ __forceinline__ void bp30_block(double *smem, int64_t e0, int nel, co
     constexpr int n = C::n, m = C::m, NP = C::NP, MP = C::MP, mm = C::mm, EPB = C::EPB;
     constexpr int S = C::S, per = C::per;
     // per element: buffer A = smem + el*per, B = A + S, C = A + 2S
-    for (int t = threadIdx.x; t < nel * NP; t += blockDim.x) {
-        const int el = t / NP, p = t - el * NP;
-        smem[el * per + S + B0::at(p % n, (p / n) % n, p / (n * n))] = __ldg(q + e0 * NP + t);
+    if (C::PREFETCH && threadIdx.x == 0)
+        prefetch_l2(G + e0 * 7 * MP, (long long)nel * 7 * MP * (long long)sizeof(T));
+    if (PCG) {
+        const T bt = (T)(*beta);
+        for (int t = threadIdx.x; t < nel * NP; t += blockDim.x) {
+            const int el = t / NP, s = t - el * NP;
+            const int64_t g = e0 * NP + t;
+            const T v = (bt == T(0)) ? z[g] : fmx(bt, p[g], z[g]);
+            p[g] = v;
+            smem[el * per + S + B0::at(s % n, (s / n) % n, s / (n * n))] = v;
+        }
+    } else {
+        for (int t = threadIdx.x; t < nel * NP; t += blockDim.x) {
+            const int el = t / NP, s = t - el * NP;
+            smem[el * per + S + B0::at(s % n, (s / n) % n, s / (n * n))] = __ldg(q + e0 * NP + t);
+        }
     }
     __syncthreads();
 
     // 1. r-interpolation (j, k): q (buffer B) -> X1 (buffer C)
     for_tasks<n * n, EPB>(nel, [&](int el, int r) {
         const int j = r % n, k = r / n;
-        const double *X0 = smem + el * per + S;
-        double *X1 = smem + el * per + 2 * S;
-        double x[n], y[m];
+        const T *X0 = smem + el * per + S;
+        T *X1 = smem + el * per + 2 * S;
+        T x[n], y[m];
 #pragma unroll
         for (int l = 0; l < n; l++) x[l] = X0[B0::at(l, j, k)];
         eo_apply<m, n, 1, C::oI>(x, y);
@@ -67,9 +90,9 @@ __device__ __forceinline__ void bp30_block(double *smem, int64_t e0, int nel, co
     // 2. s-interpolation (a, k): X1 (C) -> X2 (B)
     for_tasks<m * n, EPB>(nel, [&](int el, int r) {
         const int a = r % m, k = r / m;
-        const double *X1 = smem + el * per + 2 * S;
-        double *X2 = smem + el * per + S;
-        double x[n], y[m];
+        const T *X1 = smem + el * per + 2 * S;
+        T *X2 = smem + el * per + S;
+        T x[n], y[m];
 #pragma unroll
         for (int l = 0; l < n; l++) x[l] = X1[B1::at(a, l, k)];
         eo_apply<m, n, 1, C::oI>(x, y);
@@ -81,9 +104,9 @@ __device__ __forceinline__ void bp30_block(double *smem, int64_t e0, int nel, co
     // 3. t-interpolation (a, b): X2 (B) -> QG (A)
     for_tasks<mm, EPB>(nel, [&](int el, int r) {
         const int a = r % m, b = r / m;
-        const double *X2 = smem + el * per + S;
-        double *QG = smem + el * per;
-        double x[n], y[m];
+        const T *X2 = smem + el * per + S;
+        T *QG = smem + el * per;
+        T x[n], y[m];
 #pragma unroll
         for (int l = 0; l < n; l++) x[l] = X2[B2::at(a, b, l)];
         eo_apply<m, n, 1, C::oI>(x, y);
@@ -95,9 +118,9 @@ __device__ __forceinline__ void bp30_block(double *smem, int64_t e0, int nel, co
     // 4. r-derivative lines (b=u, c=v) -> UR (B), s-derivative lines (a=u, c=v) -> US (C)
     for_tasks<mm, EPB>(nel, [&](int el, int r) {
         const int u = r % m, v = r / m;
-        const double *QG = smem + el * per;
-        double *UR = smem + el * per + S, *US = smem + el * per + 2 * S;
-        double x[m], y[m];
+        const T *QG = smem + el * per;
+        T *UR = smem + el * per + S, *US = smem + el * per + 2 * S;
+        T x[m], y[m];
 #pragma unroll
         for (int l = 0; l < m; l++) x[l] = QG[B3::at(l, u, v)];
         eo_apply<m, m, -1, C::oDt>(x, y);
@@ -117,28 +140,28 @@ __device__ __forceinline__ void bp30_block(double *smem, int64_t e0, int nel, co
     const int cel = threadIdx.x / mm, cr = threadIdx.x - cel * mm;
     const int ca = cr % m, cb = cr / m;
     const bool cact = cel < nel;
-    double acc[m];
+    T acc[m];
     if (cact) {
-        const double *QG = smem + cel * per;
-        double *UR = smem + cel * per + S, *US = smem + cel * per + 2 * S;
-        double x[m], ut[m], Rt[m];
+        const T *QG = smem + cel * per;
+        T *UR = smem + cel * per + S, *US = smem + cel * per + 2 * S;
+        T x[m], ut[m], Rt[m];
 #pragma unroll
         for (int l = 0; l < m; l++) x[l] = QG[B3::at(ca, cb, l)];
         eo_apply<m, m, -1, C::oDt>(x, ut);
-        const double *Ge = G + (e0 + cel) * 7 * MP + cr;
+        const T *Ge = G + (e0 + cel) * 7 * MP + cr;
 #pragma unroll
         for (int c = 0; c < m; c++) {
             const int s = B3::at(ca, cb, c);
-            const double ur = UR[s], us = US[s];
-            double g[7];
+            const T ur = UR[s], us = US[s];
+            T g[7];
 #pragma unroll
             for (int h = 0; h < 7; h++) g[h] = __ldg(Ge + h * MP + c * mm);
             UR[s] = g[0] * ur + g[1] * us + g[2] * ut[c];
             US[s] = g[1] * ur + g[3] * us + g[4] * ut[c];
             Rt[c] = g[2] * ur + g[4] * us + g[5] * ut[c];
-            acc[c] = (lambda != 0.0) ? (lambda * g[6]) * x[c] : 0.0;
+            acc[c] = (lambda != 0.0) ? ((T)lambda * g[6]) * x[c] : T(0);
         }
-        double y[m];
+        T y[m];
         eo_apply<m, m, -1, C::oDtT>(Rt, y);
 #pragma unroll
         for (int c = 0; c < m; c++) acc[c] += y[c];
@@ -148,8 +171,8 @@ __device__ __forceinline__ void bp30_block(double *smem, int64_t e0, int nel, co
     // 6. r- and s-transposes in place
     for_tasks<mm, EPB>(nel, [&](int el, int r) {
         const int u = r % m, v = r / m;
-        double *UR = smem + el * per + S, *US = smem + el * per + 2 * S;
-        double x[m], y[m];
+        T *UR = smem + el * per + S, *US = smem + el * per + 2 * S;
+        T x[m], y[m];
 #pragma unroll
         for (int l = 0; l < m; l++) x[l] = UR[B3::at(l, u, v)];
         eo_apply<m, m, -1, C::oDtT>(x, y);
@@ -165,9 +188,9 @@ __device__ __forceinline__ void bp30_block(double *smem, int64_t e0, int nel, co
 
     // 7. column (a, b): sum of the three directions, t-projection -> X3 (A)
     if (cact) {
-        const double *UR = smem + cel * per + S, *US = smem + cel * per + 2 * S;
-        double *X3 = smem + cel * per;
-        double y[n];
+        const T *UR = smem + cel * per + S, *US = smem + cel * per + 2 * S;
+        T *X3 = smem + cel * per;
+        T y[n];
 #pragma unroll
         for (int c = 0; c < m; c++) {
             const int s = B3::at(ca, cb, c);
@@ -182,9 +205,9 @@ __device__ __forceinline__ void bp30_block(double *smem, int64_t e0, int nel, co
     // 8. s-projection (a, k): X3 (A) -> X4 (B)
     for_tasks<m * n, EPB>(nel, [&](int el, int r) {
         const int a = r % m, k = r / m;
-        const double *X3 = smem + el * per;
-        double *X4 = smem + el * per + S;
-        double x[m], y[n];
+        const T *X3 = smem + el * per;
+        T *X4 = smem + el * per + S;
+        T x[m], y[n];
 #pragma unroll
         for (int l = 0; l < m; l++) x[l] = X3[B2::at(a, l, k)];
         eo_apply<n, m, 1, C::oIT>(x, y);
@@ -194,17 +217,28 @@ __device__ __forceinline__ void bp30_block(double *smem, int64_t e0, int nel, co
     __syncthreads();
 
     // 9. r-projection (j, k): X4 (B) -> Aq
+    T dot = T(0);  // p . Ap of the thread's lines (PCG), in the data's precision
     for_tasks<n * n, EPB>(nel, [&](int el, int r) {
-        const double *X4 = smem + el * per + S;
+        const T *X4 = smem + el * per + S;
         const int j = r % n, k = r / n;
-        double x[m], y[n];
+        T x[m], y[n];
 #pragma unroll
         for (int l = 0; l < m; l++) x[l] = X4[B1::at(l, j, k)];
         eo_apply<n, m, 1, C::oIT>(x, y);
-        double *o = Aq + (e0 + el) * NP + r * n;
+        T *o = Aq + (e0 + el) * NP + r * n;
 #pragma unroll
         for (int l = 0; l < n; l++) o[l] = y[l];
+        if (PCG) {
+            const T *pp = p + (e0 + el) * NP + r * n;  // written by this block's staging
+#pragma unroll
+            for (int l = 0; l < n; l++) dot = fmx(pp[l], y[l], dot);
+        }
     });
+    if (PCG) {
+        __syncthreads();  // the shared boxes are reused for the reduction
+        const double tot = block_sum((double)dot, reinterpret_cast<double *>(smem));
+        if (threadIdx.x == 0) *part_out = tot;
+    }
 }
 
 }  // namespace

@@ -25,7 +25,9 @@ struct OpsLayout {
     __host__ __device__ constexpr int offRt() const { return total() + kMaxQ; }
     __host__ __device__ constexpr int offW() const { return total() + 2 * kMaxQ; }
     __host__ __device__ constexpr int offWt() const { return total() + 3 * kMaxQ; }
-    __host__ __device__ constexpr int size() const { return total() + 4 * kMaxQ; }
+    // C = Dt I (m x n): derivatives of the GLL basis at the Gauss points
+    __host__ __device__ constexpr int offC() const { return total() + 4 * kMaxQ; }
+    __host__ __device__ constexpr int size() const { return total() + 4 * kMaxQ + m * n; }
 };
 
 // Host basis: nodes, weights and operator matrices of degree N.
@@ -72,6 +74,15 @@ const double *fold_table();
 // Records the text of a CUDA error for fem_last_cuda_error() and maps it to
 // FEM_ECUDA or FEM_ENODEV.
 int record_cuda_error(cudaError_t e);
+
+// BP3.0 launchers for the solver (FP32 plain and both PCG-fused variants).
+cudaError_t launch_bp30_f32(const fem_basis *b, int64_t E, const float *G, double lambda, const float *q,
+                            float *Aq, cudaStream_t s);
+cudaError_t launch_bp30_pcg(const fem_basis *b, int64_t E, const double *G, double lambda, const double *z,
+                            double *p, const double *beta, double *Ap, double *partials, cudaStream_t s);
+cudaError_t launch_bp30_pcg_f32(const fem_basis *b, int64_t E, const float *G, double lambda, const float *z,
+                                float *p, const double *beta, float *Ap, double *partials, cudaStream_t s);
+int64_t bp30_blocks(int N, int64_t E, bool f32);
 
 // FP32 BP3.5 matvec (the inner operator of the mixed-precision solver).
 cudaError_t launch_bp35_f32(const fem_basis *b, int64_t E, const float *G, double lambda, const float *q,

@@ -17,6 +17,7 @@
 // p <- z + beta p and the p.Ap partial sums, a reduction, the fused update
 // x += alpha p, r -= alpha Ap, z = r / diag with the r.z and r.r partial
 // sums, and a reduction.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -78,6 +79,92 @@ bp35_dinv_kernel(int64_t E, const double *__restrict__ ops, const double *__rest
         if (dinv) dinv[g] = v;
         if (dinv32) dinv32[g] = (float)v;
     }
+}
+
+// Inverse diagonal of the BP3.0 operator I^T (Dt^T G Dt + lambda J) I.  With
+// B = I and C = Dt I (m x n), the gradient of basis function (i,j,k) at Gauss
+// point (a,b,c) is (C_ai B_bj B_ck, B_ai C_bj B_ck, B_ai B_bj C_ck), so the
+// diagonal is a sum of seven sum-factorised projections
+//   sum_abc X_ai Y_bj Z_ck F_abc,  X, Y, Z in {P = B*B, Q = C*C, R = B*C}
+// (elementwise products) of the factor planes F.  One element per block
+// (grid-stride), FP64.
+template <int N>
+__global__ void __launch_bounds__(256)
+bp30_dinv_kernel(int64_t E, const double *__restrict__ ops, const double *__restrict__ G, double lambda,
+                 double *__restrict__ dinv, float *__restrict__ dinv32) {
+    constexpr int n = N + 1, m = N + 2, NP = n * n * n, MP = m * m * m, mn = m * n;
+    extern __shared__ double sm[];
+    double *sP = sm, *sQ = sP + mn, *sR = sQ + mn;
+    double *F = sR + mn, *T1 = F + MP, *T2 = T1 + m * m * n;
+    const OpsLayout L{n, m};
+    for (int t = threadIdx.x; t < mn; t += blockDim.x) {
+        const double b = ops[L.offI() + t], c = ops[L.offC() + t];
+        sP[t] = b * b;
+        sQ[t] = c * c;
+        sR[t] = b * c;
+    }
+    // terms: X (along r), Y (along s), Z (along t), factor plane, coefficient
+    const double *X[7] = {sQ, sP, sP, sR, sR, sP, sP};
+    const double *Y[7] = {sP, sQ, sP, sR, sP, sR, sP};
+    const double *Z[7] = {sP, sP, sQ, sP, sR, sR, sP};
+    const int plane[7] = {0, 3, 5, 1, 2, 4, 6};
+    const double coef[7] = {1.0, 1.0, 1.0, 2.0, 2.0, 2.0, lambda};
+    const int jk = threadIdx.x, j = jk % n, k = jk / n;  // output line (j, k), i along it
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+        double out[n];
+#pragma unroll
+        for (int i = 0; i < n; i++) out[i] = 0.0;
+        for (int term = 0; term < 7; term++) {
+            __syncthreads();
+            const double *Fe = G + (e * 7 + plane[term]) * MP;
+            for (int t = threadIdx.x; t < MP; t += blockDim.x) F[t] = Fe[t];
+            __syncthreads();
+            // T1[a][b][k] = sum_c Z_ck F[a][b][c]
+            for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+                const int a = t % m, b = t / m;
+                for (int kk = 0; kk < n; kk++) {
+                    double acc = 0.0;
+                    for (int c = 0; c < m; c++) acc = fma(Z[term][c * n + kk], F[a + m * (b + m * c)], acc);
+                    T1[a + m * (b + m * kk)] = acc;
+                }
+            }
+            __syncthreads();
+            // T2[a][j][k] = sum_b Y_bj T1[a][b][k]
+            for (int t = threadIdx.x; t < m * n; t += blockDim.x) {
+                const int a = t % m, kk = t / m;
+                for (int jj = 0; jj < n; jj++) {
+                    double acc = 0.0;
+                    for (int b = 0; b < m; b++) acc = fma(Y[term][b * n + jj], T1[a + m * (b + m * kk)], acc);
+                    T2[a + m * (jj + n * kk)] = acc;
+                }
+            }
+            __syncthreads();
+            if (jk < n * n) {
+#pragma unroll
+                for (int i = 0; i < n; i++) {
+                    double acc = 0.0;
+                    for (int a = 0; a < m; a++) acc = fma(X[term][a * n + i], T2[a + m * (j + n * k)], acc);
+                    out[i] = fma(coef[term], acc, out[i]);
+                }
+            }
+        }
+        if (jk < n * n) {
+#pragma unroll
+            for (int i = 0; i < n; i++) {
+                const int64_t g = e * NP + i + n * (j + n * k);
+                const double v = 1.0 / out[i];
+                if (dinv) dinv[g] = v;
+                if (dinv32) dinv32[g] = (float)v;
+            }
+        }
+    }
+}
+
+template <int N>
+constexpr int bp30_dinv_smem() {
+    return (3 * (N + 2) * (N + 1) + (N + 2) * (N + 2) * (N + 2) + (N + 2) * (N + 2) * (N + 1) +
+            (N + 2) * (N + 1) * (N + 1)) *
+           8;
 }
 
 __global__ void __launch_bounds__(kVecThreads) cast_f32_kernel(int64_t n, const double *__restrict__ a,
@@ -298,6 +385,19 @@ struct DinvLaunch {
     }
 };
 
+template <int N>
+struct Dinv30Launch {
+    static cudaError_t run(const fem_basis *b, int64_t E, const double *G, double lambda, double *dinv, float *dinv32,
+                           cudaStream_t s) {
+        constexpr int smem = bp30_dinv_smem<N>();
+        cudaError_t e = cudaFuncSetAttribute(bp30_dinv_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        const int64_t blocks = E < 152 * 4 ? E : 152 * 4;
+        bp30_dinv_kernel<N><<<(unsigned)blocks, 256, smem, s>>>(E, b->d_ops, G, lambda, dinv, dinv32);
+        return cudaGetLastError();
+    }
+};
+
 int64_t dot_scratch_size() { return kVecBlocks; }
 
 cudaError_t launch_dot(int64_t n, const double *x, const double *y, double *result, double *scratch,
@@ -313,6 +413,8 @@ cudaError_t launch_dot(int64_t n, const double *x, const double *y, double *resu
 
 struct fem_pcg {
     const fem_basis *basis;
+    int op;        // FEM_OP_BP35 or FEM_OP_BP30
+    int64_t gpts;  // factor points per element (n^3 or m^3)
     int64_t E, len;
     const double *G;
     double lambda;
@@ -339,6 +441,25 @@ cudaError_t launch_bp35(const fem_basis *b, int64_t E, const double *G, double l
 
 namespace {
 
+// Operator dispatch of the solver.
+cudaError_t op_apply64(fem_pcg *s, const double *x, double *out, cudaStream_t st) {
+    return s->op == FEM_OP_BP30 ? launch_bp30(s->basis, s->E, s->G, s->lambda, x, out, st)
+                                : launch_bp35(s->basis, s->E, s->G, s->lambda, x, out, st);
+}
+int64_t op_blocks(const fem_pcg *s, bool f32) {
+    return s->op == FEM_OP_BP30 ? bp30_blocks(s->basis->host.N, s->E, f32) : bp35_blocks(s->basis->host.N, s->E, f32);
+}
+cudaError_t op_pcg(fem_pcg *s, const double *G, const double *z, double *p, double *Ap, cudaStream_t st) {
+    return s->op == FEM_OP_BP30
+               ? launch_bp30_pcg(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, s->part, st)
+               : launch_bp35_pcg(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, s->part, st);
+}
+cudaError_t op_pcg(fem_pcg *s, const float *G, const float *z, float *p, float *Ap, cudaStream_t st) {
+    return s->op == FEM_OP_BP30
+               ? launch_bp30_pcg_f32(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, s->part, st)
+               : launch_bp35_pcg_f32(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, s->part, st);
+}
+
 template <typename P>
 cudaError_t alloc(P **ptr, int64_t count) {
     return cudaMalloc((void **)ptr, sizeof(P) * (size_t)(count > 0 ? count : 1));
@@ -355,7 +476,7 @@ cudaError_t sync_scalars(fem_pcg *s, cudaStream_t st) {
 cudaError_t pcg_create(fem_pcg *s) {
     cudaError_t e = cudaSuccess;
     const int64_t len = s->len;
-    s->nparts = bp35_max_blocks(s->basis->host.N, s->E);
+    s->nparts = std::max(op_blocks(s, false), op_blocks(s, true));
     if (s->nparts < 3 * (int64_t)kVecBlocks) s->nparts = 3 * (int64_t)kVecBlocks;
     if (e == cudaSuccess) e = alloc(&s->part, 3 * s->nparts);
     if (e == cudaSuccess) e = alloc(&s->scal, S_COUNT);
@@ -367,7 +488,7 @@ cudaError_t pcg_create(fem_pcg *s) {
         if (e == cudaSuccess) e = alloc(&s->p, len);
         if (e == cudaSuccess) e = alloc(&s->dinv, len);
     } else {
-        if (e == cudaSuccess) e = alloc(&s->G32, 7 * len);
+        if (e == cudaSuccess) e = alloc(&s->G32, 7 * s->E * s->gpts);
         if (e == cudaSuccess) e = alloc(&s->dinv32, len);
         if (e == cudaSuccess) e = alloc(&s->d32, len);
         if (e == cudaSuccess) e = alloc(&s->r32, len);
@@ -378,10 +499,14 @@ cudaError_t pcg_create(fem_pcg *s) {
     if (e != cudaSuccess) return e;
     e = cudaMemset(s->scal, 0, sizeof(double) * S_COUNT);
     if (e != cudaSuccess) return e;
-    e = dispatch_degree<DinvLaunch>(s->basis->host.N, s->basis, s->E, s->G, s->lambda, s->dinv, s->dinv32,
-                                    (cudaStream_t)0);
+    if (s->op == FEM_OP_BP30)
+        e = dispatch_degree<Dinv30Launch>(s->basis->host.N, s->basis, s->E, s->G, s->lambda, s->dinv, s->dinv32,
+                                          (cudaStream_t)0);
+    else
+        e = dispatch_degree<DinvLaunch>(s->basis->host.N, s->basis, s->E, s->G, s->lambda, s->dinv, s->dinv32,
+                                        (cudaStream_t)0);
     if (e == cudaSuccess && s->mode != FEM_PCG_FP64)
-        cast_f32_kernel<<<kVecBlocks, kVecThreads>>>(7 * len, s->G, s->G32);
+        cast_f32_kernel<<<kVecBlocks, kVecThreads>>>(7 * s->E * s->gpts, s->G, s->G32);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     return e;
@@ -407,15 +532,10 @@ static cudaError_t pcg_loop(fem_pcg *s, const T *G, XT *x, T *p, T *r, T *Ap, T 
         int chunk = every;
         if (chunk > maxit - done_it) chunk = maxit - done_it;
         for (int c = 0; c < chunk && e == cudaSuccess; c++) {
-            if (sizeof(T) == 8)
-                e = launch_bp35_pcg(s->basis, s->E, (const double *)G, s->lambda, (const double *)z, (double *)p,
-                                    s->scal + S_BETA, (double *)Ap, s->part, st);
-            else
-                e = launch_bp35_pcg_f32(s->basis, s->E, (const float *)G, s->lambda, (const float *)z, (float *)p,
-                                        s->scal + S_BETA, (float *)Ap, s->part, st);
+            e = op_pcg(s, G, z, p, Ap, st);
             if (e != cudaSuccess) break;
-            reduce_kernel<<<1, kRedThreads, 0, st>>>(R_PQ, bp35_blocks(s->basis->host.N, s->E, sizeof(T) == 4), s->part,
-                                                     s->scal, nullptr, 0.0);
+            reduce_kernel<<<1, kRedThreads, 0, st>>>(R_PQ, op_blocks(s, sizeof(T) == 4), s->part, s->scal, nullptr,
+                                                     0.0);
             if (sizeof(T) == 4 && sizeof(XT) == 4 && len % 4 == 0)
                 update_f32x4_kernel<<<kVecBlocks, kVecThreads, 0, st>>>(
                     len / 4, s->scal, (float4 *)x, (const float4 *)p, (float4 *)r, (const float4 *)Ap, (float4 *)z,
@@ -459,7 +579,7 @@ int pcg_solve(fem_pcg *s, const double *b, double *x, const fem_pcg_opts *o, fem
         return e == cudaSuccess ? FEM_OK : -2;
     }
     if (s->mode == FEM_PCG_FP64) {
-        e = launch_bp35(s->basis, s->E, s->G, s->lambda, x, s->q, st);
+        e = op_apply64(s, x, s->q, st);
         if (e == cudaSuccess) {
             init_kernel<<<kVecBlocks, kVecThreads, 0, st>>>(len, b, s->q, s->r, s->z, s->dinv, s->part);
             reduce_kernel<<<1, kRedThreads, 0, st>>>(R_INIT, kVecBlocks, s->part, s->scal, nullptr, tol * tol);
@@ -476,7 +596,7 @@ int pcg_solve(fem_pcg *s, const double *b, double *x, const fem_pcg_opts *o, fem
         const int max_outer = 64;
         int outer = 0;
         for (; outer < max_outer; outer++) {
-            e = launch_bp35(s->basis, s->E, s->G, s->lambda, x, s->q, st);
+            e = op_apply64(s, x, s->q, st);
             if (e != cudaSuccess) break;
             outer_kernel<<<kVecBlocks, kVecThreads, 0, st>>>(len, b, s->q, s->r32, s->z32, s->d32, s->dinv32, s->part);
             reduce_kernel<<<1, kRedThreads, 0, st>>>(R_OUTER, kVecBlocks, s->part, s->scal, nullptr, itol * itol);
@@ -507,7 +627,7 @@ int pcg_solve(fem_pcg *s, const double *b, double *x, const fem_pcg_opts *o, fem
         loc.outer = outer;
     }
     // true FP64 residual of the returned x
-    e = launch_bp35(s->basis, s->E, s->G, s->lambda, x, s->q, st);
+    e = op_apply64(s, x, s->q, st);
     if (e == cudaSuccess && s->mode == FEM_PCG_FP64) {
         init_kernel<<<kVecBlocks, kVecThreads, 0, st>>>(len, b, s->q, s->r, s->z, s->dinv, s->part);
         reduce_kernel<<<1, kRedThreads, 0, st>>>(R_TRUE, kVecBlocks, s->part, s->scal, nullptr, 0.0);
@@ -548,14 +668,26 @@ int fem_bp35_jacobi(const fem_basis *b, int64_t E, const double *G, double lambd
     return e == cudaSuccess ? FEM_OK : fem::record_cuda_error(e);
 }
 
-int fem_pcg_create(const fem_basis *b, int64_t E, const double *G, double lambda, int mode, fem_pcg **out) {
+int fem_bp30_jacobi(const fem_basis *b, int64_t E, const double *G, double lambda, double *dinv, void *stream) {
+    if (!b || E < 0) return FEM_EINVAL;
+    if (E == 0) return FEM_OK;
+    if (!G || !dinv) return FEM_EINVAL;
+    cudaError_t e = fem::dispatch_degree<fem::Dinv30Launch>(b->host.N, b, E, G, lambda, dinv, (float *)nullptr,
+                                                            (cudaStream_t)stream);
+    return e == cudaSuccess ? FEM_OK : fem::record_cuda_error(e);
+}
+
+int fem_pcg_create(const fem_basis *b, int op, int64_t E, const double *G, double lambda, int mode, fem_pcg **out) {
     if (!b || !out || E < 1 || !G || (mode != FEM_PCG_FP64 && mode != FEM_PCG_MIXED)) return FEM_EINVAL;
+    if (op != FEM_OP_BP35 && op != FEM_OP_BP30) return FEM_EINVAL;
     if (!(lambda >= 0.0)) return FEM_EINVAL;
     *out = nullptr;
     fem_pcg *s = new (std::nothrow) fem_pcg();
     if (!s) return FEM_ENOMEM;
     std::memset(s, 0, sizeof(*s));
     s->basis = b;
+    s->op = op;
+    s->gpts = (op == FEM_OP_BP30) ? (int64_t)b->host.m * b->host.m * b->host.m : (int64_t)b->host.n * b->host.n * b->host.n;
     s->E = E;
     s->len = E * (int64_t)b->host.n * b->host.n * b->host.n;
     s->G = G;

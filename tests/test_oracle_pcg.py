@@ -65,3 +65,25 @@ def test_zero_rhs_and_warm_start():
     x1, _, _ = oracle.pcg_bp35(N, G, 1.0, b, tol=1e-13)
     x2, it2, rel2 = oracle.pcg_bp35(N, G, 1.0, b, x0=x1, tol=1e-10)
     assert it2 == 0 and rel2 <= 1e-10
+
+
+@pytest.mark.parametrize("N,lam", [(1, 1.0), (2, 0.5), (3, 1.0), (4, 0.0)])
+def test_bp30_diagonal_equals_dense_matrix_diagonal(N, lam):
+    v = fem_synth.box_mesh(2, jitter=0.2, seed=6)
+    G, _ = oracle.geofacs(N, oracle.KIND_BP30, v)
+    d = oracle.bp30_diag(N, G, lam)
+    for e in range(v.shape[0]):
+        A = oracle.dense_element(N, v[e], "gauss", stiff=True, lam=lam)
+        np.testing.assert_allclose(d[e], np.diag(A), rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("N", [2, 4])
+def test_bp30_manufactured_solution(N):
+    v = fem_synth.box_mesh(3)
+    G, _ = oracle.geofacs(N, oracle.KIND_BP30, v)
+    X = oracle.gll_node_coordinates(N, v)
+    u = np.sin(np.pi * X[..., 0]) * np.sin(np.pi * X[..., 1]) * np.sin(np.pi * X[..., 2])
+    b = oracle.bp30(N, G, 1.0, u)
+    x, it, rel = oracle.pcg_bp30(N, G, 1.0, b, tol=1e-12)
+    assert rel <= 1e-12 and it > 0
+    assert np.linalg.norm(x - u) / np.linalg.norm(u) <= 1e-9
