@@ -126,3 +126,28 @@ def batch_workload(count: int = 64, seed: int = SEED_BATCH, nmin: int = 2, nmax:
         out.append({"N": N, "nx": nx, "ny": ny, "nz": nz, "E": nx * ny * nz,
                     "mesh_seed": seed * 1000 + i})
     return out
+
+
+def serve_workload(count: int, seed: int = SEED_SERVE, rate: float = 200.0, nmin: int = 3, nmax: int = 9,
+                   emin: int = 512, emax: int = 32768):
+    """Request stream recipe: Poisson arrivals (exponential gaps of mean
+    1/rate seconds), operator BP3.0 or BP3.5 and precision mode (FP64 or
+    mixed) each with probability 1/2, degree N uniform in nmin..nmax, element
+    count log-uniform in [emin, emax] as a near-cubic box of the unit cube.
+    Returns dicts (t, op, N, nx, ny, nz, E, mixed, mesh_seed, rhs_seed); op is
+    3 for BP3.0 and 2 for BP3.5."""
+    u = uniform(seed, 5 * count)
+    t = 0.0
+    out = []
+    for i in range(count):
+        t += -np.log(1.0 - u[5 * i]) / rate
+        op = 3 if u[5 * i + 1] < 0.5 else 2
+        N = nmin + min(int(u[5 * i + 2] * (nmax - nmin + 1)), nmax - nmin)
+        target = float(np.exp(np.log(emin) + u[5 * i + 3] * (np.log(emax) - np.log(emin))))
+        nx = max(1, int(round(target ** (1.0 / 3.0))))
+        ny = max(1, int(round((target / nx) ** 0.5)))
+        nz = max(1, int(round(target / (nx * ny))))
+        out.append({"t": t, "op": op, "N": N, "nx": nx, "ny": ny, "nz": nz, "E": nx * ny * nz,
+                    "mixed": bool(u[5 * i + 4] < 0.5), "mesh_seed": seed * 100000 + 2 * i,
+                    "rhs_seed": seed * 100000 + 2 * i + 1})
+    return out

@@ -309,6 +309,79 @@ int fem_batch_graph_launch(fem_batch *b, void *stream);
 /* Frees a batch (NULL accepted).  Synchronous. */
 void fem_batch_destroy(fem_batch *b);
 
+/* ---------------------------------------------------------------------
+ * Continuous-batching server of Helmholtz solves on one GPU.  Each request
+ * is a BP3.5 or BP3.0 system on its own mesh (vertices and right-hand side
+ * in host memory), solved by the Jacobi-PCG above in FP64 or mixed
+ * precision with all of its state on the device.  Requests wait in a FIFO
+ * queue and are admitted while a slot is free and their device footprint
+ * fits the HBM budget; admitted solves run on separate streams and
+ * overlap on the GPU.  A request's result is bit-identical alone and in
+ * the mix (deterministic per-request reductions).
+ * --------------------------------------------------------------------- */
+typedef struct fem_server fem_server; /* opaque */
+
+typedef struct {
+    int64_t hbm_budget; /* device bytes admitted requests may hold (default 120 GiB) */
+    int max_active;     /* requests in flight at once, 1..256 (default 8)          */
+    int check_every;    /* PCG iterations between host checks (default 8)          */
+} fem_serve_opts;
+
+typedef struct {
+    int op;              /* FEM_OP_BP35 or FEM_OP_BP30                              */
+    int N;               /* degree 1..15                                            */
+    int64_t E;           /* elements                                                */
+    const double *verts; /* host, E*8*3; read when the request is admitted          */
+    const double *rhs;   /* host, E*Np; read when the request is admitted           */
+    double *x;           /* host output, E*Np; written when the request finishes    */
+    double lambda;       /* >= 0                                                    */
+    int mode;            /* FEM_PCG_FP64 or FEM_PCG_MIXED                           */
+    double tol;          /* relative residual tolerance                             */
+} fem_serve_request;
+
+#define FEM_REQ_QUEUED 0
+#define FEM_REQ_RUNNING 1
+#define FEM_REQ_DONE 2
+#define FEM_REQ_FAILED 3
+
+typedef struct {
+    int state;       /* FEM_REQ_*                                               */
+    int status;      /* FEM_OK, or why it failed (FEM_ENOMEM: over the budget)   */
+    int iters, outer;
+    double relres;   /* FP64 ||rhs - A x|| / ||rhs|| of the returned x           */
+    double t_submit, t_admit, t_done; /* seconds on the server clock           */
+    int64_t bytes;   /* device footprint charged against the budget             */
+} fem_serve_result;
+
+/* Creates a server on the current device (prepares every degree, one
+ * stream and a pinned scalar block per slot).  opts may be NULL.
+ * Errors: FEM_EINVAL, FEM_ENOMEM, FEM_ECUDA. */
+int fem_serve_create(const fem_serve_opts *opts, fem_server **out);
+
+/* Queues a request and returns its id; never blocks and never touches the
+ * GPU.  The host buffers must stay valid until the request is DONE or
+ * FAILED.  Errors: FEM_EINVAL. */
+int fem_serve_submit(fem_server *s, const fem_serve_request *req, int64_t *id);
+
+/* Moves the server on without blocking: retires finished solves, moves every
+ * solve in flight on by one step when its previous step has finished, and
+ * admits queued requests (FIFO) while a slot and budget allow.  Call it in a
+ * loop.  *active / *queued (may be NULL) receive the counts afterwards.
+ * Errors: FEM_EINVAL. */
+int fem_serve_progress(fem_server *s, int *active, int *queued);
+
+/* State and outcome of a request.  Errors: FEM_EINVAL (unknown id). */
+int fem_serve_poll(fem_server *s, int64_t id, fem_serve_result *res);
+
+/* Seconds since the server was created (the clock of fem_serve_result). */
+double fem_serve_clock(const fem_server *s);
+
+/* Device bytes currently charged against the budget. */
+int64_t fem_serve_in_use(const fem_server *s);
+
+/* Waits for the solves in flight, frees everything (NULL accepted). */
+void fem_serve_destroy(fem_server *s);
+
 /* Static name of an error code. */
 const char *fem_strerror(int code);
 

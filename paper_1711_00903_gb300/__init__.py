@@ -22,7 +22,8 @@ __all__ = [
     "fem_bp35_apply", "fem_bp30_apply", "FEM_GEO_BP1", "FEM_GEO_BP35", "FEM_GEO_BP30",
     "geo_shape", "fem_bp35_apply_f32", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot", "fem_dot_scratch_size", "Pcg",
     "fem_pcg_create", "fem_pcg_solve", "fem_pcg_destroy", "FEM_PCG_FP64", "FEM_PCG_MIXED",
-    "Batch", "fem_batch_create", "FEM_OP_BP35", "FEM_OP_BP30",
+    "Batch", "fem_batch_create", "FEM_OP_BP35", "FEM_OP_BP30", "Server",
+    "FEM_REQ_QUEUED", "FEM_REQ_RUNNING", "FEM_REQ_DONE", "FEM_REQ_FAILED",
 ]
 
 FEM_OK, FEM_EINVAL, FEM_ECUDA, FEM_ENOMEM, FEM_ENODEV = 0, -1, -2, -3, -4
@@ -30,6 +31,7 @@ FEM_EBREAKDOWN, FEM_ENOCONV, FEM_ETOOBIG = -5, -6, -7
 FEM_PCG_FP64, FEM_PCG_MIXED = 0, 1
 FEM_GEO_BP1, FEM_GEO_BP35, FEM_GEO_BP30 = 1, 2, 3
 FEM_OP_BP35, FEM_OP_BP30 = 2, 3
+FEM_REQ_QUEUED, FEM_REQ_RUNNING, FEM_REQ_DONE, FEM_REQ_FAILED = 0, 1, 2, 3
 MAX_N = 15
 
 _lock = threading.Lock()
@@ -56,6 +58,25 @@ class BatchItem(C.Structure):
 class BatchConfig(C.Structure):
     """fem_batch_config (include/fem.h)."""
     _fields_ = [("threads", C.c_int), ("group", C.c_int), ("order", C.c_int), ("ms", C.c_float)]
+
+
+class ServeOpts(C.Structure):
+    """fem_serve_opts (include/fem.h)."""
+    _fields_ = [("hbm_budget", C.c_int64), ("max_active", C.c_int), ("check_every", C.c_int)]
+
+
+class ServeRequest(C.Structure):
+    """fem_serve_request (include/fem.h)."""
+    _fields_ = [("op", C.c_int), ("N", C.c_int), ("E", C.c_int64), ("verts", C.c_void_p),
+                ("rhs", C.c_void_p), ("x", C.c_void_p), ("lam", C.c_double), ("mode", C.c_int),
+                ("tol", C.c_double)]
+
+
+class ServeResult(C.Structure):
+    """fem_serve_result (include/fem.h)."""
+    _fields_ = [("state", C.c_int), ("status", C.c_int), ("iters", C.c_int), ("outer", C.c_int),
+                ("relres", C.c_double), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double), ("bytes", C.c_int64)]
 
 
 class FemError(RuntimeError):
@@ -110,6 +131,18 @@ def lib():
             L.fem_batch_destroy.restype = None
             for f in ("fem_batch_create", "fem_batch_apply", "fem_batch_tune", "fem_batch_get_config",
                       "fem_batch_set_config", "fem_batch_graph_launch"):
+                getattr(L, f).restype = i32
+            L.fem_serve_create.argtypes = [C.POINTER(ServeOpts), C.POINTER(vp)]
+            L.fem_serve_submit.argtypes = [vp, C.POINTER(ServeRequest), C.POINTER(i64)]
+            L.fem_serve_progress.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+            L.fem_serve_poll.argtypes = [vp, i64, C.POINTER(ServeResult)]
+            L.fem_serve_clock.argtypes = [vp]
+            L.fem_serve_clock.restype = dbl
+            L.fem_serve_in_use.argtypes = [vp]
+            L.fem_serve_in_use.restype = i64
+            L.fem_serve_destroy.argtypes = [vp]
+            L.fem_serve_destroy.restype = None
+            for f in ("fem_serve_create", "fem_serve_submit", "fem_serve_progress", "fem_serve_poll"):
                 getattr(L, f).restype = i32
             L.fem_pcg_destroy.argtypes = [vp]
             L.fem_pcg_destroy.restype = None
@@ -461,3 +494,71 @@ class Batch:
 
 def fem_batch_create(items) -> Batch:
     return Batch(items)
+
+
+class Server:
+    """Owning wrapper of a fem_server (continuous batching of Helmholtz
+    solves).  Host arrays of a request are kept referenced here until the
+    request has finished."""
+
+    def __init__(self, hbm_budget=120 << 30, max_active=8, check_every=8):
+        o = ServeOpts(int(hbm_budget), int(max_active), int(check_every))
+        h = C.c_void_p()
+        _check(lib().fem_serve_create(C.byref(o), C.byref(h)), "fem_serve_create")
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, op, N, verts, rhs, lam=1.0, mode=FEM_PCG_FP64, tol=1e-8):
+        """Queues a solve; verts (E, 8, 3) and rhs (E, (N+1)^3) float64 host
+        arrays.  Returns (id, x) with x the host array the solution lands in."""
+        import numpy as np
+        verts = np.ascontiguousarray(verts, dtype=np.float64)
+        rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+        E = verts.shape[0]
+        if rhs.size != E * (N + 1) ** 3:
+            raise ValueError("rhs size does not match E and N")
+        x = np.zeros_like(rhs)
+        r = ServeRequest(int(op), int(N), E, verts.ctypes.data, rhs.ctypes.data, x.ctypes.data, float(lam),
+                         int(mode), float(tol))
+        rid = C.c_int64()
+        _check(lib().fem_serve_submit(self.handle, C.byref(r), C.byref(rid)), "fem_serve_submit")
+        self._keep[rid.value] = (verts, rhs, x)
+        return rid.value, x
+
+    def progress(self):
+        a, q = C.c_int(), C.c_int()
+        _check(lib().fem_serve_progress(self.handle, C.byref(a), C.byref(q)), "fem_serve_progress")
+        return a.value, q.value
+
+    def poll(self, rid):
+        r = ServeResult()
+        _check(lib().fem_serve_poll(self.handle, int(rid), C.byref(r)), "fem_serve_poll")
+        return {k: getattr(r, k) for k, _ in ServeResult._fields_}
+
+    def clock(self) -> float:
+        return lib().fem_serve_clock(self.handle)
+
+    def in_use(self) -> int:
+        return lib().fem_serve_in_use(self.handle)
+
+    def drain(self, poll_sleep=0.0):
+        """Progresses until nothing is queued or in flight."""
+        import time
+        while True:
+            a, q = self.progress()
+            if a == 0 and q == 0:
+                return
+            if poll_sleep:
+                time.sleep(poll_sleep)
+
+    def free(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            lib().fem_serve_destroy(self.handle)
+            self.handle = C.c_void_p(None)
+        self._keep = {}
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

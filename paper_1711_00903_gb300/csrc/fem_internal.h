@@ -91,9 +91,19 @@ cudaError_t launch_dot(int64_t n, const double *x, const double *y, double *resu
                        cudaStream_t s);
 int64_t dot_scratch_size();
 
-// PCG solver internals (pcg.cu)
+// PCG solver internals (pcg.cu).  A solve is resumable: pcg_begin enqueues
+// its first step on a stream, pcg_advance moves it on by one step when the
+// previous one has finished (1 = finished, 0 = in flight, -1 = CUDA error).
+int pcg_new(const fem_basis *b, int op, int64_t E, const double *G, double lambda, int mode, fem_pcg **out);
+void pcg_delete(fem_pcg *s);
 cudaError_t pcg_create(fem_pcg *s);
+cudaError_t pcg_create_on(fem_pcg *s, cudaStream_t st, double *lent_hscal);
 void pcg_release(fem_pcg *s);
+void pcg_release_on(fem_pcg *s, cudaStream_t st);
+cudaError_t pcg_begin(fem_pcg *s, const double *b, double *x, const fem_pcg_opts *o, cudaStream_t st);
+int pcg_advance(fem_pcg *s, bool blocking);
 int pcg_solve(fem_pcg *s, const double *b, double *x, const fem_pcg_opts *o, fem_pcg_info *info, cudaStream_t st);
+int pcg_status(const fem_pcg *s, fem_pcg_info *info);
+constexpr int kPcgScalars = 11;  // doubles of pinned host memory a solver context needs
 
 }  // namespace fem

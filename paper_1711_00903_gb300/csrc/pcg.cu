@@ -411,6 +411,10 @@ cudaError_t launch_dot(int64_t n, const double *x, const double *y, double *resu
 
 // ---------------------------------------------------------------------- solver context
 
+namespace fem {
+enum PcgState { PS_IDLE = 0, PS_BB, PS_RUN64, PS_FINAL64, PS_OUTER, PS_INNER, PS_DONE };
+}  // namespace fem
+
 struct fem_pcg {
     const fem_basis *basis;
     int op;        // FEM_OP_BP35 or FEM_OP_BP30
@@ -424,8 +428,20 @@ struct fem_pcg {
     float *G32, *dinv32, *d32, *r32, *z32, *p32, *q32;  // FP32 inner recurrence (mixed mode)
     double *part;
     int64_t nparts;
-    double *scal;   // device scalars
-    double *hscal;  // pinned host copy
+    double *scal;       // device scalars
+    double *hscal;      // pinned host copy
+    bool own_hscal;     // allocated here (not lent by a server)
+    cudaStream_t ws;    // stream the workspace was allocated on
+    // resumable solve
+    cudaEvent_t ev;
+    int state;
+    bool pending;
+    const double *b;
+    double *x;
+    cudaStream_t st;
+    double tol, itol, bb;
+    int maxit, imaxit, every, chunk_done, inner_iters, outer, status;
+    fem_pcg_info info;
 };
 
 namespace fem {
@@ -461,187 +477,288 @@ cudaError_t op_pcg(fem_pcg *s, const float *G, const float *z, float *p, float *
 }
 
 template <typename P>
-cudaError_t alloc(P **ptr, int64_t count) {
-    return cudaMalloc((void **)ptr, sizeof(P) * (size_t)(count > 0 ? count : 1));
+cudaError_t alloc(P **ptr, int64_t count, cudaStream_t st) {
+    return cudaMallocAsync((void **)ptr, sizeof(P) * (size_t)(count > 0 ? count : 1), st);
 }
 
-cudaError_t sync_scalars(fem_pcg *s, cudaStream_t st) {
-    cudaError_t e = cudaMemcpyAsync(s->hscal, s->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+// Enqueues the scalar read-back and the event that marks the end of a step.
+cudaError_t end_step(fem_pcg *s) {
+    cudaError_t e = cudaMemcpyAsync(s->hscal, s->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev, s->st);
+    s->pending = (e == cudaSuccess);
     return e;
+}
+
+// Enqueues up to `chunk` PCG iterations on (x, p, r, Ap, z).
+template <typename T, typename XT>
+cudaError_t enqueue_iterations(fem_pcg *s, const T *G, XT *x, T *p, T *r, T *Ap, T *z, const T *dinv, int chunk) {
+    cudaError_t e = cudaSuccess;
+    const int64_t len = s->len;
+    for (int c = 0; c < chunk && e == cudaSuccess; c++) {
+        e = op_pcg(s, G, z, p, Ap, s->st);
+        if (e != cudaSuccess) break;
+        reduce_kernel<<<1, kRedThreads, 0, s->st>>>(R_PQ, op_blocks(s, sizeof(T) == 4), s->part, s->scal, nullptr,
+                                                    0.0);
+        if (sizeof(T) == 4 && sizeof(XT) == 4 && len % 4 == 0)
+            update_f32x4_kernel<<<kVecBlocks, kVecThreads, 0, s->st>>>(
+                len / 4, s->scal, (float4 *)x, (const float4 *)p, (float4 *)r, (const float4 *)Ap, (float4 *)z,
+                (const float4 *)dinv, s->part);
+        else
+            update_kernel<T, XT><<<kVecBlocks, kVecThreads, 0, s->st>>>(len, s->scal, x, p, r, Ap, z, dinv, s->part);
+        reduce_kernel<<<1, kRedThreads, 0, s->st>>>(R_RZ, kVecBlocks, s->part, s->scal, nullptr, 0.0);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+cudaError_t enqueue_outer(fem_pcg *s) {
+    cudaError_t e = op_apply64(s, s->x, s->q, s->st);
+    if (e != cudaSuccess) return e;
+    outer_kernel<<<kVecBlocks, kVecThreads, 0, s->st>>>(s->len, s->b, s->q, s->r32, s->z32, s->d32, s->dinv32, s->part);
+    reduce_kernel<<<1, kRedThreads, 0, s->st>>>(R_OUTER, kVecBlocks, s->part, s->scal, nullptr, s->itol * s->itol);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = end_step(s);
+    return e;
+}
+
+int next_chunk(const fem_pcg *s, int done, int limit) {
+    int c = s->every;
+    if (c > limit - done) c = limit - done;
+    return c > 0 ? c : 0;
 }
 
 }  // namespace
 
-cudaError_t pcg_create(fem_pcg *s) {
+// Allocates the workspace on stream st (stream-ordered, no device-wide
+// synchronisation) and enqueues the Jacobi diagonal and the FP32 factor copy.
+cudaError_t pcg_create_on(fem_pcg *s, cudaStream_t st, double *lent_hscal) {
     cudaError_t e = cudaSuccess;
     const int64_t len = s->len;
+    s->ws = st;
     s->nparts = std::max(op_blocks(s, false), op_blocks(s, true));
     if (s->nparts < 3 * (int64_t)kVecBlocks) s->nparts = 3 * (int64_t)kVecBlocks;
-    if (e == cudaSuccess) e = alloc(&s->part, 3 * s->nparts);
-    if (e == cudaSuccess) e = alloc(&s->scal, S_COUNT);
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&s->hscal, sizeof(double) * S_COUNT);
-    if (e == cudaSuccess) e = alloc(&s->q, len);
+    if (e == cudaSuccess) e = alloc(&s->part, 3 * s->nparts, st);
+    if (e == cudaSuccess) e = alloc(&s->scal, S_COUNT, st);
+    if (e == cudaSuccess) e = alloc(&s->q, len, st);
     if (s->mode == FEM_PCG_FP64) {
-        if (e == cudaSuccess) e = alloc(&s->r, len);
-        if (e == cudaSuccess) e = alloc(&s->z, len);
-        if (e == cudaSuccess) e = alloc(&s->p, len);
-        if (e == cudaSuccess) e = alloc(&s->dinv, len);
+        if (e == cudaSuccess) e = alloc(&s->r, len, st);
+        if (e == cudaSuccess) e = alloc(&s->z, len, st);
+        if (e == cudaSuccess) e = alloc(&s->p, len, st);
+        if (e == cudaSuccess) e = alloc(&s->dinv, len, st);
     } else {
-        if (e == cudaSuccess) e = alloc(&s->G32, 7 * s->E * s->gpts);
-        if (e == cudaSuccess) e = alloc(&s->dinv32, len);
-        if (e == cudaSuccess) e = alloc(&s->d32, len);
-        if (e == cudaSuccess) e = alloc(&s->r32, len);
-        if (e == cudaSuccess) e = alloc(&s->z32, len);
-        if (e == cudaSuccess) e = alloc(&s->p32, len);
-        if (e == cudaSuccess) e = alloc(&s->q32, len);
+        if (e == cudaSuccess) e = alloc(&s->G32, 7 * s->E * s->gpts, st);
+        if (e == cudaSuccess) e = alloc(&s->dinv32, len, st);
+        if (e == cudaSuccess) e = alloc(&s->d32, len, st);
+        if (e == cudaSuccess) e = alloc(&s->r32, len, st);
+        if (e == cudaSuccess) e = alloc(&s->z32, len, st);
+        if (e == cudaSuccess) e = alloc(&s->p32, len, st);
+        if (e == cudaSuccess) e = alloc(&s->q32, len, st);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+        if (lent_hscal) {
+            s->hscal = lent_hscal;
+            s->own_hscal = false;
+        } else {
+            e = cudaMallocHost((void **)&s->hscal, sizeof(double) * S_COUNT);
+            s->own_hscal = (e == cudaSuccess);
+        }
     }
     if (e != cudaSuccess) return e;
-    e = cudaMemset(s->scal, 0, sizeof(double) * S_COUNT);
+    e = cudaMemsetAsync(s->scal, 0, sizeof(double) * S_COUNT, st);
     if (e != cudaSuccess) return e;
     if (s->op == FEM_OP_BP30)
-        e = dispatch_degree<Dinv30Launch>(s->basis->host.N, s->basis, s->E, s->G, s->lambda, s->dinv, s->dinv32,
-                                          (cudaStream_t)0);
+        e = dispatch_degree<Dinv30Launch>(s->basis->host.N, s->basis, s->E, s->G, s->lambda, s->dinv, s->dinv32, st);
     else
-        e = dispatch_degree<DinvLaunch>(s->basis->host.N, s->basis, s->E, s->G, s->lambda, s->dinv, s->dinv32,
-                                        (cudaStream_t)0);
+        e = dispatch_degree<DinvLaunch>(s->basis->host.N, s->basis, s->E, s->G, s->lambda, s->dinv, s->dinv32, st);
     if (e == cudaSuccess && s->mode != FEM_PCG_FP64)
-        cast_f32_kernel<<<kVecBlocks, kVecThreads>>>(7 * s->E * s->gpts, s->G, s->G32);
+        cast_f32_kernel<<<kVecBlocks, kVecThreads, 0, st>>>(7 * s->E * s->gpts, s->G, s->G32);
     if (e == cudaSuccess) e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaDeviceSynchronize();
     return e;
 }
 
-void pcg_release(fem_pcg *s) {
+cudaError_t pcg_create(fem_pcg *s) {
+    cudaError_t e = pcg_create_on(s, (cudaStream_t)0, nullptr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)0);
+    return e;
+}
+
+// Frees the workspace, stream-ordered on st (the workspace must not be in
+// use by work on other streams).
+void pcg_release_on(fem_pcg *s, cudaStream_t st) {
     void *bufs[] = {s->r,   s->z,   s->p,   s->q,   s->dinv, s->G32, s->dinv32,
                     s->d32, s->r32, s->z32, s->p32, s->q32,  s->part, s->scal};
     for (void *b : bufs)
-        if (b) cudaFree(b);
-    if (s->hscal) cudaFreeHost(s->hscal);
+        if (b) cudaFreeAsync(b, st);
+    if (s->ev) cudaEventDestroy(s->ev);
+    if (s->hscal && s->own_hscal) cudaFreeHost(s->hscal);
+    s->ev = nullptr;
+    s->hscal = nullptr;
 }
 
-// Runs PCG iterations on (x, p, r, Ap, z) until the device flags say done or
-// broken, or maxit iterations; checks on the host every `every` iterations.
-template <typename T, typename XT>
-static cudaError_t pcg_loop(fem_pcg *s, const T *G, XT *x, T *p, T *r, T *Ap, T *z, const T *dinv, int maxit,
-                            int every, cudaStream_t st, int *iters) {
-    const int64_t len = s->len;
-    int done_it = 0;
-    cudaError_t e = cudaSuccess;
-    while (done_it < maxit) {
-        int chunk = every;
-        if (chunk > maxit - done_it) chunk = maxit - done_it;
-        for (int c = 0; c < chunk && e == cudaSuccess; c++) {
-            e = op_pcg(s, G, z, p, Ap, st);
-            if (e != cudaSuccess) break;
-            reduce_kernel<<<1, kRedThreads, 0, st>>>(R_PQ, op_blocks(s, sizeof(T) == 4), s->part, s->scal, nullptr,
-                                                     0.0);
-            if (sizeof(T) == 4 && sizeof(XT) == 4 && len % 4 == 0)
-                update_f32x4_kernel<<<kVecBlocks, kVecThreads, 0, st>>>(
-                    len / 4, s->scal, (float4 *)x, (const float4 *)p, (float4 *)r, (const float4 *)Ap, (float4 *)z,
-                    (const float4 *)dinv, s->part);
-            else
-                update_kernel<T, XT><<<kVecBlocks, kVecThreads, 0, st>>>(len, s->scal, x, p, r, Ap, z, dinv, s->part);
-            reduce_kernel<<<1, kRedThreads, 0, st>>>(R_RZ, kVecBlocks, s->part, s->scal, nullptr, 0.0);
-            e = cudaGetLastError();
+void pcg_release(fem_pcg *s) {
+    if (s->pending && s->ev) cudaEventSynchronize(s->ev);
+    pcg_release_on(s, s->ws);
+    cudaStreamSynchronize(s->ws);
+}
+
+// Starts a solve of A x = b on stream st: enqueues b . b and returns.
+cudaError_t pcg_begin(fem_pcg *s, const double *b, double *x, const fem_pcg_opts *o, cudaStream_t st) {
+    s->tol = (o && o->tol > 0) ? o->tol : 1e-10;
+    s->maxit = (o && o->maxit > 0) ? o->maxit : 100000;
+    s->itol = (o && o->inner_tol > 0) ? o->inner_tol : 1e-4;
+    s->imaxit = (o && o->inner_maxit > 0) ? o->inner_maxit : 100000;
+    s->every = (o && o->check_every > 0) ? o->check_every : (s->mode == FEM_PCG_FP64 ? 8 : 16);
+    s->b = b;
+    s->x = x;
+    s->st = st;
+    s->chunk_done = 0;
+    s->inner_iters = 0;
+    s->outer = 0;
+    s->status = FEM_OK;
+    std::memset(&s->info, 0, sizeof s->info);
+    cudaError_t e = launch_dot(s->len, b, b, s->scal + S_BB, s->part, st);
+    if (e == cudaSuccess) e = end_step(s);
+    s->state = PS_BB;
+    return e;
+}
+
+// Advances a solve by at most one step.  Returns 1 when the solve has
+// finished (s->status, s->info hold the outcome), 0 when work is in flight,
+// or -1 on a CUDA error.  blocking: wait for the step in flight instead of
+// polling it.
+int pcg_advance(fem_pcg *s, bool blocking) {
+    if (s->state == PS_DONE) return 1;
+    if (s->pending) {
+        if (blocking) {
+            if (cudaEventSynchronize(s->ev) != cudaSuccess) return -1;
+        } else {
+            const cudaError_t q = cudaEventQuery(s->ev);
+            if (q == cudaErrorNotReady) return 0;
+            if (q != cudaSuccess) return -1;
         }
-        if (e != cudaSuccess) return e;
-        done_it += chunk;
-        e = sync_scalars(s, st);
-        if (e != cudaSuccess) return e;
-        if (s->hscal[S_DONE] != 0.0 || s->hscal[S_BREAK] != 0.0) break;
+        s->pending = false;
     }
-    *iters = (int)s->hscal[S_ITER];
-    return cudaSuccess;
+    const double *h = s->hscal;
+    cudaError_t e = cudaSuccess;
+    switch (s->state) {
+        case PS_BB:
+            s->bb = h[S_BB];
+            if (s->bb == 0.0) {  // the solution of A x = 0 is 0
+                e = cudaMemsetAsync(s->x, 0, sizeof(double) * s->len, s->st);
+                s->state = PS_DONE;
+                if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+                return e == cudaSuccess ? 1 : -1;
+            }
+            if (s->mode == FEM_PCG_FP64) {
+                e = op_apply64(s, s->x, s->q, s->st);
+                if (e == cudaSuccess) {
+                    init_kernel<<<kVecBlocks, kVecThreads, 0, s->st>>>(s->len, s->b, s->q, s->r, s->z, s->dinv, s->part);
+                    reduce_kernel<<<1, kRedThreads, 0, s->st>>>(R_INIT, kVecBlocks, s->part, s->scal, nullptr,
+                                                                s->tol * s->tol);
+                    e = cudaGetLastError();
+                }
+                const int c = next_chunk(s, 0, s->maxit);
+                if (e == cudaSuccess) e = enqueue_iterations<double, double>(s, s->G, s->x, s->p, s->r, s->q, s->z, s->dinv, c);
+                s->chunk_done = c;
+                if (e == cudaSuccess) e = end_step(s);
+                s->state = PS_RUN64;
+            } else {
+                e = enqueue_outer(s);
+                s->state = PS_OUTER;
+            }
+            break;
+        case PS_RUN64: {
+            const bool fin = h[S_DONE] != 0.0 || h[S_BREAK] != 0.0 || s->chunk_done >= s->maxit;
+            if (!fin) {
+                const int c = next_chunk(s, s->chunk_done, s->maxit);
+                e = enqueue_iterations<double, double>(s, s->G, s->x, s->p, s->r, s->q, s->z, s->dinv, c);
+                s->chunk_done += c;
+                if (e == cudaSuccess) e = end_step(s);
+                break;
+            }
+            s->info.iters = (int)h[S_ITER];
+            s->info.outer = 1;
+            if (h[S_BREAK] != 0.0 && h[S_DONE] == 0.0)
+                s->status = FEM_EBREAKDOWN;
+            else if (h[S_DONE] == 0.0)
+                s->status = FEM_ENOCONV;
+            // true FP64 residual of the returned x
+            e = op_apply64(s, s->x, s->q, s->st);
+            if (e == cudaSuccess) {
+                init_kernel<<<kVecBlocks, kVecThreads, 0, s->st>>>(s->len, s->b, s->q, s->r, s->z, s->dinv, s->part);
+                reduce_kernel<<<1, kRedThreads, 0, s->st>>>(R_TRUE, kVecBlocks, s->part, s->scal, nullptr, 0.0);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = end_step(s);
+            s->state = PS_FINAL64;
+            break;
+        }
+        case PS_FINAL64:
+            s->info.relres = std::sqrt(h[S_RR] / s->bb);
+            s->state = PS_DONE;
+            return 1;
+        case PS_OUTER: {
+            s->info.relres = std::sqrt(h[S_RR_OUTER] / s->bb);
+            s->info.outer = s->outer;
+            s->info.iters = s->inner_iters;
+            if (h[S_RR_OUTER] <= s->tol * s->tol * s->bb) {
+                s->state = PS_DONE;
+                return 1;
+            }
+            if (s->outer >= 64 || s->inner_iters >= s->maxit) {
+                s->status = FEM_ENOCONV;
+                s->state = PS_DONE;
+                return 1;
+            }
+            s->chunk_done = 0;
+            const int c = next_chunk(s, 0, s->imaxit);
+            e = enqueue_iterations<float, float>(s, s->G32, s->d32, s->p32, s->r32, s->q32, s->z32, s->dinv32, c);
+            s->chunk_done = c;
+            if (e == cudaSuccess) e = end_step(s);
+            s->state = PS_INNER;
+            break;
+        }
+        case PS_INNER: {
+            const bool fin = h[S_DONE] != 0.0 || h[S_BREAK] != 0.0 || s->chunk_done >= s->imaxit;
+            if (!fin) {
+                const int c = next_chunk(s, s->chunk_done, s->imaxit);
+                e = enqueue_iterations<float, float>(s, s->G32, s->d32, s->p32, s->r32, s->q32, s->z32, s->dinv32, c);
+                s->chunk_done += c;
+                if (e == cudaSuccess) e = end_step(s);
+                break;
+            }
+            const int it = (int)h[S_ITER];
+            s->inner_iters += it;
+            if (it == 0 && h[S_BREAK] != 0.0) {
+                s->status = FEM_EBREAKDOWN;
+                s->info.iters = s->inner_iters;
+                s->state = PS_DONE;
+                return 1;
+            }
+            add_f32_kernel<<<kVecBlocks, kVecThreads, 0, s->st>>>(s->len, s->x, s->d32);
+            e = cudaGetLastError();
+            s->outer++;
+            if (e == cudaSuccess) e = enqueue_outer(s);
+            s->state = PS_OUTER;
+            break;
+        }
+        default:
+            return 1;
+    }
+    return e == cudaSuccess ? 0 : -1;
 }
-
 
 int pcg_solve(fem_pcg *s, const double *b, double *x, const fem_pcg_opts *o, fem_pcg_info *info, cudaStream_t st) {
-    const double tol = (o && o->tol > 0) ? o->tol : 1e-10;
-    const int maxit = (o && o->maxit > 0) ? o->maxit : 100000;
-    const double itol = (o && o->inner_tol > 0) ? o->inner_tol : 1e-4;
-    const int imaxit = (o && o->inner_maxit > 0) ? o->inner_maxit : 100000;
-    const int every = (o && o->check_every > 0) ? o->check_every : (s->mode == FEM_PCG_FP64 ? 8 : 16);
-    const int64_t len = s->len;
-    fem_pcg_info loc;
-    std::memset(&loc, 0, sizeof loc);
     cudaError_t e = cudaSetDevice(s->device);
-    // b . b
-    if (e == cudaSuccess) e = launch_dot(len, b, b, s->scal + S_BB, s->part, st);
-    if (e == cudaSuccess) e = sync_scalars(s, st);
+    if (e == cudaSuccess) e = pcg_begin(s, b, x, o, st);
     if (e != cudaSuccess) return -2;
-    const double bb = s->hscal[S_BB];
-    int status = FEM_OK;
-    if (bb == 0.0) {  // the solution of A x = 0 is 0
-        e = cudaMemsetAsync(x, 0, sizeof(double) * len, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (info) *info = loc;
-        return e == cudaSuccess ? FEM_OK : -2;
+    int r;
+    while ((r = pcg_advance(s, true)) == 0) {
     }
-    if (s->mode == FEM_PCG_FP64) {
-        e = op_apply64(s, x, s->q, st);
-        if (e == cudaSuccess) {
-            init_kernel<<<kVecBlocks, kVecThreads, 0, st>>>(len, b, s->q, s->r, s->z, s->dinv, s->part);
-            reduce_kernel<<<1, kRedThreads, 0, st>>>(R_INIT, kVecBlocks, s->part, s->scal, nullptr, tol * tol);
-            e = cudaGetLastError();
-        }
-        int it = 0;
-        if (e == cudaSuccess) e = pcg_loop<double, double>(s, s->G, x, s->p, s->r, s->q, s->z, s->dinv, maxit, every, st, &it);
-        if (e != cudaSuccess) return -2;
-        loc.iters = it;
-        loc.outer = 1;
-        if (s->hscal[S_BREAK] != 0.0 && s->hscal[S_DONE] == 0.0) status = FEM_EBREAKDOWN;
-        else if (s->hscal[S_DONE] == 0.0) status = FEM_ENOCONV;
-    } else {
-        const int max_outer = 64;
-        int outer = 0;
-        for (; outer < max_outer; outer++) {
-            e = op_apply64(s, x, s->q, st);
-            if (e != cudaSuccess) break;
-            outer_kernel<<<kVecBlocks, kVecThreads, 0, st>>>(len, b, s->q, s->r32, s->z32, s->d32, s->dinv32, s->part);
-            reduce_kernel<<<1, kRedThreads, 0, st>>>(R_OUTER, kVecBlocks, s->part, s->scal, nullptr, itol * itol);
-            e = cudaGetLastError();
-            if (e == cudaSuccess) e = sync_scalars(s, st);
-            if (e != cudaSuccess) break;
-            loc.relres = std::sqrt(s->hscal[S_RR_OUTER] / bb);
-            if (s->hscal[S_RR_OUTER] <= tol * tol * bb) break;
-            if (loc.iters >= imaxit * max_outer || loc.iters >= maxit) {
-                status = FEM_ENOCONV;
-                break;
-            }
-            int it = 0;
-            e = pcg_loop<float, float>(s, s->G32, s->d32, s->p32, s->r32, s->q32, s->z32, s->dinv32, imaxit, every, st,
-                                       &it);
-            if (e != cudaSuccess) break;
-            loc.iters += it;
-            if (it == 0 && s->hscal[S_BREAK] != 0.0) {
-                status = FEM_EBREAKDOWN;
-                break;
-            }
-            add_f32_kernel<<<kVecBlocks, kVecThreads, 0, st>>>(len, x, s->d32);
-            e = cudaGetLastError();
-            if (e != cudaSuccess) break;
-        }
-        if (e != cudaSuccess) return -2;
-        if (outer == max_outer) status = FEM_ENOCONV;
-        loc.outer = outer;
-    }
-    // true FP64 residual of the returned x
-    e = op_apply64(s, x, s->q, st);
-    if (e == cudaSuccess && s->mode == FEM_PCG_FP64) {
-        init_kernel<<<kVecBlocks, kVecThreads, 0, st>>>(len, b, s->q, s->r, s->z, s->dinv, s->part);
-        reduce_kernel<<<1, kRedThreads, 0, st>>>(R_TRUE, kVecBlocks, s->part, s->scal, nullptr, 0.0);
-    }
-    if (e == cudaSuccess && s->mode != FEM_PCG_FP64) {
-        outer_kernel<<<kVecBlocks, kVecThreads, 0, st>>>(len, b, s->q, s->r32, s->z32, s->d32, s->dinv32, s->part);
-        reduce_kernel<<<1, kRedThreads, 0, st>>>(R_OUTER, kVecBlocks, s->part, s->scal, nullptr, itol * itol);
-    }
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e == cudaSuccess) e = sync_scalars(s, st);
-    if (e != cudaSuccess) return -2;
-    loc.relres = std::sqrt((s->mode == FEM_PCG_FP64 ? s->hscal[S_RR] : s->hscal[S_RR_OUTER]) / bb);
-    if (info) *info = loc;
-    return status;
+    if (r < 0) return -2;
+    if (info) *info = s->info;
+    return s->status;
 }
 
 }  // namespace fem
@@ -677,22 +794,49 @@ int fem_bp30_jacobi(const fem_basis *b, int64_t E, const double *G, double lambd
     return e == cudaSuccess ? FEM_OK : fem::record_cuda_error(e);
 }
 
-int fem_pcg_create(const fem_basis *b, int op, int64_t E, const double *G, double lambda, int mode, fem_pcg **out) {
+}  // extern "C"
+
+namespace fem {
+
+int pcg_new(const fem_basis *b, int op, int64_t E, const double *G, double lambda, int mode, fem_pcg **out) {
     if (!b || !out || E < 1 || !G || (mode != FEM_PCG_FP64 && mode != FEM_PCG_MIXED)) return FEM_EINVAL;
     if (op != FEM_OP_BP35 && op != FEM_OP_BP30) return FEM_EINVAL;
     if (!(lambda >= 0.0)) return FEM_EINVAL;
     *out = nullptr;
     fem_pcg *s = new (std::nothrow) fem_pcg();
     if (!s) return FEM_ENOMEM;
-    std::memset(s, 0, sizeof(*s));
+    std::memset((void *)s, 0, sizeof(*s));
     s->basis = b;
     s->op = op;
-    s->gpts = (op == FEM_OP_BP30) ? (int64_t)b->host.m * b->host.m * b->host.m : (int64_t)b->host.n * b->host.n * b->host.n;
+    s->gpts = (op == FEM_OP_BP30) ? (int64_t)b->host.m * b->host.m * b->host.m
+                                  : (int64_t)b->host.n * b->host.n * b->host.n;
     s->E = E;
     s->len = E * (int64_t)b->host.n * b->host.n * b->host.n;
     s->G = G;
     s->lambda = lambda;
     s->mode = mode;
+    s->state = PS_IDLE;
+    *out = s;
+    return FEM_OK;
+}
+
+void pcg_delete(fem_pcg *s) { delete s; }
+
+int pcg_status(const fem_pcg *s, fem_pcg_info *info) {
+    if (info) *info = s->info;
+    return s->status;
+}
+
+static_assert(kPcgScalars == S_COUNT, "pinned scalar block size");
+
+}  // namespace fem
+
+extern "C" {
+
+int fem_pcg_create(const fem_basis *b, int op, int64_t E, const double *G, double lambda, int mode, fem_pcg **out) {
+    fem_pcg *s = nullptr;
+    const int r = fem::pcg_new(b, op, E, G, lambda, mode, &s);
+    if (r != FEM_OK) return r;
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = fem::pcg_create(s);
     if (e != cudaSuccess) {

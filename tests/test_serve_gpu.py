@@ -1,0 +1,87 @@
+"""The continuous-batching solve server: each request's result is the same
+bits alone and in the mix, the results meet their tolerance and agree with
+the oracle's solve, and admission respects the HBM budget."""
+import numpy as np
+import pytest
+
+import fem_synth
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _fem():
+    import paper_1711_00903_gb300 as fem
+    return fem
+
+
+def _requests():
+    out = []
+    specs = [(2, 2, 2, 2, 0), (3, 3, 2, 2, 1), (3, 4, 2, 1, 0), (2, 5, 3, 2, 1), (3, 2, 1, 3, 1), (2, 6, 2, 2, 0)]
+    for k, (op, N, nx, ny, mixed) in enumerate(specs):
+        v = fem_synth.box_mesh(nx, ny, 2, jitter=0.1, seed=700 + k)
+        rhs = fem_synth.field(800 + k, v.shape[0], (N + 1) ** 3)
+        out.append((op, N, v, rhs, 0.5 + k % 2, mixed))
+    return out
+
+
+def _run(server, reqs, one_at_a_time, tol=1e-9):
+    fem = _fem()
+    ids = []
+    for op, N, v, rhs, lam, mixed in reqs:
+        rid, x = server.submit(op, N, v, rhs, lam=lam, mode=fem.FEM_PCG_MIXED if mixed else fem.FEM_PCG_FP64,
+                               tol=tol)
+        ids.append((rid, x))
+        if one_at_a_time:
+            server.drain()
+    server.drain()
+    return [(x, server.poll(rid)) for rid, x in ids]
+
+
+def test_same_bits_alone_and_in_the_mix():
+    fem = _fem()
+    reqs = _requests()
+    alone = _run(fem.Server(max_active=1), reqs, one_at_a_time=True)
+    mixed = _run(fem.Server(max_active=8), reqs, one_at_a_time=False)
+    for (xa, ra), (xm, rm), req in zip(alone, mixed, reqs):
+        assert ra["state"] == rm["state"] == fem.FEM_REQ_DONE
+        assert np.array_equal(xa, xm), req[:2]
+        assert ra["iters"] == rm["iters"] and ra["relres"] == rm["relres"]
+        assert rm["relres"] <= 1e-9
+
+
+def test_results_against_the_oracle():
+    fem = _fem()
+    reqs = _requests()
+    res = _run(fem.Server(max_active=4), reqs, one_at_a_time=False, tol=1e-11)
+    for (x, r), (op, N, v, rhs, lam, mixed) in zip(res, reqs):
+        if op == 2:
+            G, _ = oracle.geofacs(N, oracle.KIND_BP35, v)
+            xo, _, _ = oracle.pcg_bp35(N, G, lam, rhs, tol=1e-12)
+            Ax = oracle.bp35(N, G, lam, x)
+        else:
+            G, _ = oracle.geofacs(N, oracle.KIND_BP30, v)
+            xo, _, _ = oracle.pcg_bp30(N, G, lam, rhs, tol=1e-12)
+            Ax = oracle.bp30(N, G, lam, x)
+        assert np.linalg.norm(rhs - Ax) / np.linalg.norm(rhs) <= 2e-11
+        assert np.linalg.norm(x - xo) / np.linalg.norm(xo) <= 1e-7
+
+
+def test_admission_under_the_budget():
+    fem = _fem()
+    reqs = _requests()[:3]
+    # a budget below any request's footprint: every request fails cleanly
+    s = fem.Server(hbm_budget=1024, max_active=4)
+    res = _run(s, reqs, one_at_a_time=False)
+    for x, r in res:
+        assert r["state"] == fem.FEM_REQ_FAILED and r["status"] == fem.FEM_ENOMEM
+    # a budget that holds one request at a time: they run one after another
+    big = max(r["bytes"] for _, r in res)
+    s = fem.Server(hbm_budget=big + big // 2, max_active=4)
+    res = _run(s, reqs, one_at_a_time=False)
+    assert all(r["state"] == fem.FEM_REQ_DONE for _, r in res)
+    for (_, a), (_, b) in zip(res, res[1:]):
+        assert b["t_admit"] >= a["t_done"]
+    assert s.in_use() == 0
+    with pytest.raises(fem.FemError):
+        s.poll(12345)
