@@ -428,6 +428,7 @@ def run_ours(args):
 
     pcg = None if args.no_pcg else run_pcg(fem, torch, device, verts_h, args)
     batch = None if args.no_batch else run_batch(fem, torch, device, args)
+    serve = None if args.serve_requests <= 0 else run_serve(fem, torch, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -458,6 +459,7 @@ def run_ours(args):
             "kernels": kern,
             "pcg": pcg,
             "batch": batch,
+            "serve": serve,
         }
         print(json.dumps(line))
     b.free()
@@ -574,6 +576,59 @@ def run_batch(fem, torch, device, args):
     return out
 
 
+def run_serve(fem, torch, args):
+    """Poisson arrivals (mean 200 requests/s) of Helmholtz PCG solves, BP3.0
+    or BP3.5 at random, N uniform in 3..9, E log-uniform in 512..32768, rhs
+    uniform in [-1, 1], tolerance 1e-8, FP64 or mixed precision at random,
+    120 GiB HBM budget; continuous batching with 8 slots against one request
+    at a time (first come, first served)."""
+    reqs = fem_synth.serve_workload(args.serve_requests)
+    data = []
+    for r in reqs:
+        v = fem_synth.box_mesh(r["nx"], r["ny"], r["nz"], jitter=0.1, seed=r["mesh_seed"])
+        rhs = fem_synth.field(r["rhs_seed"], r["E"], (r["N"] + 1) ** 3)
+        data.append((r, v, rhs))
+
+    def play(max_active):
+        srv = fem.Server(hbm_budget=120 << 30, max_active=max_active)
+        t0 = srv.clock()
+        k, ids = 0, []
+        while True:
+            now = srv.clock() - t0
+            while k < len(data) and data[k][0]["t"] <= now:
+                r, v, rhs = data[k]
+                mode = fem.FEM_PCG_MIXED if r["mixed"] else fem.FEM_PCG_FP64
+                rid, x = srv.submit(r["op"], r["N"], v, rhs, lam=1.0, mode=mode, tol=1e-8)
+                ids.append((rid, r, x))
+                k += 1
+            a, q = srv.progress()
+            if k == len(data) and a == 0 and q == 0:
+                break
+        res = [(srv.poll(rid), r, x) for rid, r, x in ids]
+        srv.free()
+        lat = np.array([p["t_done"] - p["t_submit"] for p, _, _ in res])
+        span = max(p["t_done"] for p, _, _ in res) - min(p["t_submit"] for p, _, _ in res)
+        out = {"solves_per_s": len(res) / span, "makespan_s": span,
+               "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+               "failed": int(sum(p["state"] != fem.FEM_REQ_DONE for p, _, _ in res)),
+               "max_relres": float(max(p["relres"] for p, _, _ in res))}
+        for name, flag in (("mixed", True), ("fp64", False)):
+            sel = np.array([r["mixed"] == flag for _, r, _ in res])
+            if sel.any():
+                out[name] = {"count": int(sel.sum()), "p50_s": float(np.percentile(lat[sel], 50)),
+                             "p99_s": float(np.percentile(lat[sel], 99)),
+                             "mean_iters": float(np.mean([p["iters"] for (p, _, _), s_ in zip(res, sel) if s_]))}
+        return out, [x for _, _, x in res]
+
+    cb, xs_cb = play(8)
+    fifo, xs_fifo = play(1)
+    same = all(np.array_equal(a, b) for a, b in zip(xs_cb, xs_fifo))
+    return {"workload": f"{len(data)} requests, Poisson arrivals at 200/s, BP3.0|BP3.5, N 3..9, E 512..32768 "
+                        "log-uniform, rhs U[-1,1], tol 1e-8, FP64|mixed, 120 GiB budget",
+            "continuous_batching_8_slots": cb, "one_at_a_time": fifo,
+            "results_identical_alone_and_in_mix": same}
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -589,6 +644,8 @@ def main(argv=None):
     ap.add_argument("--no-pcg", action="store_true", help="skip the Helmholtz solve measurement")
     ap.add_argument("--pcg-solves", type=int, default=3)
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-order batch measurement")
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="requests of the Poisson-arrival serving measurement (0 skips it)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         raise SystemExit("--warmup must be at least 3")

@@ -442,6 +442,13 @@ struct fem_pcg {
     double tol, itol, bb;
     int maxit, imaxit, every, chunk_done, inner_iters, outer, status;
     fem_pcg_info info;
+    // CUDA graphs of one full chunk of iterations (and of the outer
+    // defect-correction step), captured on first use and replayed
+    cudaGraphExec_t g_iter64, g_iter32, g_outer;
+    int g_every;                   // chunk length the iteration graphs were captured with
+    const double *g_b;             // right-hand side and solution the graphs were captured with
+    double *g_x;
+    bool use_graphs;               // not on the legacy default stream, which cannot be captured
 };
 
 namespace fem {
@@ -511,12 +518,72 @@ cudaError_t enqueue_iterations(fem_pcg *s, const T *G, XT *x, T *p, T *r, T *Ap,
     return e;
 }
 
-cudaError_t enqueue_outer(fem_pcg *s) {
+cudaError_t outer_body(fem_pcg *s) {
     cudaError_t e = op_apply64(s, s->x, s->q, s->st);
     if (e != cudaSuccess) return e;
     outer_kernel<<<kVecBlocks, kVecThreads, 0, s->st>>>(s->len, s->b, s->q, s->r32, s->z32, s->d32, s->dinv32, s->part);
     reduce_kernel<<<1, kRedThreads, 0, s->st>>>(R_OUTER, kVecBlocks, s->part, s->scal, nullptr, s->itol * s->itol);
     e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->hscal, s->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s->st);
+    return e;
+}
+
+// Captures whatever `body` enqueues on s->st into an executable graph.
+template <class F>
+cudaError_t capture(fem_pcg *s, cudaGraphExec_t *exec, F body) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s->st, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return e;
+    cudaError_t be = body();
+    e = cudaStreamEndCapture(s->st, &g);
+    if (be != cudaSuccess) e = be;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e;
+}
+
+cudaError_t enqueue_outer(fem_pcg *s) {
+    cudaError_t e = cudaSuccess;
+    if (!s->use_graphs) {
+        e = outer_body(s);
+        if (e == cudaSuccess) e = cudaEventRecord(s->ev, s->st);
+        s->pending = (e == cudaSuccess);
+        return e;
+    }
+    if (!s->g_outer) e = capture(s, &s->g_outer, [&] { return outer_body(s); });
+    if (e == cudaSuccess) e = cudaGraphLaunch(s->g_outer, s->st);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev, s->st);
+    s->pending = (e == cudaSuccess);
+    return e;
+}
+
+// A chunk of iterations followed by the scalar read-back and the event; a
+// full chunk replays its captured graph.
+template <typename T, typename XT>
+cudaError_t enqueue_chunk(fem_pcg *s, const T *G, XT *x, T *p, T *r, T *Ap, T *z, const T *dinv, int chunk) {
+    cudaError_t e = cudaSuccess;
+    cudaGraphExec_t *g = sizeof(T) == 8 ? &s->g_iter64 : &s->g_iter32;
+    if (chunk == s->every && s->use_graphs) {
+        if (*g && s->g_every != s->every) {
+            cudaGraphExecDestroy(*g);
+            *g = nullptr;
+        }
+        if (!*g) {
+            e = capture(s, g, [&] {
+                cudaError_t ce = enqueue_iterations<T, XT>(s, G, x, p, r, Ap, z, dinv, chunk);
+                if (ce == cudaSuccess)
+                    ce = cudaMemcpyAsync(s->hscal, s->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s->st);
+                return ce;
+            });
+            s->g_every = s->every;
+        }
+        if (e == cudaSuccess) e = cudaGraphLaunch(*g, s->st);
+        if (e == cudaSuccess) e = cudaEventRecord(s->ev, s->st);
+        s->pending = (e == cudaSuccess);
+        return e;
+    }
+    e = enqueue_iterations<T, XT>(s, G, x, p, r, Ap, z, dinv, chunk);
     if (e == cudaSuccess) e = end_step(s);
     return e;
 }
@@ -592,6 +659,10 @@ void pcg_release_on(fem_pcg *s, cudaStream_t st) {
         if (b) cudaFreeAsync(b, st);
     if (s->ev) cudaEventDestroy(s->ev);
     if (s->hscal && s->own_hscal) cudaFreeHost(s->hscal);
+    cudaGraphExec_t gs[] = {s->g_iter64, s->g_iter32, s->g_outer};
+    for (cudaGraphExec_t g : gs)
+        if (g) cudaGraphExecDestroy(g);
+    s->g_iter64 = s->g_iter32 = s->g_outer = nullptr;
     s->ev = nullptr;
     s->hscal = nullptr;
 }
@@ -609,9 +680,18 @@ cudaError_t pcg_begin(fem_pcg *s, const double *b, double *x, const fem_pcg_opts
     s->itol = (o && o->inner_tol > 0) ? o->inner_tol : 1e-4;
     s->imaxit = (o && o->inner_maxit > 0) ? o->inner_maxit : 100000;
     s->every = (o && o->check_every > 0) ? o->check_every : (s->mode == FEM_PCG_FP64 ? 8 : 16);
+    if (s->g_b != b || s->g_x != x) {  // the captured graphs name the old vectors
+        cudaGraphExec_t gs[] = {s->g_iter64, s->g_iter32, s->g_outer};
+        for (cudaGraphExec_t g : gs)
+            if (g) cudaGraphExecDestroy(g);
+        s->g_iter64 = s->g_iter32 = s->g_outer = nullptr;
+        s->g_b = b;
+        s->g_x = x;
+    }
     s->b = b;
     s->x = x;
     s->st = st;
+    s->use_graphs = !(st == (cudaStream_t)0 || st == cudaStreamLegacy || st == cudaStreamPerThread);
     s->chunk_done = 0;
     s->inner_iters = 0;
     s->outer = 0;
@@ -659,9 +739,8 @@ int pcg_advance(fem_pcg *s, bool blocking) {
                     e = cudaGetLastError();
                 }
                 const int c = next_chunk(s, 0, s->maxit);
-                if (e == cudaSuccess) e = enqueue_iterations<double, double>(s, s->G, s->x, s->p, s->r, s->q, s->z, s->dinv, c);
+                if (e == cudaSuccess) e = enqueue_chunk<double, double>(s, s->G, s->x, s->p, s->r, s->q, s->z, s->dinv, c);
                 s->chunk_done = c;
-                if (e == cudaSuccess) e = end_step(s);
                 s->state = PS_RUN64;
             } else {
                 e = enqueue_outer(s);
@@ -672,9 +751,8 @@ int pcg_advance(fem_pcg *s, bool blocking) {
             const bool fin = h[S_DONE] != 0.0 || h[S_BREAK] != 0.0 || s->chunk_done >= s->maxit;
             if (!fin) {
                 const int c = next_chunk(s, s->chunk_done, s->maxit);
-                e = enqueue_iterations<double, double>(s, s->G, s->x, s->p, s->r, s->q, s->z, s->dinv, c);
+                e = enqueue_chunk<double, double>(s, s->G, s->x, s->p, s->r, s->q, s->z, s->dinv, c);
                 s->chunk_done += c;
-                if (e == cudaSuccess) e = end_step(s);
                 break;
             }
             s->info.iters = (int)h[S_ITER];
@@ -713,9 +791,8 @@ int pcg_advance(fem_pcg *s, bool blocking) {
             }
             s->chunk_done = 0;
             const int c = next_chunk(s, 0, s->imaxit);
-            e = enqueue_iterations<float, float>(s, s->G32, s->d32, s->p32, s->r32, s->q32, s->z32, s->dinv32, c);
+            e = enqueue_chunk<float, float>(s, s->G32, s->d32, s->p32, s->r32, s->q32, s->z32, s->dinv32, c);
             s->chunk_done = c;
-            if (e == cudaSuccess) e = end_step(s);
             s->state = PS_INNER;
             break;
         }
@@ -723,9 +800,8 @@ int pcg_advance(fem_pcg *s, bool blocking) {
             const bool fin = h[S_DONE] != 0.0 || h[S_BREAK] != 0.0 || s->chunk_done >= s->imaxit;
             if (!fin) {
                 const int c = next_chunk(s, s->chunk_done, s->imaxit);
-                e = enqueue_iterations<float, float>(s, s->G32, s->d32, s->p32, s->r32, s->q32, s->z32, s->dinv32, c);
+                e = enqueue_chunk<float, float>(s, s->G32, s->d32, s->p32, s->r32, s->q32, s->z32, s->dinv32, c);
                 s->chunk_done += c;
-                if (e == cudaSuccess) e = end_step(s);
                 break;
             }
             const int it = (int)h[S_ITER];

@@ -223,3 +223,31 @@ def test_bp30_f32_matvec_through_mixed_solver_components():
     s = fem.fem_pcg_create(basis, _dev(G), 1.0, fem.FEM_PCG_MIXED, op=fem.FEM_OP_BP30)
     x, info, code = s.solve(_dev(b), tol=1e-9, inner_tol=1e-5)
     assert code == 0 and info["outer"] <= 4
+
+
+def test_solve_on_a_side_stream_replays_graphs_with_the_same_bits():
+    """On a created stream the solver replays captured CUDA graphs of its
+    iteration chunks; the result equals the direct launches on the default
+    stream bit for bit, also when the right-hand side buffer changes."""
+    import torch
+    fem = _fem()
+    for op, kind, apply in ((fem.FEM_OP_BP35, oracle.KIND_BP35, oracle.bp35),
+                            (fem.FEM_OP_BP30, oracle.KIND_BP30, oracle.bp30)):
+        N = 3
+        v = fem_synth.box_mesh(3)
+        G, _ = oracle.geofacs(N, kind, v)
+        b1 = _dev(fem_synth.field(41, v.shape[0], 64))
+        b2 = _dev(fem_synth.field(42, v.shape[0], 64))
+        basis = fem.fem_basis_setup(N)
+        for mode in (0, 1):
+            s = fem.fem_pcg_create(basis, _dev(G), 1.0, mode, op=op)
+            ref1, i1, _ = s.solve(b1, tol=1e-10)
+            ref2, i2, _ = s.solve(b2, tol=1e-10)
+            st = torch.cuda.Stream()
+            with torch.cuda.stream(st):
+                x1, j1, _ = s.solve(b1, tol=1e-10, stream=st)
+                x1b, j1b, _ = s.solve(b1, x=torch.zeros_like(b1), tol=1e-10, stream=st)
+                x2, j2, _ = s.solve(b2, tol=1e-10, stream=st)
+            st.synchronize()
+            assert torch.equal(ref1, x1) and torch.equal(ref1, x1b) and torch.equal(ref2, x2)
+            assert i1["iters"] == j1["iters"] and i2["iters"] == j2["iters"]
