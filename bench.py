@@ -20,6 +20,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -42,8 +43,9 @@ KERNELS = ["geofacs_bp1", "geofacs_bp35", "geofacs_bp30", "bp1", "bp35", "bp30"]
 # element at N = 7, with the sha256 of the kernel source it was taken from;
 # a kernel whose source changed since reports traffic null.
 NCU_TRAFFIC = {
-    # profiles/bp30_f64_N7_E4096.md: 194.3 MB over 4096 elements
-    "bp30": {"N": 7, "bytes_per_elem": 47430, "sha": "6b3131ac7a833798"},
+    # profiles/fp64_operators_N7_E4096.md: 194.8 MB over 4096 elements
+    "bp30": {"N": 7, "bytes_per_elem": 47570, "sha": "c33d1b1cdc630f0e",
+             "files": ["bp30.cu", "bp30_body.cuh", "eo.cuh"]},
 }
 
 
@@ -123,6 +125,32 @@ def alg_counts(N: int):
         "bp30": 8 * (2 * n3 + 7 * m3),
     }
     return std, inst, byts
+
+
+def smem_counts(N: int, word: int = 8):
+    """Shared-memory bytes per element that the operator kernels load and
+    store, counted from their phases (the quantity of the paper's
+    shared-memory roofline, Section 5):
+    BP1.0  2n^3 + 3mn^2 + 4m^2n words (staging, five line phases);
+    BP3.5  17n^3 words (staging, three derivative lines, chain rule with the
+           mass term, two in-place transposes, final sum);
+    BP3.0  2n^3 + 3mn^2 + 4m^2n + 16m^3 words (BP1.0's interpolation and
+           projection phases plus the Gauss-point derivative, chain-rule and
+           transpose phases)."""
+    n, m = N + 1, N + 2
+    return {
+        "bp1": word * (2 * n ** 3 + 3 * m * n * n + 4 * m * m * n),
+        "bp35": word * 17 * n ** 3,
+        "bp30": word * (2 * n ** 3 + 3 * m * n * n + 4 * m * m * n + 16 * m ** 3),
+    }
+
+
+# Shared-memory bandwidth of the SM: 32 banks x 4 bytes per clock.
+SMEM_BYTES_PER_CLK_SM = 128
+
+
+def smem_peak_gbs(sm_mhz: float) -> float:
+    return SMS * SMEM_BYTES_PER_CLK_SM * sm_mhz * 1e6 / 1e9
 
 
 class ClockSampler:
@@ -220,13 +248,30 @@ def workload_arrays(N: int, E_side: int, rank: int):
     return verts, q
 
 
-def _src_hash(name: str) -> str:
-    path = os.path.join(ROOT, "paper_1711_00903_gb300", "csrc", name)
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def _src_hash(names) -> str:
+    """Hash of the kernel's source files (a name or a list of names under csrc/)."""
+    h = hashlib.sha256()
+    for name in ([names] if isinstance(names, str) else names):
+        with open(os.path.join(ROOT, "paper_1711_00903_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 # ---------------------------------------------------------------- CPU oracle
+
+def cpu_model() -> str:
+    """The host CPU's architecture and model name, as lscpu reports them."""
+    name = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                name = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return f"{platform.machine()}, {name or 'model not reported'}"
+
 
 def cpu_oracle_rate(N: int, verts, q, lam: float, target_s: float, cores: int):
     """Times the oracle's step (geometric factors + the three operators) on a
@@ -394,6 +439,7 @@ def run_ours(args):
     dofs = 3 * E * n ** 3
     value = world * dofs * args.steps / (ms / 1e3) / 1e9
     std, inst, byts = alg_counts(N)
+    smem = smem_counts(N)
     hbm, hbm_src, _ = _peaks()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     kern = {}
@@ -407,11 +453,11 @@ def run_ours(args):
             "fp64_tflops": E * std[name] / t / 1e12,
             "fp64_frac": E * std[name] / t / 1e12 / fp64_peak_tflops(2070.0),
             "fp64_issue_frac": E * inst[name] / t / 1e9 / fp64_peak_ginst(sm_mhz),
+            "smem_frac": E * smem[name] / t / 1e9 / smem_peak_gbs(sm_mhz) if name in smem else None,
         }
     dom = max(KERNELS, key=lambda k: per_kernel[k])
-    src_file = {"bp1": "bp1.cu", "bp35": "bp35.cu", "bp30": "bp30.cu"}.get(dom, "geofacs.cu")
     tr = NCU_TRAFFIC.get(dom)
-    traffic = tr["bytes_per_elem"] * E if tr and tr["sha"] == _src_hash(src_file) and tr["N"] == N else None
+    traffic = tr["bytes_per_elem"] * E if tr and tr["sha"] == _src_hash(tr["files"]) and tr["N"] == N else None
     peak_alu = fp64_peak_tflops(2070.0)
     roofline = {
         "kernel": dom, "bound": "alu", "unit": "TFLOP/s",
@@ -424,8 +470,13 @@ def run_ours(args):
         "traffic": traffic,
         "hbm": {"achieved_gbs": kern[dom]["alg_gbs"], "peak_gbs": hbm, "peak_source": hbm_src,
                 "frac": kern[dom]["hbm_frac"]},
+        "smem": None if dom not in smem else {
+            "bytes_per_elem": smem[dom], "achieved_gbs": E * smem[dom] / (per_kernel[dom] / 1e3) / 1e9,
+            "peak_gbs": smem_peak_gbs(sm_mhz), "frac": kern[dom]["smem_frac"],
+            "peak_source": "152 SMs x 128 B/clk x median SM clock (the paper's Section 5 model)"},
     }
 
+    sweep = None if (args.no_sweep or rank != 0) else run_sweep(fem, torch, device, verts, args, sm_mhz)
     pcg = None if args.no_pcg else run_pcg(fem, torch, device, verts_h, args)
     batch = None if args.no_batch else run_batch(fem, torch, device, args)
     serve = None if args.serve_requests <= 0 else run_serve(fem, torch, args)
@@ -437,6 +488,10 @@ def run_ours(args):
         cpu = {"value": rate, "unit": "GDOF/s", "cores": threads, "kind": "oracle",
                "sample": f"{reps} pass(es) over the first {Es} of {E} elements (geometric factors + "
                          f"BP1.0 + BP3.5 + BP3.0, N={N}), {dt:.1f} s"}
+        r1, Es1, reps1, dt1, _ = cpu_oracle_rate(N, verts_h, q_h, lam, args.cpu_seconds / 4, 1)
+        cpu["single_thread"] = {"value": r1, "unit": "GDOF/s", "cores": 1,
+                                "sample": f"{reps1} pass(es) over the first {Es1} of {E} elements, {dt1:.1f} s"}
+        cpu["host"] = cpu_model()
 
     if rank == 0:
         line = {
@@ -457,6 +512,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "clocks": clocks,
             "kernels": kern,
+            "sweep": sweep,
             "pcg": pcg,
             "batch": batch,
             "serve": serve,
@@ -467,6 +523,120 @@ def run_ours(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def parse_degrees(spec: str):
+    out = []
+    for part in spec.split(","):
+        part = part.strip()
+        if not part:
+            continue
+        if "-" in part:
+            lo, hi = part.split("-")
+            out.extend(range(int(lo), int(hi) + 1))
+        else:
+            out.append(int(part))
+    return out
+
+
+def run_sweep(fem, torch, device, verts, args, sm_mhz):
+    """GDOF/s and roofline fractions of the three FP64 operators (and the
+    FP32 BP3.5/BP3.0 operators of the mixed-precision solver) against N on
+    the benchmark mesh, with the copy roofline recalibrated at every size as
+    the paper does (Section 5): a device-to-device copy of half the
+    operator's algorithmic bytes (a copy of T/2 bytes moves T), and a
+    reduction with the operator's read:write ratio (k planes read, one
+    written).  Each figure is the mean of `reps` launches timed with CUDA
+    events after two warm-up launches; every input is larger than L2 from
+    N = 2 on (at N = 1 the BP3.5 factors, 14.7 MB, fit in L2 and the figure
+    is an upper bound)."""
+    stream = torch.cuda.current_stream(device)
+    E = verts.shape[0]
+    lam, reps = 1.0, args.sweep_reps
+    hbm, _, _ = _peaks()
+    rows = []
+
+    def timed(fn, count):
+        for _ in range(2):
+            fn()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(count + 1)]
+        ev[0].record(stream)
+        for i in range(count):
+            fn()
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+        return statistics.fmean(ev[i].elapsed_time(ev[i + 1]) for i in range(count))
+
+    degrees = parse_degrees(args.sweep)
+    if not degrees:
+        return None
+    # one seeded U[-1,1] field of the largest size; smaller N take a prefix
+    q_all = torch.from_numpy(fem_synth.field(fem_synth.SEED_Q, E, (max(degrees) + 1) ** 3)).to(device).view(-1)
+    for N in degrees:
+        n = N + 1
+        b = fem.fem_basis_setup(N)
+        q = q_all[:E * n ** 3].view(E, n ** 3)
+        out = torch.empty_like(q)
+        std, inst, byts = alg_counts(N)
+        smem = smem_counts(N)
+        row = {"N": N, "dofs": E * n ** 3}
+        for name, kind in (("bp1", 1), ("bp35", 2), ("bp30", 3), ("bp35_f32", 2), ("bp30_f32", 3)):
+            f32 = name.endswith("_f32")
+            base = name[:-4] if f32 else name
+            geo = torch.empty(fem.geo_shape(b, kind, E), dtype=torch.float64, device=device)
+            fem.fem_mesh_geofacs(b, kind, verts, geo=geo, stream=stream)
+            if f32:
+                geo, qx = geo.float(), q.float()
+                o = torch.empty_like(qx)
+                fn = fem.fem_bp35_apply_f32 if base == "bp35" else fem.fem_bp30_apply_f32
+                ms = timed(lambda: fn(b, geo, lam, qx, out=o, stream=stream), reps)
+                del qx, o
+            elif name == "bp1":
+                ms = timed(lambda: fem.fem_bp1_apply(b, geo, q, out=out, stream=stream), reps)
+            elif name == "bp35":
+                ms = timed(lambda: fem.fem_bp35_apply(b, geo, lam, q, out=out, stream=stream), reps)
+            else:
+                ms = timed(lambda: fem.fem_bp30_apply(b, geo, lam, q, out=out, stream=stream), reps)
+            del geo
+            word = 4 if f32 else 8
+            per_elem = byts[base] * word // 8
+            T = E * per_elem
+            # recalibrated copy roofline at this byte count
+            half = torch.empty(T // 2 // 8, dtype=torch.float64, device=device)
+            dst = torch.empty_like(half)
+            copy_ms = timed(lambda: dst.copy_(half), 10)
+            del half, dst
+            # read:write ratio of the operator (planes read per plane written)
+            k = round((byts[base] - 8 * n ** 3) / (8 * n ** 3))
+            src = torch.empty((k, E * n ** 3), dtype=torch.float32 if f32 else torch.float64, device=device)
+            src.fill_(1.0)
+            red = torch.empty(E * n ** 3, dtype=src.dtype, device=device)
+            ratio_ms = timed(lambda: torch.sum(src, dim=0, out=red), 10)
+            ratio_gbs = word * (k + 1) * E * n ** 3 / (ratio_ms / 1e3) / 1e9
+            del src, red
+            t = ms / 1e3
+            gbs = T / t / 1e9
+            copy_gbs = T / (copy_ms / 1e3) / 1e9
+            row[name] = {
+                "ms": ms, "gdofs": E * n ** 3 / t / 1e9, "alg_gbs": gbs,
+                "hbm_frac": gbs / hbm, "copy_gbs_at_size": copy_gbs, "copy_frac_at_size": gbs / copy_gbs,
+                "ratio_stream_gbs": ratio_gbs, "ratio_read_planes": k,
+                "hbm_bound_gdofs": copy_gbs / (per_elem / n ** 3),
+                "smem_frac": E * smem[base] * word // 8 / t / 1e9 / smem_peak_gbs(sm_mhz),
+            }
+            if not f32:
+                row[name]["fp64_tflops"] = E * std[name] / t / 1e12
+                row[name]["fp64_issue_frac"] = E * inst[name] / t / 1e9 / fp64_peak_ginst(sm_mhz)
+        rows.append(row)
+        del q, out
+        b.free()
+    del q_all
+    torch.cuda.empty_cache()
+    return {"workload": f"BP1.0/BP3.5/BP3.0 FP64 (and BP3.5/BP3.0 FP32, the mixed solver's inner operators) "
+                        f"sweep, E={E} jittered hexes, lambda=1, mean of {reps} launches per point",
+            "copy_roofline": "device-to-device copy of T/2 bytes moving T = the operator's algorithmic "
+                             "bytes, recalibrated at every N (Section 5 of the paper)",
+            "rows": rows}
 
 
 def manufactured_u(fem, basis, verts_h):
@@ -641,6 +811,10 @@ def main(argv=None):
                          "smaller sides are for profiling captures)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", default="1-15",
+                    help="degrees of the per-N operator sweep (e.g. 1-15 or 3,7,11)")
+    ap.add_argument("--sweep-reps", type=int, default=5)
+    ap.add_argument("--no-sweep", action="store_true", help="skip the per-N operator sweep")
     ap.add_argument("--no-pcg", action="store_true", help="skip the Helmholtz solve measurement")
     ap.add_argument("--pcg-solves", type=int, default=3)
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-order batch measurement")

@@ -143,6 +143,14 @@ int fem_bp30_apply(const fem_basis *b, int64_t E, const double *G, double lambda
 int fem_bp35_apply_f32(const fem_basis *b, int64_t E, const float *G, double lambda,
                        const float *q, float *Aq, void *stream);
 
+/* BP3.0 matvec in FP32 (Algorithm 5 with float data and FP32 arithmetic;
+ * the inner operator of the mixed-precision BP3.0 solver).  Same layouts as
+ * fem_bp30_apply: G device E*7*m^3 floats, q and Aq device E*n^3 floats,
+ * 16-byte aligned, Aq != q.  Asynchronous on stream, allocates nothing.
+ * Errors: FEM_EINVAL, FEM_ECUDA. */
+int fem_bp30_apply_f32(const fem_basis *b, int64_t E, const float *G, double lambda,
+                       const float *q, float *Aq, void *stream);
+
 /* Inverse of the diagonal of the BP3.5 operator D^T G D + lambda J (the
  * Jacobi preconditioner), in closed form:
  *   diag_ijk = sum_l (D_li^2 Grr_ljk + D_lj^2 Gss_ilk + D_lk^2 Gtt_ijl)

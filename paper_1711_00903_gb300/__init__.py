@@ -20,7 +20,7 @@ __all__ = [
     "FemError", "lib", "Basis", "fem_version", "fem_basis_setup", "fem_basis_free",
     "fem_basis_tables", "fem_basis_host_tables", "fem_mesh_geofacs", "fem_bp1_apply",
     "fem_bp35_apply", "fem_bp30_apply", "FEM_GEO_BP1", "FEM_GEO_BP35", "FEM_GEO_BP30",
-    "geo_shape", "fem_bp35_apply_f32", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot", "fem_dot_scratch_size", "Pcg",
+    "geo_shape", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot", "fem_dot_scratch_size", "Pcg",
     "fem_pcg_create", "fem_pcg_solve", "fem_pcg_destroy", "FEM_PCG_FP64", "FEM_PCG_MIXED",
     "Batch", "fem_batch_create", "FEM_OP_BP35", "FEM_OP_BP30", "Server",
     "FEM_REQ_QUEUED", "FEM_REQ_RUNNING", "FEM_REQ_DONE", "FEM_REQ_FAILED",
@@ -111,6 +111,7 @@ def lib():
             L.fem_bp35_apply.argtypes = [vp, i64, dp, dbl, dp, dp, vp]
             L.fem_bp30_apply.argtypes = [vp, i64, dp, dbl, dp, dp, vp]
             L.fem_bp35_apply_f32.argtypes = [vp, i64, dp, dbl, dp, dp, vp]
+            L.fem_bp30_apply_f32.argtypes = [vp, i64, dp, dbl, dp, dp, vp]
             L.fem_bp35_jacobi.argtypes = [vp, i64, dp, dbl, dp, vp]
             L.fem_dot_scratch_size.restype = i64
             L.fem_dot.argtypes = [i64, dp, dp, dp, dp, vp]
@@ -148,7 +149,7 @@ def lib():
             L.fem_pcg_destroy.restype = None
             for f in ("fem_basis_setup", "fem_basis_tables", "fem_basis_host_tables",
                       "fem_mesh_geofacs", "fem_bp1_apply", "fem_bp35_apply", "fem_bp30_apply",
-                      "fem_basis_degree", "fem_bp35_apply_f32", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot",
+                      "fem_basis_degree", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot",
                       "fem_pcg_create", "fem_pcg_solve"):
                 getattr(L, f).restype = i32
             _lib = L
@@ -321,6 +322,20 @@ def fem_bp35_apply_f32(b: Basis, G, lam: float, q, out=None, stream=None):
     _dev32(out, "out", E * b.n ** 3)
     _check(lib().fem_bp35_apply_f32(b.handle, E, G.data_ptr(), float(lam), q.data_ptr(), out.data_ptr(),
                                     _stream(stream, q.device)), "fem_bp35_apply_f32")
+    return out
+
+
+def fem_bp30_apply_f32(b: Basis, G, lam: float, q, out=None, stream=None):
+    """BP3.0 matvec in FP32 (FP32 factors and field)."""
+    import torch
+    E = q.shape[0]
+    _dev32(q, "q", E * b.n ** 3)
+    _dev32(G, "G", E * 7 * b.m ** 3)
+    if out is None:
+        out = torch.empty_like(q)
+    _dev32(out, "out", E * b.n ** 3)
+    _check(lib().fem_bp30_apply_f32(b.handle, E, G.data_ptr(), float(lam), q.data_ptr(), out.data_ptr(),
+                                    _stream(stream, q.device)), "fem_bp30_apply_f32")
     return out
 
 

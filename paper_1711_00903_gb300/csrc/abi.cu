@@ -198,6 +198,16 @@ int fem_bp35_apply_f32(const fem_basis *b, int64_t E, const float *G, double lam
     return e == cudaSuccess ? FEM_OK : cuda_fail(e);
 }
 
+int fem_bp30_apply_f32(const fem_basis *b, int64_t E, const float *G, double lambda, const float *q, float *Aq,
+                       void *stream) {
+    if (!b || E < 0) return FEM_EINVAL;
+    if (E == 0) return FEM_OK;
+    if (!G || !q || !Aq || !aligned16(G) || !aligned16(q) || !aligned16(Aq)) return FEM_EINVAL;
+    if ((const void *)Aq == (const void *)q || (E + 1) > (int64_t)0x7fffffff) return FEM_EINVAL;
+    cudaError_t e = fem::launch_bp30_f32(b, E, G, lambda, q, Aq, (cudaStream_t)stream);
+    return e == cudaSuccess ? FEM_OK : cuda_fail(e);
+}
+
 int fem_bp30_apply(const fem_basis *b, int64_t E, const double *G, double lambda, const double *q,
                    double *Aq, void *stream) {
     const int c = check_apply(b, E, G, b ? 7 * cube(b->host.m) : 0, q, Aq);

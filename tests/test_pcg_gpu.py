@@ -66,6 +66,22 @@ def test_bp35_f32_matches_fp64_operator(N):
     assert _rel(got, ref) < 2e-6 * (N + 1)
 
 
+@pytest.mark.parametrize("N", [1, 2, 5, 7, 11, 15])
+def test_bp30_f32_matches_fp64_operator(N):
+    """FP32 BP3.0 matvec against the FP64 oracle on the same FP32-rounded
+    inputs; the bound grows with the length of the contraction chain."""
+    fem, torch = _fem(), _torch()
+    v = fem_synth.box_mesh(3)[:19]
+    E = v.shape[0]
+    G, _ = oracle.geofacs(N, oracle.KIND_BP30, v)
+    q = fem_synth.field(2, E, (N + 1) ** 3)
+    G32, q32 = G.astype(np.float32), q.astype(np.float32)
+    ref = oracle.bp30(N, G32.astype(np.float64), 1.0, q32.astype(np.float64))
+    b = fem.fem_basis_setup(N)
+    got = fem.fem_bp30_apply_f32(b, _dev(G32), 1.0, _dev(q32)).cpu().numpy().astype(np.float64)
+    assert _rel(got, ref) < 2e-6 * (N + 2)
+
+
 def test_dot_deterministic_and_exact():
     fem, torch = _fem(), _torch()
     x = fem_synth.field(11, 1, 3_000_001)[0]
