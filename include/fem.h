@@ -111,6 +111,18 @@ int fem_basis_host_tables(int N, double *r, double *w, double *rt, double *wt,
 int fem_mesh_geofacs(const fem_basis *b, fem_geo_kind kind, int64_t E,
                      const double *verts, double *geo, double *detJ_min, void *stream);
 
+/* The factors of all three operators of one mesh in one call: wJ for
+ * BP1.0 (E*NpG), G for BP3.5 (E*7*Np) and G for BP3.0 (E*7*NpG), each
+ * exactly as fem_mesh_geofacs writes it (same values bit for bit).  Any
+ * of the three outputs may be NULL (at least one must not be); outputs
+ * must not overlap each other or verts.  When both wJ and the BP3.0
+ * factors are asked for, one kernel writes both: BP1.0's wJ is the
+ * seventh BP3.0 factor at the same Gauss points (Section 4).  Asynchronous
+ * on stream, allocates nothing.  E == 0 enqueues nothing.
+ * Errors: FEM_EINVAL, FEM_ECUDA. */
+int fem_mesh_geofacs_set(const fem_basis *b, int64_t E, const double *verts, double *wJ,
+                         double *G35, double *G30, void *stream);
+
 /* BP1.0 mass matvec (Algorithm 3: interpolate GLL -> Gauss with
  * I x I x I (Algorithm 1), scale by wJ, project with I^T x I^T x I^T
  * (Algorithm 2)), six tensor contractions per element, IEEE FP64.
@@ -142,6 +154,25 @@ int fem_bp30_apply(const fem_basis *b, int64_t E, const double *G, double lambda
  * Errors: FEM_EINVAL, FEM_ECUDA. */
 int fem_bp35_apply_f32(const fem_basis *b, int64_t E, const float *G, double lambda,
                        const float *q, float *Aq, void *stream);
+
+/* Number of bounded device-side waits that gave up on the current device
+ * since the library was loaded or last reset (reset != 0 clears it).  The
+ * kernels that stage data with TMA bulk copies wait on mbarriers with an
+ * iteration limit (about a second) instead of spinning forever; a wait
+ * that gives up is counted here and the kernel's output is not to be
+ * trusted.  0 in normal operation.  Synchronous.
+ * Errors: FEM_EINVAL (count NULL), FEM_ECUDA. */
+int fem_wait_timeouts(unsigned long long *count, int reset);
+
+/* Roofline calibration stream with a chosen read:write ratio (Section 5
+ * calibrates the bandwidth roofline by a copy; the operators read several
+ * planes per plane written): dst[i] = sum over p = 0..planes-1, in that
+ * order, of src[p*n + i].  src device planes*n values, dst device n values,
+ * of word bytes each (8: double, 4: float); both 16-byte aligned, n*word a
+ * multiple of 16, 1 <= planes <= 32, no overlap.  Asynchronous on stream,
+ * allocates nothing.  Moves (planes + 1) * n * word bytes.
+ * Errors: FEM_EINVAL, FEM_ECUDA. */
+int fem_stream_sum(int planes, int64_t n, const void *src, void *dst, int word, void *stream);
 
 /* BP3.0 matvec in FP32 (Algorithm 5 with float data and FP32 arithmetic;
  * the inner operator of the mixed-precision BP3.0 solver).  Same layouts as

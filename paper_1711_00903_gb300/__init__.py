@@ -20,7 +20,7 @@ __all__ = [
     "FemError", "lib", "Basis", "fem_version", "fem_basis_setup", "fem_basis_free",
     "fem_basis_tables", "fem_basis_host_tables", "fem_mesh_geofacs", "fem_bp1_apply",
     "fem_bp35_apply", "fem_bp30_apply", "FEM_GEO_BP1", "FEM_GEO_BP35", "FEM_GEO_BP30",
-    "geo_shape", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot", "fem_dot_scratch_size", "Pcg",
+    "geo_shape", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot", "fem_dot_scratch_size", "Pcg",
     "fem_pcg_create", "fem_pcg_solve", "fem_pcg_destroy", "FEM_PCG_FP64", "FEM_PCG_MIXED",
     "Batch", "fem_batch_create", "FEM_OP_BP35", "FEM_OP_BP30", "Server",
     "FEM_REQ_QUEUED", "FEM_REQ_RUNNING", "FEM_REQ_DONE", "FEM_REQ_FAILED",
@@ -112,6 +112,9 @@ def lib():
             L.fem_bp30_apply.argtypes = [vp, i64, dp, dbl, dp, dp, vp]
             L.fem_bp35_apply_f32.argtypes = [vp, i64, dp, dbl, dp, dp, vp]
             L.fem_bp30_apply_f32.argtypes = [vp, i64, dp, dbl, dp, dp, vp]
+            L.fem_stream_sum.argtypes = [i32, i64, dp, dp, i32, vp]
+            L.fem_mesh_geofacs_set.argtypes = [vp, i64, dp, dp, dp, dp, vp]
+            L.fem_wait_timeouts.argtypes = [C.POINTER(C.c_ulonglong), i32]
             L.fem_bp35_jacobi.argtypes = [vp, i64, dp, dbl, dp, vp]
             L.fem_dot_scratch_size.restype = i64
             L.fem_dot.argtypes = [i64, dp, dp, dp, dp, vp]
@@ -149,7 +152,7 @@ def lib():
             L.fem_pcg_destroy.restype = None
             for f in ("fem_basis_setup", "fem_basis_tables", "fem_basis_host_tables",
                       "fem_mesh_geofacs", "fem_bp1_apply", "fem_bp35_apply", "fem_bp30_apply",
-                      "fem_basis_degree", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot",
+                      "fem_basis_degree", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot",
                       "fem_pcg_create", "fem_pcg_solve"):
                 getattr(L, f).restype = i32
             _lib = L
@@ -263,6 +266,25 @@ def fem_mesh_geofacs(b: Basis, kind: int, verts, geo=None, detJ_min=None, stream
     return geo
 
 
+def fem_mesh_geofacs_set(b: Basis, verts, wJ=None, G35=None, G30=None, stream=None):
+    """The factors of the three operators of one mesh in one call (any
+    subset; wJ and the BP3.0 factors share one kernel).  Outputs passed as
+    None are not computed.  Returns (wJ, G35, G30)."""
+    E = verts.shape[0] if verts.dim() else 0
+    _dev(verts, "verts", E * 24)
+    ptrs = []
+    for t, kind, name in ((wJ, FEM_GEO_BP1, "wJ"), (G35, FEM_GEO_BP35, "G35"), (G30, FEM_GEO_BP30, "G30")):
+        if t is None:
+            ptrs.append(None)
+        else:
+            import torch
+            _dev(t, name, int(torch.Size(geo_shape(b, kind, E)).numel()))
+            ptrs.append(t.data_ptr())
+    _check(lib().fem_mesh_geofacs_set(b.handle, E, verts.data_ptr(), *ptrs, _stream(stream, verts.device)),
+           "fem_mesh_geofacs_set")
+    return wJ, G35, G30
+
+
 def _apply_out(q, out, b):
     import torch
     E = q.shape[0]
@@ -322,6 +344,30 @@ def fem_bp35_apply_f32(b: Basis, G, lam: float, q, out=None, stream=None):
     _dev32(out, "out", E * b.n ** 3)
     _check(lib().fem_bp35_apply_f32(b.handle, E, G.data_ptr(), float(lam), q.data_ptr(), out.data_ptr(),
                                     _stream(stream, q.device)), "fem_bp35_apply_f32")
+    return out
+
+
+def fem_wait_timeouts(reset: bool = False) -> int:
+    """Bounded device-side waits that gave up (0 in normal operation)."""
+    c = C.c_ulonglong(0)
+    _check(lib().fem_wait_timeouts(C.byref(c), 1 if reset else 0), "fem_wait_timeouts")
+    return int(c.value)
+
+
+def fem_stream_sum(src, out=None, stream=None):
+    """Roofline calibration stream: out = src.sum(0) over the planes of a
+    (planes, n) float64 or float32 CUDA tensor, in plane order."""
+    import torch
+    if not isinstance(src, torch.Tensor) or not src.is_cuda or src.dim() != 2 or not src.is_contiguous() \
+            or src.dtype not in (torch.float64, torch.float32):
+        raise TypeError("src must be a contiguous 2-D float64/float32 CUDA tensor")
+    planes, n = src.shape
+    if out is None:
+        out = torch.empty(n, dtype=src.dtype, device=src.device)
+    if not out.is_cuda or out.dtype != src.dtype or out.numel() != n or not out.is_contiguous():
+        raise TypeError("out must be a contiguous CUDA tensor of n values of src's dtype")
+    _check(lib().fem_stream_sum(int(planes), int(n), src.data_ptr(), out.data_ptr(), src.element_size(),
+                                _stream(stream, src.device)), "fem_stream_sum")
     return out
 
 

@@ -170,6 +170,35 @@ int fem_mesh_geofacs(const fem_basis *b, fem_geo_kind kind, int64_t E, const dou
     return e == cudaSuccess ? FEM_OK : cuda_fail(e);
 }
 
+int fem_mesh_geofacs_set(const fem_basis *b, int64_t E, const double *verts, double *wJ, double *G35, double *G30,
+                         void *stream) {
+    if (!b || E < 0) return FEM_EINVAL;
+    if (!wJ && !G35 && !G30) return FEM_EINVAL;
+    if (E == 0) return FEM_OK;
+    if (!verts || !aligned16(verts) || E + 1 > (int64_t)0x7fffffff) return FEM_EINVAL;
+    const int64_t nw = E * cube(b->host.m), n35 = E * 7 * cube(b->host.n), n30 = E * 7 * cube(b->host.m);
+    const double *outs[3] = {wJ, G35, G30};
+    const int64_t sizes[3] = {nw, n35, n30};
+    for (int i = 0; i < 3; i++) {
+        if (!outs[i]) continue;
+        if (!aligned16(outs[i]) || overlap(outs[i], sizes[i], verts, E * 24)) return FEM_EINVAL;
+        for (int j = 0; j < i; j++)
+            if (outs[j] && overlap(outs[i], sizes[i], outs[j], sizes[j])) return FEM_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (G35) e = fem::launch_geofacs(b, FEM_GEO_BP35, E, verts, G35, nullptr, s);
+    if (e == cudaSuccess) {
+        if (G30 && wJ)
+            e = fem::launch_geofacs_gauss_pair(b, E, verts, G30, wJ, s);
+        else if (G30)
+            e = fem::launch_geofacs(b, FEM_GEO_BP30, E, verts, G30, nullptr, s);
+        else if (wJ)
+            e = fem::launch_geofacs(b, FEM_GEO_BP1, E, verts, wJ, nullptr, s);
+    }
+    return e == cudaSuccess ? FEM_OK : cuda_fail(e);
+}
+
 int fem_bp1_apply(const fem_basis *b, int64_t E, const double *wJ, const double *q, double *Mq,
                   void *stream) {
     const int c = check_apply(b, E, wJ, b ? cube(b->host.m) : 0, q, Mq);
@@ -195,6 +224,23 @@ int fem_bp35_apply_f32(const fem_basis *b, int64_t E, const float *G, double lam
     if ((const void *)Aq == (const void *)q || (E + 1) > (int64_t)0x7fffffff) return FEM_EINVAL;
     (void)np;
     cudaError_t e = fem::launch_bp35_f32(b, E, G, lambda, q, Aq, (cudaStream_t)stream);
+    return e == cudaSuccess ? FEM_OK : cuda_fail(e);
+}
+
+int fem_wait_timeouts(unsigned long long *count, int reset) {
+    if (!count) return FEM_EINVAL;
+    cudaError_t e = fem::wait_timeouts_bp35(count, reset != 0);
+    return e == cudaSuccess ? FEM_OK : cuda_fail(e);
+}
+
+int fem_stream_sum(int planes, int64_t n, const void *src, void *dst, int word, void *stream) {
+    if (planes < 1 || planes > fem::stream_max_planes() || n < 0 || (word != 4 && word != 8)) return FEM_EINVAL;
+    if (n == 0) return FEM_OK;
+    if (!src || !dst || !aligned16(src) || !aligned16(dst) || (n * word) % 16 != 0) return FEM_EINVAL;
+    const char *s0 = (const char *)src, *d0 = (const char *)dst;
+    const int64_t sb = (int64_t)planes * n * word, db = n * word;
+    if (d0 < s0 + sb && s0 < d0 + db) return FEM_EINVAL;  // overlapping buffers
+    cudaError_t e = fem::launch_stream_sum(planes, n, src, dst, word, (cudaStream_t)stream);
     return e == cudaSuccess ? FEM_OK : cuda_fail(e);
 }
 

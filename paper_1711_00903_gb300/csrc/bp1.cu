@@ -34,9 +34,10 @@ struct Bp1Cfg {
     static constexpr int threads = ((m * m * EPB + 31) / 32) * 32;
     static constexpr int smem = EPB * per * 8;
     static constexpr int oI = fold_offset(N, kFoldI), oIT = fold_offset(N, kFoldIT);
-    // two resident blocks per SM let one block's barriers overlap the other's
-    // FP64 work; above N = 8 the register cap would spill heavily
-    static constexpr int min_blocks = (N <= 8) ? 2 : 1;
+    // three resident blocks per SM let one block's barriers overlap the
+    // others' FP64 work; the register cap this implies costs a few spills
+    // at high degree but was measured faster at every degree
+    static constexpr int min_blocks = 3;
 };
 
 template <int N>

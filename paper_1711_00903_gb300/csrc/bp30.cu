@@ -24,17 +24,52 @@
 namespace fem {
 namespace {
 
+// Minimum resident blocks per SM that the register allocation must allow
+// (0: the compiler's own heuristic); see bp35.cu.  Chosen per precision and
+// degree from the operator sweep on GB300.
+template <typename T, int N>
+constexpr int bp30_min_blocks() {
+    if (sizeof(T) == 8) return (N >= 9 && N <= 14) ? 2 : 0;
+    if (N >= 9 && N <= 12) return 4;
+    if (N == 13) return 3;
+    if (N == 15) return 2;
+    return 0;
+}
+
 template <typename T, int N, bool PCG>
-__global__ void __launch_bounds__(Bp30Cfg<N, T>::threads)
-bp30_kernel(int64_t E, const T *__restrict__ G, double lambda, const T *__restrict__ q, T *__restrict__ Aq,
-            const T *__restrict__ z, T *__restrict__ p, const double *__restrict__ beta,
-            double *__restrict__ partials) {
+__device__ __forceinline__ void bp30_entry(int64_t E, const T *__restrict__ G, double lambda, const T *__restrict__ q,
+                                           T *__restrict__ Aq, const T *__restrict__ z, T *__restrict__ p,
+                                           const double *__restrict__ beta, double *__restrict__ partials) {
     using C = Bp30Cfg<N, T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t e0 = (int64_t)blockIdx.x * C::EPB;
     const int nel = (int)((E - e0) < C::EPB ? (E - e0) : C::EPB);
     bp30_block<N, C::EPB, T, PCG>(reinterpret_cast<T *>(smem_raw), e0, nel, G, lambda, q, Aq, z, p, beta,
                                   PCG ? partials + blockIdx.x : nullptr);
+}
+
+template <typename T, int N, bool PCG>
+__global__ void __launch_bounds__(Bp30Cfg<N, T>::threads)
+bp30_kernel(int64_t E, const T *__restrict__ G, double lambda, const T *__restrict__ q, T *__restrict__ Aq,
+            const T *__restrict__ z, T *__restrict__ p, const double *__restrict__ beta,
+            double *__restrict__ partials) {
+    bp30_entry<T, N, PCG>(E, G, lambda, q, Aq, z, p, beta, partials);
+}
+
+template <typename T, int N, bool PCG>
+__global__ void __launch_bounds__(Bp30Cfg<N, T>::threads, bp30_min_blocks<T, N>())
+bp30_kernel_capped(int64_t E, const T *__restrict__ G, double lambda, const T *__restrict__ q, T *__restrict__ Aq,
+                   const T *__restrict__ z, T *__restrict__ p, const double *__restrict__ beta,
+                   double *__restrict__ partials) {
+    bp30_entry<T, N, PCG>(E, G, lambda, q, Aq, z, p, beta, partials);
+}
+
+template <typename T, int N, bool PCG>
+constexpr auto bp30_fn() {
+    if constexpr (bp30_min_blocks<T, N>() > 0)
+        return &bp30_kernel_capped<T, N, PCG>;
+    else
+        return &bp30_kernel<T, N, PCG>;
 }
 
 FEM_DEFINE_FOLD_UPLOAD(upload_fold_bp30_tu)
@@ -47,8 +82,8 @@ struct Bp30LaunchT {
                                const double *beta, double *partials, cudaStream_t s) {
             using C = Bp30Cfg<N, T>;
             const int64_t blocks = (E + C::EPB - 1) / C::EPB;
-            bp30_kernel<T, N, PCG><<<(unsigned)blocks, C::threads, C::smem, s>>>(E, G, lambda, q, Aq, z, p, beta,
-                                                                                partials);
+            bp30_fn<T, N, PCG>()<<<(unsigned)blocks, C::threads, C::smem, s>>>(E, G, lambda, q, Aq, z, p, beta,
+                                                                              partials);
             return cudaGetLastError();
         }
     };
@@ -67,7 +102,7 @@ template <int N>
 struct Bp30Prepare {
     template <typename T, bool PCG>
     static cudaError_t one() {
-        return cudaFuncSetAttribute(bp30_kernel<T, N, PCG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        return cudaFuncSetAttribute(bp30_fn<T, N, PCG>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     Bp30Cfg<N, T>::smem);
     }
     static cudaError_t run() {

@@ -24,17 +24,51 @@
 namespace fem {
 namespace {
 
+// Minimum resident blocks per SM that the register allocation must allow
+// (0: the compiler's own heuristic).  At high degree the fully unrolled line
+// kernels take up to 255 registers and leave one block per SM; capping them
+// trades a few spills for latency hiding.  Chosen per precision and degree
+// from the operator sweep on GB300.
+template <typename T, int N>
+constexpr int bp35_min_blocks() {
+    if (sizeof(T) == 8) return N >= 10 ? 3 : 0;
+    return N == 15 ? 3 : 0;
+}
+
+template <typename T, int N, bool PCG>
+__device__ __forceinline__ void bp35_entry(int64_t E, const T *__restrict__ G, double lambda, const T *__restrict__ q,
+                                           T *__restrict__ Aq, const T *__restrict__ z, T *__restrict__ p,
+                                           const double *__restrict__ beta, double *__restrict__ partials) {
+    using C = Bp35Cfg<T, N>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t e0 = (int64_t)blockIdx.x * C::EPB;
+    const int nel = (int)((E - e0) < C::EPB ? (E - e0) : C::EPB);
+    bp35_block<T, N, C::EPB, PCG, C::STAGE_G>(smem_raw, e0, nel, G, lambda, q, Aq, z, p, beta,
+                                              PCG ? partials + blockIdx.x : nullptr);
+}
+
 template <typename T, int N, bool PCG>
 __global__ void __launch_bounds__(Bp35Cfg<T, N>::threads)
 bp35_kernel(int64_t E, const T *__restrict__ G, double lambda, const T *__restrict__ q, T *__restrict__ Aq,
             const T *__restrict__ z, T *__restrict__ p, const double *__restrict__ beta,
             double *__restrict__ partials) {
-    using C = Bp35Cfg<T, N>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int64_t e0 = (int64_t)blockIdx.x * C::EPB;
-    const int nel = (int)((E - e0) < C::EPB ? (E - e0) : C::EPB);
-    bp35_block<T, N, C::EPB, PCG>(smem_raw, e0, nel, G, lambda, q, Aq, z, p, beta,
-                                  PCG ? partials + blockIdx.x : nullptr);
+    bp35_entry<T, N, PCG>(E, G, lambda, q, Aq, z, p, beta, partials);
+}
+
+template <typename T, int N, bool PCG>
+__global__ void __launch_bounds__(Bp35Cfg<T, N>::threads, bp35_min_blocks<T, N>())
+bp35_kernel_capped(int64_t E, const T *__restrict__ G, double lambda, const T *__restrict__ q, T *__restrict__ Aq,
+                   const T *__restrict__ z, T *__restrict__ p, const double *__restrict__ beta,
+                   double *__restrict__ partials) {
+    bp35_entry<T, N, PCG>(E, G, lambda, q, Aq, z, p, beta, partials);
+}
+
+template <typename T, int N, bool PCG>
+constexpr auto bp35_fn() {
+    if constexpr (bp35_min_blocks<T, N>() > 0)
+        return &bp35_kernel_capped<T, N, PCG>;
+    else
+        return &bp35_kernel<T, N, PCG>;
 }
 
 template <int N>
@@ -43,7 +77,7 @@ struct Bp35Launch {
                            cudaStream_t s) {
         using C = Bp35Cfg<double, N>;
         const int64_t blocks = (E + C::EPB - 1) / C::EPB;
-        bp35_kernel<double, N, false><<<(unsigned)blocks, C::threads, C::smem, s>>>(
+        bp35_fn<double, N, false>()<<<(unsigned)blocks, C::threads, C::smem, s>>>(
             E, G, lambda, q, Aq, nullptr, nullptr, nullptr, nullptr);
         return cudaGetLastError();
     }
@@ -55,7 +89,7 @@ struct Bp35F32Launch {
                            cudaStream_t s) {
         using C = Bp35Cfg<float, N>;
         const int64_t blocks = (E + C::EPB - 1) / C::EPB;
-        bp35_kernel<float, N, false><<<(unsigned)blocks, C::threads, C::smem, s>>>(
+        bp35_fn<float, N, false>()<<<(unsigned)blocks, C::threads, C::smem, s>>>(
             E, G, lambda, q, Aq, nullptr, nullptr, nullptr, nullptr);
         return cudaGetLastError();
     }
@@ -69,8 +103,8 @@ struct Bp35PcgLaunchT {
                                T *Ap, double *partials, cudaStream_t s) {
             using C = Bp35Cfg<T, N>;
             const int64_t blocks = (E + C::EPB - 1) / C::EPB;
-            bp35_kernel<T, N, true><<<(unsigned)blocks, C::threads, C::smem, s>>>(E, G, lambda, nullptr, Ap, z,
-                                                                                 p, beta, partials);
+            bp35_fn<T, N, true>()<<<(unsigned)blocks, C::threads, C::smem, s>>>(E, G, lambda, nullptr, Ap, z, p,
+                                                                               beta, partials);
             return cudaGetLastError();
         }
     };
@@ -91,7 +125,7 @@ template <int N>
 struct Bp35Prepare {
     template <typename T, bool PCG>
     static cudaError_t one() {
-        return cudaFuncSetAttribute(bp35_kernel<T, N, PCG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        return cudaFuncSetAttribute(bp35_fn<T, N, PCG>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     Bp35Cfg<T, N>::smem);
     }
     static cudaError_t run() {
@@ -106,6 +140,8 @@ struct Bp35Prepare {
 FEM_DEFINE_FOLD_UPLOAD(upload_fold_bp35_tu)
 
 }  // namespace
+
+FEM_DEFINE_WAIT_COUNTER(wait_timeouts_bp35)
 
 cudaError_t launch_bp35(const fem_basis *b, int64_t E, const double *G, double lambda, const double *q,
                         double *Aq, cudaStream_t s) {

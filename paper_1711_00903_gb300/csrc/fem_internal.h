@@ -66,6 +66,8 @@ cudaError_t launch_bp30(const fem_basis *b, int64_t E, const double *G, double l
 cudaError_t prepare_bp1(int N, const double *fold_table);
 cudaError_t prepare_bp35(int N, const double *fold_table);
 cudaError_t prepare_bp30(int N, const double *fold_table);
+cudaError_t launch_geofacs_gauss_pair(const fem_basis *b, int64_t E, const double *verts, double *G30, double *wJ,
+                                      cudaStream_t s);
 cudaError_t prepare_geofacs(int N);
 
 // Host copy of the folded operator table of all degrees 1..15 (built once).
@@ -85,6 +87,9 @@ cudaError_t launch_bp30_pcg_f32(const fem_basis *b, int64_t E, const float *G, d
 int64_t bp30_blocks(int N, int64_t E, bool f32);
 
 // FP32 BP3.5 matvec (the inner operator of the mixed-precision solver).
+cudaError_t wait_timeouts_bp35(unsigned long long *count, bool reset);
+cudaError_t launch_stream_sum(int planes, int64_t n, const void *src, void *dst, int word, cudaStream_t s);
+int stream_max_planes();
 cudaError_t launch_bp35_f32(const fem_basis *b, int64_t E, const float *G, double lambda, const float *q,
                             float *Aq, cudaStream_t s);
 cudaError_t launch_dot(int64_t n, const double *x, const double *y, double *result, double *scratch,

@@ -40,12 +40,15 @@ __device__ __forceinline__ double recip(double d) {
     return fma(r, e, r);
 }
 
-// kind: 1 = wJ only, otherwise 7 planes; MIN: also the per-element minimum |J|.
+// kind: 1 = wJ only, 2 and 3 = 7 planes, 4 = 7 planes and, in wj2, a copy
+// of the wJ plane in the BP1.0 layout (BP3.0 and BP1.0 factors live at the
+// same Gauss points, so one pass serves both); MIN: also the per-element
+// minimum |J|.
 template <int qn, int kind, bool MIN>
-__global__ void __launch_bounds__(GeoCfg<qn>::threads)
-geofacs_kernel(int64_t E, const double *__restrict__ nodes, const double *__restrict__ weights,
-               const double *__restrict__ verts, double *__restrict__ geo,
-               double *__restrict__ detJ_min) {
+__device__ __forceinline__ void geofacs_body(int64_t E, const double *__restrict__ nodes,
+                                             const double *__restrict__ weights, const double *__restrict__ verts,
+                                             double *__restrict__ geo, double *__restrict__ detJ_min,
+                                             double *__restrict__ wj2) {
     using C = GeoCfg<qn>;
     constexpr int QP = C::QP, qq = C::qq, EPB = C::EPB;
     constexpr int PER = pad2(24 + 9 * qq + C::SD);
@@ -166,6 +169,7 @@ geofacs_kernel(int64_t E, const double *__restrict__ nodes, const double *__rest
                 g[4 * QP] = f * (Cs0 * Ct0 + Cs1 * Ct1 + Cs2 * Ct2);
                 g[5 * QP] = f * (Ct0 * Ct0 + Ct1 * Ct1 + Ct2 * Ct2);
                 g[6 * QP] = W * det;
+                if (kind == 4) wj2[e * (int64_t)QP + c * qq + ab] = W * det;
             }
         }
     }
@@ -180,6 +184,35 @@ geofacs_kernel(int64_t E, const double *__restrict__ nodes, const double *__rest
     }
 }
 
+// Five resident blocks per SM (a register cap of about 48) was measured
+// faster than the compiler's own choice (58 registers, four blocks) up to
+// 10 points per direction; above that the cap would spill.
+constexpr int geo_min_blocks(int qn) { return qn <= 10 ? 5 : 0; }
+
+template <int qn, int kind, bool MIN>
+__global__ void __launch_bounds__(GeoCfg<qn>::threads)
+geofacs_kernel(int64_t E, const double *__restrict__ nodes, const double *__restrict__ weights,
+               const double *__restrict__ verts, double *__restrict__ geo, double *__restrict__ detJ_min,
+               double *__restrict__ wj2) {
+    geofacs_body<qn, kind, MIN>(E, nodes, weights, verts, geo, detJ_min, wj2);
+}
+
+template <int qn, int kind, bool MIN>
+__global__ void __launch_bounds__(GeoCfg<qn>::threads, geo_min_blocks(qn) > 0 ? geo_min_blocks(qn) : 1)
+geofacs_kernel_capped(int64_t E, const double *__restrict__ nodes, const double *__restrict__ weights,
+                      const double *__restrict__ verts, double *__restrict__ geo, double *__restrict__ detJ_min,
+                      double *__restrict__ wj2) {
+    geofacs_body<qn, kind, MIN>(E, nodes, weights, verts, geo, detJ_min, wj2);
+}
+
+template <int qn, int kind, bool MIN>
+constexpr auto geo_fn() {
+    if constexpr (geo_min_blocks(qn) > 0)
+        return &geofacs_kernel_capped<qn, kind, MIN>;
+    else
+        return &geofacs_kernel<qn, kind, MIN>;
+}
+
 template <int N>
 struct GeoLaunch {
     static cudaError_t run(const fem_basis *b, int kind, int64_t E, const double *verts, double *geo,
@@ -188,17 +221,30 @@ struct GeoLaunch {
         if (kind == FEM_GEO_BP35) {
             using C = GeoCfg<N + 1>;
             const int64_t blocks = (E + C::EPB - 1) / C::EPB;
-            auto k = detJ_min ? geofacs_kernel<N + 1, 2, true> : geofacs_kernel<N + 1, 2, false>;
+            auto k = detJ_min ? geo_fn<N + 1, 2, true>() : geo_fn<N + 1, 2, false>();
             k<<<(unsigned)blocks, C::threads, C::smem, s>>>(E, b->d_ops + L.offR(), b->d_ops + L.offW(), verts,
-                                                            geo, detJ_min);
+                                                            geo, detJ_min, nullptr);
         } else {
             using C = GeoCfg<N + 2>;
             const int64_t blocks = (E + C::EPB - 1) / C::EPB;
             const double *x = b->d_ops + L.offRt(), *w = b->d_ops + L.offWt();
-            auto k = (kind == FEM_GEO_BP1) ? (detJ_min ? geofacs_kernel<N + 2, 1, true> : geofacs_kernel<N + 2, 1, false>)
-                                           : (detJ_min ? geofacs_kernel<N + 2, 3, true> : geofacs_kernel<N + 2, 3, false>);
-            k<<<(unsigned)blocks, C::threads, C::smem, s>>>(E, x, w, verts, geo, detJ_min);
+            auto k = (kind == FEM_GEO_BP1) ? (detJ_min ? geo_fn<N + 2, 1, true>() : geo_fn<N + 2, 1, false>())
+                                           : (detJ_min ? geo_fn<N + 2, 3, true>() : geo_fn<N + 2, 3, false>());
+            k<<<(unsigned)blocks, C::threads, C::smem, s>>>(E, x, w, verts, geo, detJ_min, nullptr);
         }
+        return cudaGetLastError();
+    }
+};
+
+template <int N>
+struct GeoPairLaunch {
+    static cudaError_t run(const fem_basis *b, int64_t E, const double *verts, double *G30, double *wJ,
+                           cudaStream_t s) {
+        const OpsLayout L{N + 1, N + 2};
+        using C = GeoCfg<N + 2>;
+        const int64_t blocks = (E + C::EPB - 1) / C::EPB;
+        geo_fn<N + 2, 4, false>()<<<(unsigned)blocks, C::threads, C::smem, s>>>(
+            E, b->d_ops + L.offRt(), b->d_ops + L.offWt(), verts, G30, nullptr, wJ);
         return cudaGetLastError();
     }
 };
@@ -207,7 +253,7 @@ template <int N>
 struct GeoPrepare {
     template <int qn, int kind, bool MIN>
     static cudaError_t one() {
-        return cudaFuncSetAttribute(geofacs_kernel<qn, kind, MIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        return cudaFuncSetAttribute(geo_fn<qn, kind, MIN>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     GeoCfg<qn>::smem);
     }
     static cudaError_t run() {
@@ -218,6 +264,7 @@ struct GeoPrepare {
         if (e == cudaSuccess) e = one<N + 2, 1, true>();
         if (e == cudaSuccess) e = one<N + 2, 3, false>();
         if (e == cudaSuccess) e = one<N + 2, 3, true>();
+        if (e == cudaSuccess) e = one<N + 2, 4, false>();
         return e;
     }
 };
@@ -227,6 +274,11 @@ struct GeoPrepare {
 cudaError_t launch_geofacs(const fem_basis *b, int kind, int64_t E, const double *verts, double *geo,
                            double *detJ_min, cudaStream_t s) {
     return dispatch_degree<GeoLaunch>(b->host.N, b, kind, E, verts, geo, detJ_min, s);
+}
+
+cudaError_t launch_geofacs_gauss_pair(const fem_basis *b, int64_t E, const double *verts, double *G30, double *wJ,
+                                      cudaStream_t s) {
+    return dispatch_degree<GeoPairLaunch>(b->host.N, b, E, verts, G30, wJ, s);
 }
 
 cudaError_t prepare_geofacs(int N) { return dispatch_degree<GeoPrepare>(N); }

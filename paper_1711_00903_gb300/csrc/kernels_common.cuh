@@ -51,6 +51,66 @@ __device__ __forceinline__ void prefetch_l2(const void *p, long long bytes) {
     }
 }
 
+// ---- mbarrier and TMA bulk copies (global -> shared), CTA scope.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// Initialises a shared-memory mbarrier expecting `count` arrivals and makes
+// the initialisation visible to the asynchronous (TMA) proxy.
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+// One arrival that also announces `bytes` of asynchronous transfer.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// TMA bulk copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned) from global to this CTA's shared memory, completing on bar.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Bounded wait for the completion of phase `parity` of bar: at most
+// kMbarWaitTries probes, each suspending the thread for up to about 1 us,
+// so a wait gives up after about a second instead of hanging.  Returns
+// whether the phase completed.
+constexpr unsigned kMbarWaitTries = 1u << 20;
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+    for (unsigned it = 0; it < kMbarWaitTries; it++) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity), "r"(1000u)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// Count of bounded waits that gave up, one per translation unit (no
+// relocatable device code); fem_wait_timeouts adds them up.
+static __device__ unsigned long long g_wait_timeouts;
+
+// Host side: reads (and with reset, clears) this translation unit's count.
+#define FEM_DEFINE_WAIT_COUNTER(fn)                                                          \
+    cudaError_t fn(unsigned long long *count, bool reset) {                                  \
+        cudaError_t e = cudaMemcpyFromSymbol(count, g_wait_timeouts, sizeof(*count));        \
+        if (e == cudaSuccess && reset) {                                                     \
+            const unsigned long long zero = 0;                                               \
+            e = cudaMemcpyToSymbol(g_wait_timeouts, &zero, sizeof(zero));                    \
+        }                                                                                    \
+        return e;                                                                            \
+    }
+
 // Fused multiply-add in the precision of the operands.
 __device__ __forceinline__ double fmx(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmx(float a, float b, float c) { return fmaf(a, b, c); }

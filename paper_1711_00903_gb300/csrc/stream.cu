@@ -1,0 +1,70 @@
+// Roofline calibration kernel: a stream with a chosen read:write ratio.
+//
+// Section 5 of the paper calibrates its bandwidth roofline with a plain
+// device-to-device copy (one byte read per byte written).  The operators
+// read several arrays for each one they write (BP3.5: eight planes of N_p
+// values per plane written), so a second calibration point is a stream
+// that reads k planes and writes their sum, dst[i] = sum_p src[p n + i],
+// summed in plane order p = 0, 1, ..., k-1.
+//
+// GB300 design: 16-byte vector loads and stores (double2 / float4; the
+// plane length is a multiple of the vector width, checked by the caller), a
+// grid-stride loop over a grid of 152 SMs x 8 blocks, and the loads of an
+// output vector issued in groups of eight before their adds, so that up to
+// eight independent HBM requests are in flight per thread.
+#include "fem_internal.h"
+#include "kernels_common.cuh"
+
+namespace fem {
+namespace {
+
+constexpr int kStreamThreads = 256;
+constexpr int kStreamBlocks = 152 * 8;
+constexpr int kMaxPlanes = 32;
+
+template <typename V, typename T, int W>
+__global__ void __launch_bounds__(kStreamThreads)
+stream_sum_kernel(int planes, int64_t n, const T *__restrict__ src, T *__restrict__ dst) {
+    constexpr int kChunk = 8;  // loads issued before their adds
+    const int64_t nv = n / W;  // vectors per plane (n is a multiple of W)
+    const V *s = reinterpret_cast<const V *>(src);
+    V *d = reinterpret_cast<V *>(dst);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+        V acc;
+        for (int p0 = 0; p0 < planes; p0 += kChunk) {
+            V v[kChunk];
+#pragma unroll
+            for (int c = 0; c < kChunk; c++)
+                if (p0 + c < planes) v[c] = __ldcs(s + (int64_t)(p0 + c) * nv + i);
+#pragma unroll
+            for (int c = 0; c < kChunk; c++) {
+                if (p0 + c >= planes) break;
+                if (p0 + c == 0) {
+                    acc = v[0];
+                } else {
+                    const T *pv = reinterpret_cast<const T *>(&v[c]);
+                    T *pa = reinterpret_cast<T *>(&acc);
+#pragma unroll
+                    for (int w = 0; w < W; w++) pa[w] += pv[w];
+                }
+            }
+        }
+        __stcs(d + i, acc);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_stream_sum(int planes, int64_t n, const void *src, void *dst, int word, cudaStream_t s) {
+    if (word == 8)
+        stream_sum_kernel<double2, double, 2><<<kStreamBlocks, kStreamThreads, 0, s>>>(
+            planes, n, (const double *)src, (double *)dst);
+    else
+        stream_sum_kernel<float4, float, 4><<<kStreamBlocks, kStreamThreads, 0, s>>>(
+            planes, n, (const float *)src, (float *)dst);
+    return cudaGetLastError();
+}
+
+int stream_max_planes() { return kMaxPlanes; }
+
+}  // namespace fem

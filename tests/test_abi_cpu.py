@@ -74,6 +74,18 @@ def test_argument_errors_need_no_gpu():
     assert L.fem_basis_degree(None) == fem.FEM_EINVAL
     assert L.fem_basis_tables(None, *([None] * 7)) == fem.FEM_EINVAL
     L.fem_basis_free(None)  # accepted
+    assert L.fem_bp35_apply_f32(None, 1, p, 1.0, p, p, None) == fem.FEM_EINVAL
+    assert L.fem_bp30_apply_f32(None, 1, p, 1.0, p, p, None) == fem.FEM_EINVAL
+    # calibration stream: plane count, word size, vector alignment, overlap
+    a, b = C.c_void_p(1 << 20), C.c_void_p(1 << 24)
+    assert L.fem_stream_sum(0, 64, a, b, 8, None) == fem.FEM_EINVAL
+    assert L.fem_stream_sum(33, 64, a, b, 8, None) == fem.FEM_EINVAL
+    assert L.fem_stream_sum(2, 64, a, b, 2, None) == fem.FEM_EINVAL
+    assert L.fem_stream_sum(2, 3, a, b, 8, None) == fem.FEM_EINVAL
+    assert L.fem_stream_sum(2, 64, C.c_void_p((1 << 20) + 8), b, 8, None) == fem.FEM_EINVAL
+    assert L.fem_stream_sum(2, 64, a, C.c_void_p((1 << 20) + 512), 8, None) == fem.FEM_EINVAL
+    assert L.fem_stream_sum(2, 0, a, b, 8, None) == 0  # nothing to do
+    assert L.fem_mesh_geofacs_set(None, 1, p, p, None, None, None) == fem.FEM_EINVAL
 
 
 def test_binding_refuses_host_tensors():

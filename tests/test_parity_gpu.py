@@ -273,3 +273,45 @@ def test_small_bp1_config_full_oracle(bases):
     b = bases[N]
     got = fem.fem_bp1_apply(b, fem.fem_mesh_geofacs(b, 1, _dev(v)), _dev(q)).cpu().numpy()
     assert _rel(got, ref) < TOL
+
+
+@pytest.mark.parametrize("dtype,planes,n", [("float64", 1, 2), ("float64", 8, 4096 * 3 + 2),
+                                            ("float64", 25, 1 << 16), ("float32", 3, 4),
+                                            ("float32", 9, 100_004), ("float32", 32, 1 << 15)])
+def test_stream_sum_calibration_kernel(dtype, planes, n):
+    """The roofline calibration stream sums its planes in plane order: bit
+    for bit the sequential sum on the host."""
+    import torch
+    fem = _fem()
+    src = fem_synth.field(31, planes, n).astype(dtype)
+    ref = src[0].copy()
+    for p in range(1, planes):
+        ref = (ref + src[p]).astype(dtype)
+    got = fem.fem_stream_sum(torch.from_numpy(src).to("cuda")).cpu().numpy()
+    assert got.dtype == np.dtype(dtype)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("N", [1, 4, 7, 15])
+def test_geofacs_set_equals_single_kind_calls(N):
+    """All three factor sets in one call (wJ from the BP3.0 kernel) are the
+    single-kind results bit for bit, and every subset works."""
+    import torch
+    fem = _fem()
+    v = fem_synth.box_mesh(3)
+    E = v.shape[0]
+    b = fem.fem_basis_setup(N)
+    vd = torch.from_numpy(v).to("cuda")
+    ref = [fem.fem_mesh_geofacs(b, k, vd) for k in (1, 2, 3)]
+    outs = [torch.full(fem.geo_shape(b, k, E), float("nan"), dtype=torch.float64, device="cuda") for k in (1, 2, 3)]
+    fem.fem_mesh_geofacs_set(b, vd, *outs)
+    for got, want in zip(outs, ref):
+        assert torch.equal(got, want)
+    w1 = torch.zeros_like(outs[0])
+    fem.fem_mesh_geofacs_set(b, vd, wJ=w1)
+    assert torch.equal(w1, ref[0])
+    g3 = torch.zeros_like(outs[2])
+    fem.fem_mesh_geofacs_set(b, vd, G30=g3)
+    assert torch.equal(g3, ref[2])
+    wJo, _ = oracle.geofacs(N, oracle.KIND_BP1, v)
+    assert _rel(outs[0].cpu().numpy(), wJo) < 1e-13

@@ -50,7 +50,7 @@ def test_jacobi_diagonal(N):
     assert _rel(got, ref) < 1e-12
 
 
-@pytest.mark.parametrize("N", [1, 2, 5, 7, 11, 15])
+@pytest.mark.parametrize("N", [1, 2, 3, 5, 7, 9, 11, 13, 15])
 def test_bp35_f32_matches_fp64_operator(N):
     """FP32 matvec against the FP64 oracle applied to the same FP32-rounded
     inputs: the difference is FP32 rounding of the arithmetic only."""
@@ -80,6 +80,25 @@ def test_bp30_f32_matches_fp64_operator(N):
     b = fem.fem_basis_setup(N)
     got = fem.fem_bp30_apply_f32(b, _dev(G32), 1.0, _dev(q32)).cpu().numpy().astype(np.float64)
     assert _rel(got, ref) < 2e-6 * (N + 2)
+
+
+def test_staged_f32_operator_ragged_blocks_and_no_wait_timeouts():
+    """The FP32 BP3.5 kernel that stages the factors with TMA bulk copies
+    (odd degrees): an element count that leaves the last block partly
+    filled, results equal to the oracle's on the same FP32 inputs, and no
+    bounded wait gave up."""
+    fem, torch = _fem(), _torch()
+    fem.fem_wait_timeouts(reset=True)
+    for N, E in ((7, 1), (7, 37), (3, 33), (11, 3)):
+        v = fem_synth.box_mesh(4)[:E]
+        G, _ = oracle.geofacs(N, oracle.KIND_BP35, v)
+        q = fem_synth.field(3, E, (N + 1) ** 3)
+        G32, q32 = G.astype(np.float32), q.astype(np.float32)
+        ref = oracle.bp35(N, G32.astype(np.float64), 1.0, q32.astype(np.float64))
+        b = fem.fem_basis_setup(N)
+        got = fem.fem_bp35_apply_f32(b, _dev(G32), 1.0, _dev(q32)).cpu().numpy().astype(np.float64)
+        assert _rel(got, ref) < 2e-6 * (N + 1)
+    assert fem.fem_wait_timeouts() == 0
 
 
 def test_dot_deterministic_and_exact():
