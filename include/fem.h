@@ -257,7 +257,9 @@ typedef struct fem_pcg fem_pcg; /* opaque */
 typedef struct {
     double tol;       /* stop when ||rhs - A x||_2 <= tol ||rhs||_2 (default 1e-10) */
     int maxit;        /* iteration limit (default 100000)                          */
-    double inner_tol; /* mixed: relative tolerance of each FP32 solve (1e-4)       */
+    double inner_tol; /* mixed: relative tolerance of each FP32 solve (1e-4); an
+                       * FP32 solve also stops once its residual is below
+                       * tol/2 * ||rhs|| (the outer target is then in reach) */
     int inner_maxit;  /* mixed: iteration limit of each FP32 solve (100000)        */
     int check_every;  /* host convergence check period (8 FP64, 16 FP32)           */
 } fem_pcg_opts;

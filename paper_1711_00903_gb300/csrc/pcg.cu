@@ -317,7 +317,7 @@ enum RedMode { R_SUM = 0, R_PQ, R_RZ, R_INIT, R_OUTER, R_TRUE };
 // the scalar logic of the recurrence.
 __global__ void __launch_bounds__(kRedThreads)
 reduce_kernel(int mode, int64_t nparts, const double *__restrict__ part, double *__restrict__ scal,
-              double *__restrict__ out, double tol2_rel) {
+              double *__restrict__ out, double tol2_rel, double floor2_rel = 0.0) {
     __shared__ double sh[32];
     const int stride = (mode == R_OUTER) ? 3 : (mode == R_RZ || mode == R_INIT || mode == R_TRUE) ? 2 : 1;
     double acc[3] = {0.0, 0.0, 0.0};
@@ -363,7 +363,11 @@ reduce_kernel(int mode, int64_t nparts, const double *__restrict__ part, double 
         scal[S_BETA] = 0.0;
         scal[S_ITER] = 0.0;
         scal[S_BREAK] = 0.0;
-        scal[S_TOL2] = tol2_rel * (mode == R_INIT ? scal[S_BB] : tot[1]);
+        // R_OUTER: the inner solve reduces the defect by inner_tol, but need
+        // not go below the floor floor2_rel * b.b (a fraction of the outer
+        // tolerance): the last defect-correction step then stops as soon as
+        // the outer target is in reach instead of over-solving
+        scal[S_TOL2] = (mode == R_INIT) ? tol2_rel * scal[S_BB] : fmax(tol2_rel * tot[1], floor2_rel * scal[S_BB]);
         scal[S_DONE] = (tot[1] <= scal[S_TOL2]) ? 1.0 : 0.0;
         if (mode == R_OUTER) scal[S_RR_OUTER] = tot[2];
     }
@@ -448,6 +452,7 @@ struct fem_pcg {
     int g_every;                   // chunk length the iteration graphs were captured with
     const double *g_b;             // right-hand side and solution the graphs were captured with
     double *g_x;
+    double g_tol, g_itol;          // and the tolerances
     bool use_graphs;               // not on the legacy default stream, which cannot be captured
 };
 
@@ -522,7 +527,8 @@ cudaError_t outer_body(fem_pcg *s) {
     cudaError_t e = op_apply64(s, s->x, s->q, s->st);
     if (e != cudaSuccess) return e;
     outer_kernel<<<kVecBlocks, kVecThreads, 0, s->st>>>(s->len, s->b, s->q, s->r32, s->z32, s->d32, s->dinv32, s->part);
-    reduce_kernel<<<1, kRedThreads, 0, s->st>>>(R_OUTER, kVecBlocks, s->part, s->scal, nullptr, s->itol * s->itol);
+    reduce_kernel<<<1, kRedThreads, 0, s->st>>>(R_OUTER, kVecBlocks, s->part, s->scal, nullptr, s->itol * s->itol,
+                                                0.25 * s->tol * s->tol);
     e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->hscal, s->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s->st);
@@ -680,13 +686,17 @@ cudaError_t pcg_begin(fem_pcg *s, const double *b, double *x, const fem_pcg_opts
     s->itol = (o && o->inner_tol > 0) ? o->inner_tol : 1e-4;
     s->imaxit = (o && o->inner_maxit > 0) ? o->inner_maxit : 100000;
     s->every = (o && o->check_every > 0) ? o->check_every : (s->mode == FEM_PCG_FP64 ? 8 : 16);
-    if (s->g_b != b || s->g_x != x) {  // the captured graphs name the old vectors
+    // the captured graphs name the vectors and the tolerances they were
+    // captured with
+    if (s->g_b != b || s->g_x != x || s->g_tol != s->tol || s->g_itol != s->itol) {
         cudaGraphExec_t gs[] = {s->g_iter64, s->g_iter32, s->g_outer};
         for (cudaGraphExec_t g : gs)
             if (g) cudaGraphExecDestroy(g);
         s->g_iter64 = s->g_iter32 = s->g_outer = nullptr;
         s->g_b = b;
         s->g_x = x;
+        s->g_tol = s->tol;
+        s->g_itol = s->itol;
     }
     s->b = b;
     s->x = x;
