@@ -43,9 +43,9 @@ KERNELS = ["geofacs_bp35", "geofacs_bp30_bp1", "bp1", "bp35", "bp30"]
 # element at N = 7, with the sha256 of the kernel source it was taken from;
 # a kernel whose source changed since reports traffic null.
 NCU_TRAFFIC = {
-    # profiles/fp64_operators_N7_E4096.md: 194.8 MB over 4096 elements
-    "bp30": {"N": 7, "bytes_per_elem": 47570, "sha": "c33d1b1cdc630f0e",
-             "files": ["bp30.cu", "bp30_body.cuh", "eo.cuh"]},
+    # profiles/fp64_operators_N7_E4096.md: (184.07 + 10.55) MB over 4096 elements
+    "bp30": {"N": 7, "bytes_per_elem": 47516, "sha": "4767b770f5592311",
+             "files": ["bp30.cu", "bp30_body.cuh", "eo.cuh", "kernels_common.cuh"]},
 }
 
 
@@ -100,7 +100,9 @@ def alg_counts(N: int):
     i_dd, f_dd = eo_cost(n, n, -1)     # GLL derivative line
     i_gg, f_gg = eo_cost(m, m, -1)     # Gauss derivative line
     lam_i, lam_f = 3, 3                # lambda * wJ * q and its accumulation
+    fma_pts = 2 * (m * n3 + m * m * n * n + m3 * n) + 6 * m ** 4  # direct contractions of the point layout
     inst = {
+        "bp30_points": fma_pts + m3 * (9 + lam_i + 2),
         "bp1": (nn + m * n + mm) * (i_mn + i_nm) + m3,
         "bp35": 6 * nn * i_dd + n3 * (9 + lam_i + 2),
         "bp30": (nn + m * n + mm) * (i_mn + i_nm) + 6 * mm * i_gg + m3 * (9 + lam_i + 2),
@@ -108,6 +110,7 @@ def alg_counts(N: int):
         "geofacs_bp35": 52 * n3 + 27 * nn,
     }
     std = {
+        "bp30_points": 2 * interp + 12 * m ** 4 + 18 * m3,
         "bp1": 2 * interp + m3,
         "bp35": 12 * n ** 4 + 18 * n3,
         "bp30": 2 * interp + 12 * m ** 4 + 18 * m3,
@@ -115,6 +118,7 @@ def alg_counts(N: int):
         "geofacs_bp35": 79 * n3 + 54 * nn,
     }
     byts = {
+        "bp30_points": 8 * (2 * n3 + 7 * m3),
         "geofacs_bp30_bp1": 8 * (24 + 8 * m3),
         "geofacs_bp35": 8 * (24 + 7 * n3),
         "bp1": 8 * (2 * n3 + m3),
@@ -133,9 +137,16 @@ def smem_counts(N: int, word: int = 8):
            mass term, two in-place transposes, final sum);
     BP3.0  2n^3 + 3mn^2 + 4m^2n + 16m^3 words (BP1.0's interpolation and
            projection phases plus the Gauss-point derivative, chain-rule and
-           transpose phases)."""
+           transpose phases);
+    BP3.0, point layout: two words per multiply-add (operand and operator
+           entry) plus every phase output."""
     n, m = N + 1, N + 2
+    # point layout: every multiply-add reads an operand and an operator entry
+    # from shared memory; every phase output is stored once
+    fma_pts = 2 * (m * n ** 3 + m * m * n * n + m ** 3 * n) + 6 * m ** 4
+    outs_pts = n ** 3 + 2 * (m * n * n + m * m * n) + 5 * m ** 3 + n ** 3
     return {
+        "bp30_points": word * (2 * fma_pts + outs_pts + m ** 3),
         "bp1": word * (2 * n ** 3 + 3 * m * n * n + 4 * m * m * n),
         "bp35": word * 17 * n ** 3,
         "bp30": word * (2 * n ** 3 + 3 * m * n * n + 4 * m * m * n + 16 * m ** 3),
@@ -577,9 +588,11 @@ def run_sweep(fem, torch, device, verts, args, sm_mhz):
         std, inst, byts = alg_counts(N)
         smem = smem_counts(N)
         row = {"N": N, "dofs": E * n ** 3}
-        for name, kind in (("bp1", 1), ("bp35", 2), ("bp30", 3), ("bp35_f32", 2), ("bp30_f32", 3)):
+        for name, kind in (("bp1", 1), ("bp35", 2), ("bp30", 3), ("bp30_points", 3), ("bp35_f32", 2),
+                           ("bp30_f32", 3)):
             f32 = name.endswith("_f32")
             base = name[:-4] if f32 else name
+            ratio_base = "bp30" if base == "bp30_points" else base
             geo = torch.empty(fem.geo_shape(b, kind, E), dtype=torch.float64, device=device)
             fem.fem_mesh_geofacs(b, kind, verts, geo=geo, stream=stream)
             if f32:
@@ -588,6 +601,9 @@ def run_sweep(fem, torch, device, verts, args, sm_mhz):
                 fn = fem.fem_bp35_apply_f32 if base == "bp35" else fem.fem_bp30_apply_f32
                 ms = timed(lambda: fn(b, geo, lam, qx, out=o, stream=stream), reps)
                 del qx, o
+            elif name == "bp30_points":
+                ms = timed(lambda: fem.fem_bp30_apply_layout(b, geo, lam, q, fem.FEM_LAYOUT_POINTS, out=out,
+                                                             stream=stream), reps)
             elif name == "bp1":
                 ms = timed(lambda: fem.fem_bp1_apply(b, geo, q, out=out, stream=stream), reps)
             elif name == "bp35":
@@ -604,7 +620,7 @@ def run_sweep(fem, torch, device, verts, args, sm_mhz):
             copy_ms = timed(lambda: dst.copy_(half), 10)
             del half, dst
             # read:write ratio of the operator (planes read per plane written)
-            k = round((byts[base] - 8 * n ** 3) / (8 * n ** 3))
+            k = round((byts[ratio_base] - 8 * n ** 3) / (8 * n ** 3))
             src = torch.empty((k, E * n ** 3), dtype=torch.float32 if f32 else torch.float64, device=device)
             src.fill_(1.0)
             red = torch.empty(E * n ** 3, dtype=src.dtype, device=device)
@@ -629,8 +645,9 @@ def run_sweep(fem, torch, device, verts, args, sm_mhz):
         b.free()
     del q_all
     torch.cuda.empty_cache()
-    return {"workload": f"BP1.0/BP3.5/BP3.0 FP64 (and BP3.5/BP3.0 FP32, the mixed solver's inner operators) "
-                        f"sweep, E={E} jittered hexes, lambda=1, mean of {reps} launches per point",
+    return {"workload": f"BP1.0/BP3.5/BP3.0 FP64 (BP3.0 also in the point-per-thread layout; BP3.5/BP3.0 FP32, "
+                        f"the mixed solver's inner operators) sweep, E={E} jittered hexes, lambda=1, mean of "
+                        f"{reps} launches per point",
             "copy_roofline": "device-to-device copy of T/2 bytes moving T = the operator's algorithmic "
                              "bytes, recalibrated at every N (Section 5 of the paper)",
             "rows": rows}

@@ -174,6 +174,20 @@ int fem_wait_timeouts(unsigned long long *count, int reset);
  * Errors: FEM_EINVAL, FEM_ECUDA. */
 int fem_stream_sum(int planes, int64_t n, const void *src, void *dst, int word, void *stream);
 
+/* Thread layouts of the operator kernels (Section 6 compares both):
+ * FEM_LAYOUT_LINES   two-dimensional: one thread per line of an element,
+ *                    even-odd folded 1D operators (the default everywhere);
+ * FEM_LAYOUT_POINTS  three-dimensional: one thread per quadrature point,
+ *                    one element per block, operators in shared memory. */
+#define FEM_LAYOUT_LINES 0
+#define FEM_LAYOUT_POINTS 1
+
+/* fem_bp30_apply with a chosen thread layout (same arguments, layouts and
+ * errors; FEM_EINVAL for an unknown layout).  Both layouts compute the same
+ * operator and agree to rounding. */
+int fem_bp30_apply_layout(const fem_basis *b, int64_t E, const double *G, double lambda,
+                          const double *q, double *Aq, int layout, void *stream);
+
 /* BP3.0 matvec in FP32 (Algorithm 5 with float data and FP32 arithmetic;
  * the inner operator of the mixed-precision BP3.0 solver).  Same layouts as
  * fem_bp30_apply: G device E*7*m^3 floats, q and Aq device E*n^3 floats,
@@ -297,7 +311,8 @@ void fem_pcg_destroy(fem_pcg *s);
  * with its own operator (BP3.5 or BP3.0, FP64), factors, lambda, input and
  * output, applied in ONE persistent launch (Section 4: every element is
  * independent, so meshes are just more elements).  Each element's result is
- * bit-identical to the per-mesh fem_bp35_apply / fem_bp30_apply call.
+ * bit-identical to the per-mesh fem_bp35_apply / fem_bp30_apply_layout call
+ * with the batch's layout.
  * --------------------------------------------------------------------- */
 
 typedef struct {
@@ -314,6 +329,8 @@ typedef struct {
     int threads; /* threads per persistent block: 256 or 512              */
     int group;   /* tasks taken per fetch of the shared counter, 1..64    */
     int order;   /* 0: tasks by decreasing cost per element; 1: as given  */
+    int layout;  /* BP3.0 tasks up to N = 8: FEM_LAYOUT_LINES (default) or
+                  * FEM_LAYOUT_POINTS (one thread per Gauss point)         */
     float ms;    /* measured time of one launch (fem_batch_tune), or 0    */
 } fem_batch_config;
 
@@ -331,7 +348,8 @@ int fem_batch_create(const fem_batch_item *items, int count, fem_batch **out);
 int fem_batch_apply(fem_batch *b, void *stream);
 
 /* Autotuner: times every configuration (threads 256/512 x group 1/2/4/8 x
- * both task orders, reps launches each after a warm-up) on the batch itself,
+ * both task orders x both BP3.0 layouts when the batch has BP3.0 meshes of
+ * degree <= 8; reps launches each after a warm-up) on the batch itself,
  * keeps the fastest as the batch's configuration, and writes up to
  * max_results timings to results (may be NULL) and their count to
  * *nresults (may be NULL).  Synchronous.  Errors: FEM_EINVAL, FEM_ECUDA. */

@@ -20,7 +20,8 @@ __all__ = [
     "FemError", "lib", "Basis", "fem_version", "fem_basis_setup", "fem_basis_free",
     "fem_basis_tables", "fem_basis_host_tables", "fem_mesh_geofacs", "fem_bp1_apply",
     "fem_bp35_apply", "fem_bp30_apply", "FEM_GEO_BP1", "FEM_GEO_BP35", "FEM_GEO_BP30",
-    "geo_shape", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot", "fem_dot_scratch_size", "Pcg",
+    "geo_shape", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_bp30_apply_layout",
+    "FEM_LAYOUT_LINES", "FEM_LAYOUT_POINTS", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot", "fem_dot_scratch_size", "Pcg",
     "fem_pcg_create", "fem_pcg_solve", "fem_pcg_destroy", "FEM_PCG_FP64", "FEM_PCG_MIXED",
     "Batch", "fem_batch_create", "FEM_OP_BP35", "FEM_OP_BP30", "Server",
     "FEM_REQ_QUEUED", "FEM_REQ_RUNNING", "FEM_REQ_DONE", "FEM_REQ_FAILED",
@@ -31,6 +32,7 @@ FEM_EBREAKDOWN, FEM_ENOCONV, FEM_ETOOBIG = -5, -6, -7
 FEM_PCG_FP64, FEM_PCG_MIXED = 0, 1
 FEM_GEO_BP1, FEM_GEO_BP35, FEM_GEO_BP30 = 1, 2, 3
 FEM_OP_BP35, FEM_OP_BP30 = 2, 3
+FEM_LAYOUT_LINES, FEM_LAYOUT_POINTS = 0, 1
 FEM_REQ_QUEUED, FEM_REQ_RUNNING, FEM_REQ_DONE, FEM_REQ_FAILED = 0, 1, 2, 3
 MAX_N = 15
 
@@ -57,7 +59,8 @@ class BatchItem(C.Structure):
 
 class BatchConfig(C.Structure):
     """fem_batch_config (include/fem.h)."""
-    _fields_ = [("threads", C.c_int), ("group", C.c_int), ("order", C.c_int), ("ms", C.c_float)]
+    _fields_ = [("threads", C.c_int), ("group", C.c_int), ("order", C.c_int), ("layout", C.c_int),
+                ("ms", C.c_float)]
 
 
 class ServeOpts(C.Structure):
@@ -115,6 +118,7 @@ def lib():
             L.fem_stream_sum.argtypes = [i32, i64, dp, dp, i32, vp]
             L.fem_mesh_geofacs_set.argtypes = [vp, i64, dp, dp, dp, dp, vp]
             L.fem_wait_timeouts.argtypes = [C.POINTER(C.c_ulonglong), i32]
+            L.fem_bp30_apply_layout.argtypes = [vp, i64, dp, dbl, dp, dp, i32, vp]
             L.fem_bp35_jacobi.argtypes = [vp, i64, dp, dbl, dp, vp]
             L.fem_dot_scratch_size.restype = i64
             L.fem_dot.argtypes = [i64, dp, dp, dp, dp, vp]
@@ -152,7 +156,7 @@ def lib():
             L.fem_pcg_destroy.restype = None
             for f in ("fem_basis_setup", "fem_basis_tables", "fem_basis_host_tables",
                       "fem_mesh_geofacs", "fem_bp1_apply", "fem_bp35_apply", "fem_bp30_apply",
-                      "fem_basis_degree", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot",
+                      "fem_basis_degree", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_bp30_apply_layout", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot",
                       "fem_pcg_create", "fem_pcg_solve"):
                 getattr(L, f).restype = i32
             _lib = L
@@ -331,6 +335,16 @@ def _dev32(t, name, numel=None):
     if numel is not None and t.numel() != numel:
         raise ValueError(f"{name} has {t.numel()} entries, expected {numel}")
     return t.data_ptr()
+
+
+def fem_bp30_apply_layout(b: Basis, G, lam: float, q, layout: int, out=None, stream=None):
+    """BP3.0 matvec with a chosen thread layout (FEM_LAYOUT_LINES or
+    FEM_LAYOUT_POINTS)."""
+    E, out = _apply_out(q, out, b)
+    _dev(G, "G", E * 7 * b.m ** 3)
+    _check(lib().fem_bp30_apply_layout(b.handle, E, G.data_ptr(), float(lam), q.data_ptr(), out.data_ptr(),
+                                       int(layout), _stream(stream, q.device)), "fem_bp30_apply_layout")
+    return out
 
 
 def fem_bp35_apply_f32(b: Basis, G, lam: float, q, out=None, stream=None):
@@ -522,23 +536,23 @@ class Batch:
 
     def tune(self, reps=5, stream=None):
         """Times every launch configuration; keeps the fastest.  Returns the
-        list of (threads, group, order, ms)."""
+        list of (threads, group, order, layout, ms)."""
         dev = self.items[0][4].device if self.items else None
         res = (BatchConfig * 64)()
         cnt = C.c_int(0)
         _check(lib().fem_batch_tune(self.handle, _stream(stream, dev), int(reps), res, 64, C.byref(cnt)),
                "fem_batch_tune")
-        return [(r.threads, r.group, r.order, r.ms) for r in res[:cnt.value]]
+        return [(r.threads, r.group, r.order, r.layout, r.ms) for r in res[:cnt.value]]
 
     @property
     def config(self):
         c = BatchConfig()
         _check(lib().fem_batch_get_config(self.handle, C.byref(c)), "fem_batch_get_config")
-        return {"threads": c.threads, "group": c.group, "order": c.order, "ms": c.ms}
+        return {"threads": c.threads, "group": c.group, "order": c.order, "layout": c.layout, "ms": c.ms}
 
     @config.setter
     def config(self, cfg):
-        c = BatchConfig(int(cfg["threads"]), int(cfg["group"]), int(cfg["order"]), 0.0)
+        c = BatchConfig(int(cfg["threads"]), int(cfg["group"]), int(cfg["order"]), int(cfg.get("layout", 0)), 0.0)
         _check(lib().fem_batch_set_config(self.handle, C.byref(c)), "fem_batch_set_config")
 
     def free(self):

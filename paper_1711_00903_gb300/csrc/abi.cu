@@ -110,6 +110,7 @@ int fem_basis_setup(int N, fem_basis **out) {
     if (e == cudaSuccess) e = fem::prepare_bp35(N, fem::fold_table());
     if (e == cudaSuccess) e = fem::prepare_bp30(N, fem::fold_table());
     if (e == cudaSuccess) e = fem::prepare_geofacs(N);
+    if (e == cudaSuccess) e = fem::prepare_bp30_point(N);
     if (e != cudaSuccess) {
         cudaFree(b->d_ops);
         delete b;
@@ -241,6 +242,16 @@ int fem_stream_sum(int planes, int64_t n, const void *src, void *dst, int word, 
     const int64_t sb = (int64_t)planes * n * word, db = n * word;
     if (d0 < s0 + sb && s0 < d0 + db) return FEM_EINVAL;  // overlapping buffers
     cudaError_t e = fem::launch_stream_sum(planes, n, src, dst, word, (cudaStream_t)stream);
+    return e == cudaSuccess ? FEM_OK : cuda_fail(e);
+}
+
+int fem_bp30_apply_layout(const fem_basis *b, int64_t E, const double *G, double lambda, const double *q,
+                          double *Aq, int layout, void *stream) {
+    if (layout != FEM_LAYOUT_LINES && layout != FEM_LAYOUT_POINTS) return FEM_EINVAL;
+    if (layout == FEM_LAYOUT_LINES) return fem_bp30_apply(b, E, G, lambda, q, Aq, stream);
+    const int c = check_apply(b, E, G, b ? 7 * cube(b->host.m) : 0, q, Aq);
+    if (c != FEM_OK || E == 0) return c;
+    cudaError_t e = fem::launch_bp30_point(b, E, G, lambda, q, Aq, (cudaStream_t)stream);
     return e == cudaSuccess ? FEM_OK : cuda_fail(e);
 }
 

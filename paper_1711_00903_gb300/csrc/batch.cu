@@ -11,25 +11,29 @@
 // default, so that the expensive high-degree work starts first and the tail
 // is made of cheap tasks.
 //
-// The launch shape (threads per block, tasks per counter fetch, task order)
-// is chosen by a small autotuner that times every candidate on the batch
-// itself; the chosen configuration can be replayed from a CUDA graph that
-// contains the counter reset and the kernel.
+// The launch shape (threads per block, tasks per counter fetch, task order,
+// and the thread layout of BP3.0 tasks up to N = 8: lines or one thread per
+// Gauss point, bp30_point.cuh) is chosen by a small autotuner that times
+// every candidate on the batch itself; the chosen configuration can be
+// replayed from a CUDA graph that contains the counter reset and the kernel.
 #include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
 
 #include "bp30_body.cuh"
+#include "bp30_point.cuh"
 #include "bp35_body.cuh"
 
 namespace fem {
 namespace {
 
 constexpr int kBatchMaxN = 10;
+constexpr int kBatchMaxPointN = 8;  // point layout: m^3 <= 1000 points, 4 m^3 doubles of shared memory
 constexpr int kBatchSmemBudget = 96 * 1024;
 
 struct BatchMesh {
+    const double *ops;  // basis table of the mesh's degree (point layout)
     const double *G;
     const double *q;
     double *out;
@@ -64,7 +68,9 @@ template <int THREADS, int N>
 constexpr int batch_smem_n() {
     constexpr int s35 = Bp35Layout<double, N, Epb35<THREADS, N>::v>::smem;
     constexpr int s30 = Bp30Layout<N, Epb30<THREADS, N>::v>::smem;
-    return s35 > s30 ? s35 : s30;
+    constexpr int sp = N <= kBatchMaxPointN ? Bp30Point<N>::smem : 0;
+    constexpr int s = s35 > s30 ? s35 : s30;
+    return s > sp ? s : sp;
 }
 
 template <int THREADS>
@@ -105,11 +111,19 @@ template <int THREADS, int K>
 __device__ __noinline__ void task30(unsigned char *smem, const BatchTask tk, const BatchMesh M) {
     bp30_block<K, Epb30<THREADS, K>::v>(reinterpret_cast<double *>(smem), tk.e0, tk.nel, M.G, M.lambda, M.q, M.out);
 }
+// the same task in the point layout: its elements one after the other
+template <int THREADS, int K>
+__device__ __noinline__ void task30_point(unsigned char *smem, const BatchTask tk, const BatchMesh M) {
+    for (int el = 0; el < tk.nel; el++) {
+        if (el > 0) __syncthreads();
+        bp30_point_block<K, THREADS>(reinterpret_cast<double *>(smem), M.ops, tk.e0 + el, M.G, M.lambda, M.q, M.out);
+    }
+}
 
 template <int THREADS>
 __global__ void __launch_bounds__(THREADS)
 batch_kernel(const BatchMesh *__restrict__ meshes, const BatchTask *__restrict__ tasks, int ntasks, int group,
-             int *__restrict__ counter) {
+             int layout, int *__restrict__ counter) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_t;
     for (;;) {
@@ -124,12 +138,15 @@ batch_kernel(const BatchMesh *__restrict__ meshes, const BatchTask *__restrict__
             const BatchTask tk = tasks[t];
             const BatchMesh M = meshes[tk.mesh];
             switch (M.op * 16 + M.N) {
-#define FEM_TASK(K)                  \
-    case FEM_OP_BP35 * 16 + K:       \
-        task35<THREADS, K>(smem, tk, M); \
-        break;                       \
-    case FEM_OP_BP30 * 16 + K:       \
-        task30<THREADS, K>(smem, tk, M); \
+#define FEM_TASK(K)                                           \
+    case FEM_OP_BP35 * 16 + K:                                \
+        task35<THREADS, K>(smem, tk, M);                      \
+        break;                                                \
+    case FEM_OP_BP30 * 16 + K:                                \
+        if (K <= kBatchMaxPointN && layout == FEM_LAYOUT_POINTS) \
+            task30_point<THREADS, (K <= kBatchMaxPointN ? K : 1)>(smem, tk, M); \
+        else                                                  \
+            task30<THREADS, K>(smem, tk, M);                  \
         break;
                 FEM_TASK(1) FEM_TASK(2) FEM_TASK(3) FEM_TASK(4) FEM_TASK(5)
                 FEM_TASK(6) FEM_TASK(7) FEM_TASK(8) FEM_TASK(9) FEM_TASK(10)
@@ -215,10 +232,10 @@ cudaError_t launch(fem_batch *b, const fem_batch_config &c, cudaStream_t s) {
     if (b->ntasks[v][o] == 0) return cudaSuccess;
     if (v == 0)
         batch_kernel<256><<<b->blocks[0], 256, batch_smem<256>(), s>>>(b->d_meshes, b->d_tasks[0][o], b->ntasks[0][o],
-                                                                       c.group, b->d_counter);
+                                                                       c.group, c.layout, b->d_counter);
     else
         batch_kernel<512><<<b->blocks[1], 512, batch_smem<512>(), s>>>(b->d_meshes, b->d_tasks[1][o], b->ntasks[1][o],
-                                                                       c.group, b->d_counter);
+                                                                       c.group, c.layout, b->d_counter);
     return cudaGetLastError();
 }
 
@@ -235,7 +252,7 @@ void release(fem_batch *b) {
 
 bool valid_config(const fem_batch_config *c) {
     return c && (c->threads == 256 || c->threads == 512) && c->group >= 1 && c->group <= 64 &&
-           (c->order == 0 || c->order == 1);
+           (c->order == 0 || c->order == 1) && (c->layout == FEM_LAYOUT_LINES || c->layout == FEM_LAYOUT_POINTS);
 }
 
 }  // namespace
@@ -255,6 +272,7 @@ int fem_batch_create(const fem_batch_item *items, int count, fem_batch **out) {
         if (it.E > 0 && (!it.geo || !it.q || !it.out)) return FEM_EINVAL;
         if (it.E > 0 && (it.out == it.q || it.out == it.geo)) return FEM_EINVAL;
         fem::BatchMesh m;
+        m.ops = it.basis->d_ops;
         m.G = it.geo;
         m.q = it.q;
         m.out = it.out;
@@ -271,6 +289,7 @@ int fem_batch_create(const fem_batch_item *items, int count, fem_batch **out) {
     b->cfg.threads = 256;
     b->cfg.group = 1;
     b->cfg.order = 0;
+    b->cfg.layout = FEM_LAYOUT_LINES;
     b->cfg.ms = 0.0f;
     cudaError_t e = cudaGetDevice(&b->device);
     if (e == cudaSuccess) e = fem::upload_fold_batch_tu(fem::fold_table());
@@ -327,6 +346,11 @@ int fem_batch_tune(fem_batch *b, void *stream, int reps, fem_batch_config *resul
     if (!b || reps < 1) return FEM_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     const int threads[2] = {256, 512}, groups[4] = {1, 2, 4, 8};
+    // the point layout is a candidate only when the batch has BP3.0 meshes it applies to
+    bool point_ok = false;
+    for (const fem::BatchMesh &m : b->host_meshes)
+        point_ok = point_ok || (m.op == FEM_OP_BP30 && m.N <= fem::kBatchMaxPointN && m.E > 0);
+    const int nlayouts = point_ok ? 2 : 1;
     cudaEvent_t e0, e1;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -334,6 +358,7 @@ int fem_batch_tune(fem_batch *b, void *stream, int reps, fem_batch_config *resul
     fem_batch_config best = b->cfg;
     best.ms = 1e30f;
     int k = 0;
+    for (int li = 0; li < nlayouts && e == cudaSuccess; li++)
     for (int ti = 0; ti < 2 && e == cudaSuccess; ti++)
         for (int gi = 0; gi < 4 && e == cudaSuccess; gi++)
             for (int order = 0; order < 2 && e == cudaSuccess; order++) {
@@ -341,6 +366,7 @@ int fem_batch_tune(fem_batch *b, void *stream, int reps, fem_batch_config *resul
                 c.threads = threads[ti];
                 c.group = groups[gi];
                 c.order = order;
+                c.layout = li;
                 e = fem::launch(b, c, s);  // warm-up
                 if (e == cudaSuccess) e = cudaEventRecord(e0, s);
                 for (int r = 0; r < reps && e == cudaSuccess; r++) e = fem::launch(b, c, s);
@@ -365,7 +391,7 @@ int fem_batch_graph_launch(fem_batch *b, void *stream) {
     if (!b) return FEM_EINVAL;
     cudaError_t e = cudaSuccess;
     const bool stale = !b->graph_exec || b->graph_cfg.threads != b->cfg.threads || b->graph_cfg.group != b->cfg.group ||
-                       b->graph_cfg.order != b->cfg.order;
+                       b->graph_cfg.order != b->cfg.order || b->graph_cfg.layout != b->cfg.layout;
     if (stale) {
         if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
         if (b->graph) cudaGraphDestroy(b->graph);

@@ -86,6 +86,8 @@ def test_argument_errors_need_no_gpu():
     assert L.fem_stream_sum(2, 64, a, C.c_void_p((1 << 20) + 512), 8, None) == fem.FEM_EINVAL
     assert L.fem_stream_sum(2, 0, a, b, 8, None) == 0  # nothing to do
     assert L.fem_mesh_geofacs_set(None, 1, p, p, None, None, None) == fem.FEM_EINVAL
+    assert L.fem_bp30_apply_layout(None, 1, p, 1.0, p, p, fem.FEM_LAYOUT_POINTS, None) == fem.FEM_EINVAL
+    assert L.fem_bp30_apply_layout(None, 1, p, 1.0, p, p, 7, None) == fem.FEM_EINVAL
 
 
 def test_binding_refuses_host_tensors():

@@ -80,9 +80,13 @@ def test_tuner_and_graph_replay_keep_the_bits(bases):
     items, refs = _build(specs, bases)
     batch = fem.Batch(items)
     results = batch.tune(reps=2)
-    assert len(results) == 16 and all(r[3] > 0 for r in results)
+    # the BP3.0 meshes of degree <= 8 make the point layout a candidate too
+    assert len(results) == 32 and all(r[4] > 0 for r in results)
+    assert {r[3] for r in results} == {fem.FEM_LAYOUT_LINES, fem.FEM_LAYOUT_POINTS}
     cfg = batch.config
-    assert cfg["ms"] == min(r[3] for r in results)
+    assert cfg["ms"] == min(r[4] for r in results)
+    if cfg["layout"] != fem.FEM_LAYOUT_LINES:  # compare with the lines layout below
+        batch.config = {"threads": cfg["threads"], "group": cfg["group"], "order": cfg["order"]}
     for _, _, _, _, _, out in items:
         out.fill_(float("nan"))
     batch.graph_launch()
@@ -100,6 +104,31 @@ def test_tuner_and_graph_replay_keep_the_bits(bases):
             torch.cuda.synchronize()
             for (op, b, geo, lam, q, out), (ref, v, _) in zip(items, refs):
                 assert torch.equal(out, ref)
+
+
+def test_point_layout_in_batch_matches_per_mesh_point_calls(bases):
+    """BP3.0 tasks in the point layout: bit for bit the per-mesh call in the
+    same layout, and within rounding of the lines layout and the oracle;
+    BP3.5 tasks and BP3.0 above N = 8 keep the lines layout."""
+    import torch
+    fem = _fem()
+    specs = [(fem.FEM_OP_BP30, N, 2, 1, 2, 500 + N) for N in (1, 3, 6, 8, 9)]
+    specs.append((fem.FEM_OP_BP35, 4, 2, 2, 1, 600))
+    items, refs = _build(specs, bases)
+    batch = fem.Batch(items)
+    batch.config = {"threads": 256, "group": 2, "order": 0, "layout": fem.FEM_LAYOUT_POINTS}
+    batch.apply()
+    torch.cuda.synchronize()
+    for (op, b, geo, lam, q, out), (ref, v, _), spec in zip(items, refs, specs):
+        if op == fem.FEM_OP_BP30 and b.N <= 8:
+            pt = fem.fem_bp30_apply_layout(b, geo, lam, q, fem.FEM_LAYOUT_POINTS)
+            assert torch.equal(out, pt), spec
+            G, _ = oracle.geofacs(b.N, oracle.KIND_BP30, v)
+            o = oracle.bp30(b.N, G, lam, q.cpu().numpy())
+            assert np.abs(out.cpu().numpy() - o).max() / np.abs(o).max() < 1e-12, spec
+            assert (out - ref).abs().max().item() / ref.abs().max().item() < 1e-12, spec
+        else:
+            assert torch.equal(out, ref), spec
 
 
 def test_batch_rejects_bad_items(bases):
