@@ -683,7 +683,9 @@ def run_pcg(fem, torch, device, verts_h, args):
            "error_reference": "u_I, the exact discrete solution (the oracle PCG agrees with the GPU "
                               "solvers to 1e-8 on the smaller meshes of tests/test_pcg_gpu.py)"}
     xs = {}
-    for name, mode, itol in (("fp64", fem.FEM_PCG_FP64, 0.0), ("mixed", fem.FEM_PCG_MIXED, 1e-3)):
+    modes = [m for m in (("fp64", fem.FEM_PCG_FP64, 0.0), ("mixed", fem.FEM_PCG_MIXED, 1e-3),
+                         ("mixed16", fem.FEM_PCG_MIXED16, 1e-3)) if m[0] in args.pcg_modes.split(",")]
+    for name, mode, itol in modes:
         s = fem.fem_pcg_create(basis, G, lam, mode)
         x, info, code = s.solve(b, tol=tol, inner_tol=itol)  # warm-up
         times = []
@@ -701,9 +703,15 @@ def run_pcg(fem, torch, device, verts_h, args):
                      "rel_err_vs_u_I": err}
         xs[name] = x.clone()
         s.free()
-    out["mixed"]["rel_diff_vs_fp64_solve"] = (torch.linalg.norm(xs["mixed"] - xs["fp64"]) /
-                                              torch.linalg.norm(xs["fp64"])).item()
-    out["mixed_speedup"] = out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    for name in ("mixed", "mixed16"):
+        if name in xs and "fp64" in xs:
+            out[name]["rel_diff_vs_fp64_solve"] = (torch.linalg.norm(xs[name] - xs["fp64"]) /
+                                                   torch.linalg.norm(xs["fp64"])).item()
+            out[name + "_speedup"] = out[name]["solves_per_s"] / out["fp64"]["solves_per_s"]
+    out["modes"] = {"fp64": "all-FP64 Jacobi-PCG",
+                    "mixed": "FP64 defect correction, FP32 inner PCG with FP32 factors",
+                    "mixed16": "FP64 defect correction, FP32 inner PCG with binary16 factors (power-of-two "
+                               "scaled) widened to FP32 in the kernel"}
     basis.free()
     return out
 
@@ -831,6 +839,8 @@ def main(argv=None):
     ap.add_argument("--no-sweep", action="store_true", help="skip the per-N operator sweep")
     ap.add_argument("--no-pcg", action="store_true", help="skip the Helmholtz solve measurement")
     ap.add_argument("--pcg-solves", type=int, default=3)
+    ap.add_argument("--pcg-modes", default="fp64,mixed,mixed16",
+                    help="solver modes of the Helmholtz measurement (comma list of fp64, mixed, mixed16)")
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-order batch measurement")
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the Poisson-arrival serving measurement (0 skips it)")

@@ -174,6 +174,18 @@ int fem_wait_timeouts(unsigned long long *count, int reset);
  * Errors: FEM_EINVAL, FEM_ECUDA. */
 int fem_stream_sum(int planes, int64_t n, const void *src, void *dst, int word, void *stream);
 
+/* BP3.5 and BP3.0 matvecs with half-precision factors: the inner operators
+ * of FEM_PCG_MIXED16.  G16: device, the factor layout of fem_bp35_apply /
+ * fem_bp30_apply with IEEE binary16 values (uint16_t bits), 16-byte
+ * aligned; ginv: device, one double, multiplied into the output (the
+ * inverse of the power of two the factors were scaled by; 1.0 for none);
+ * q, Aq: device floats.  FP32 arithmetic.  Asynchronous on stream,
+ * allocates nothing.  Errors: FEM_EINVAL, FEM_ECUDA. */
+int fem_bp35_apply_f16g(const fem_basis *b, int64_t E, const void *G16, const double *ginv, double lambda,
+                        const float *q, float *Aq, void *stream);
+int fem_bp30_apply_f16g(const fem_basis *b, int64_t E, const void *G16, const double *ginv, double lambda,
+                        const float *q, float *Aq, void *stream);
+
 /* Thread layouts of the operator kernels (Section 6 compares both):
  * FEM_LAYOUT_LINES   two-dimensional: one thread per line of an element,
  *                    even-odd folded 1D operators (the default everywhere);
@@ -254,8 +266,14 @@ int fem_dot_noalloc(int64_t n, const double *x, const double *y, double *result,
  *                  and the update of x in FP64; each correction A d = r
  *                  solved to inner_tol by an FP32 PCG (FP32 factors, FP32
  *                  matvec, FP64 dot products).
+ *   FEM_PCG_MIXED16  as FEM_PCG_MIXED, with the inner matvec reading the
+ *                  factors in IEEE binary16, scaled by a power of two (set
+ *                  on the device from the largest factor) and widened to
+ *                  FP32 in the kernel: half the factor bytes, same FP32
+ *                  arithmetic.  The FP64 outer loop still reaches tol.
  * A solver context owns its device workspace (about 5 vectors in FP64
- * mode; 7 FP32 factor planes and 6 FP32 + 1 FP64 vectors in mixed mode).
+ * mode; 7 FP32 (MIXED16: FP16) factor planes and 6 FP32 + 1 FP64 vectors in
+ * the mixed modes).
  * --------------------------------------------------------------------- */
 #define FEM_EBREAKDOWN (-5) /* p.Ap <= 0 or a non-finite value in the recurrence */
 #define FEM_ENOCONV (-6)    /* iteration limit reached; x holds the last iterate */
@@ -265,6 +283,7 @@ int fem_dot_noalloc(int64_t n, const double *x, const double *y, double *result,
 
 #define FEM_PCG_FP64 0
 #define FEM_PCG_MIXED 1
+#define FEM_PCG_MIXED16 2
 
 typedef struct fem_pcg fem_pcg; /* opaque */
 
@@ -394,7 +413,7 @@ typedef struct {
     const double *rhs;   /* host, E*Np; read when the request is admitted           */
     double *x;           /* host output, E*Np; written when the request finishes    */
     double lambda;       /* >= 0                                                    */
-    int mode;            /* FEM_PCG_FP64 or FEM_PCG_MIXED                           */
+    int mode;            /* FEM_PCG_FP64, FEM_PCG_MIXED or FEM_PCG_MIXED16          */
     double tol;          /* relative residual tolerance                             */
 } fem_serve_request;
 

@@ -22,14 +22,14 @@ __all__ = [
     "fem_bp35_apply", "fem_bp30_apply", "FEM_GEO_BP1", "FEM_GEO_BP35", "FEM_GEO_BP30",
     "geo_shape", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_bp30_apply_layout",
     "FEM_LAYOUT_LINES", "FEM_LAYOUT_POINTS", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot", "fem_dot_scratch_size", "Pcg",
-    "fem_pcg_create", "fem_pcg_solve", "fem_pcg_destroy", "FEM_PCG_FP64", "FEM_PCG_MIXED",
+    "fem_pcg_create", "fem_pcg_solve", "fem_pcg_destroy", "FEM_PCG_FP64", "FEM_PCG_MIXED", "FEM_PCG_MIXED16", "fem_bp35_apply_f16g", "fem_bp30_apply_f16g",
     "Batch", "fem_batch_create", "FEM_OP_BP35", "FEM_OP_BP30", "Server",
     "FEM_REQ_QUEUED", "FEM_REQ_RUNNING", "FEM_REQ_DONE", "FEM_REQ_FAILED",
 ]
 
 FEM_OK, FEM_EINVAL, FEM_ECUDA, FEM_ENOMEM, FEM_ENODEV = 0, -1, -2, -3, -4
 FEM_EBREAKDOWN, FEM_ENOCONV, FEM_ETOOBIG = -5, -6, -7
-FEM_PCG_FP64, FEM_PCG_MIXED = 0, 1
+FEM_PCG_FP64, FEM_PCG_MIXED, FEM_PCG_MIXED16 = 0, 1, 2
 FEM_GEO_BP1, FEM_GEO_BP35, FEM_GEO_BP30 = 1, 2, 3
 FEM_OP_BP35, FEM_OP_BP30 = 2, 3
 FEM_LAYOUT_LINES, FEM_LAYOUT_POINTS = 0, 1
@@ -119,6 +119,8 @@ def lib():
             L.fem_mesh_geofacs_set.argtypes = [vp, i64, dp, dp, dp, dp, vp]
             L.fem_wait_timeouts.argtypes = [C.POINTER(C.c_ulonglong), i32]
             L.fem_bp30_apply_layout.argtypes = [vp, i64, dp, dbl, dp, dp, i32, vp]
+            L.fem_bp35_apply_f16g.argtypes = [vp, i64, dp, dp, dbl, dp, dp, vp]
+            L.fem_bp30_apply_f16g.argtypes = [vp, i64, dp, dp, dbl, dp, dp, vp]
             L.fem_bp35_jacobi.argtypes = [vp, i64, dp, dbl, dp, vp]
             L.fem_dot_scratch_size.restype = i64
             L.fem_dot.argtypes = [i64, dp, dp, dp, dp, vp]
@@ -156,7 +158,8 @@ def lib():
             L.fem_pcg_destroy.restype = None
             for f in ("fem_basis_setup", "fem_basis_tables", "fem_basis_host_tables",
                       "fem_mesh_geofacs", "fem_bp1_apply", "fem_bp35_apply", "fem_bp30_apply",
-                      "fem_basis_degree", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_bp30_apply_layout", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot",
+                      "fem_basis_degree", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_bp30_apply_layout",
+                      "fem_bp35_apply_f16g", "fem_bp30_apply_f16g", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot",
                       "fem_pcg_create", "fem_pcg_solve"):
                 getattr(L, f).restype = i32
             _lib = L
@@ -335,6 +338,34 @@ def _dev32(t, name, numel=None):
     if numel is not None and t.numel() != numel:
         raise ValueError(f"{name} has {t.numel()} entries, expected {numel}")
     return t.data_ptr()
+
+
+def _apply_f16g(name, b: Basis, G16, ginv, lam, q, out, stream, gpts):
+    import torch
+    E = q.shape[0]
+    _dev32(q, "q", E * b.n ** 3)
+    if not isinstance(G16, torch.Tensor) or not G16.is_cuda or G16.dtype != torch.float16 or \
+            not G16.is_contiguous() or G16.numel() != E * 7 * gpts:
+        raise TypeError("G16 must be a contiguous float16 CUDA tensor of E*7*points values")
+    if not isinstance(ginv, torch.Tensor) or not ginv.is_cuda or ginv.dtype != torch.float64 or ginv.numel() != 1:
+        raise TypeError("ginv must be a one-element float64 CUDA tensor")
+    if out is None:
+        out = torch.empty_like(q)
+    _dev32(out, "out", E * b.n ** 3)
+    _check(getattr(lib(), name)(b.handle, E, G16.data_ptr(), ginv.data_ptr(), float(lam), q.data_ptr(),
+                                out.data_ptr(), _stream(stream, q.device)), name)
+    return out
+
+
+def fem_bp35_apply_f16g(b: Basis, G16, ginv, lam: float, q, out=None, stream=None):
+    """BP3.5 matvec with binary16 factors (float16 tensor) and FP32 data;
+    the output is multiplied by ginv (one-element float64 device tensor)."""
+    return _apply_f16g("fem_bp35_apply_f16g", b, G16, ginv, lam, q, out, stream, b.n ** 3)
+
+
+def fem_bp30_apply_f16g(b: Basis, G16, ginv, lam: float, q, out=None, stream=None):
+    """BP3.0 matvec with binary16 factors and FP32 data (see fem_bp35_apply_f16g)."""
+    return _apply_f16g("fem_bp30_apply_f16g", b, G16, ginv, lam, q, out, stream, b.m ** 3)
 
 
 def fem_bp30_apply_layout(b: Basis, G, lam: float, q, layout: int, out=None, stream=None):

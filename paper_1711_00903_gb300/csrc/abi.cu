@@ -111,6 +111,8 @@ int fem_basis_setup(int N, fem_basis **out) {
     if (e == cudaSuccess) e = fem::prepare_bp30(N, fem::fold_table());
     if (e == cudaSuccess) e = fem::prepare_geofacs(N);
     if (e == cudaSuccess) e = fem::prepare_bp30_point(N);
+    if (e == cudaSuccess) e = fem::prepare_bp35_f16(N, fem::fold_table());
+    if (e == cudaSuccess) e = fem::prepare_bp30_f16(N, fem::fold_table());
     if (e != cudaSuccess) {
         cudaFree(b->d_ops);
         delete b;
@@ -230,7 +232,10 @@ int fem_bp35_apply_f32(const fem_basis *b, int64_t E, const float *G, double lam
 
 int fem_wait_timeouts(unsigned long long *count, int reset) {
     if (!count) return FEM_EINVAL;
-    cudaError_t e = fem::wait_timeouts_bp35(count, reset != 0);
+    unsigned long long a = 0, b = 0;
+    cudaError_t e = fem::wait_timeouts_bp35(&a, reset != 0);
+    if (e == cudaSuccess) e = fem::wait_timeouts_bp35_f16(&b, reset != 0);
+    *count = a + b;
     return e == cudaSuccess ? FEM_OK : cuda_fail(e);
 }
 
@@ -242,6 +247,26 @@ int fem_stream_sum(int planes, int64_t n, const void *src, void *dst, int word, 
     const int64_t sb = (int64_t)planes * n * word, db = n * word;
     if (d0 < s0 + sb && s0 < d0 + db) return FEM_EINVAL;  // overlapping buffers
     cudaError_t e = fem::launch_stream_sum(planes, n, src, dst, word, (cudaStream_t)stream);
+    return e == cudaSuccess ? FEM_OK : cuda_fail(e);
+}
+
+int fem_bp35_apply_f16g(const fem_basis *b, int64_t E, const void *G16, const double *ginv, double lambda,
+                        const float *q, float *Aq, void *stream) {
+    if (!b || E < 0) return FEM_EINVAL;
+    if (E == 0) return FEM_OK;
+    if (!G16 || !ginv || !q || !Aq || !aligned16(G16) || !aligned16(q) || !aligned16(Aq)) return FEM_EINVAL;
+    if ((const void *)Aq == (const void *)q || (E + 1) > (int64_t)0x7fffffff) return FEM_EINVAL;
+    cudaError_t e = fem::launch_bp35_f16g(b, E, (const __half *)G16, ginv, lambda, q, Aq, (cudaStream_t)stream);
+    return e == cudaSuccess ? FEM_OK : cuda_fail(e);
+}
+
+int fem_bp30_apply_f16g(const fem_basis *b, int64_t E, const void *G16, const double *ginv, double lambda,
+                        const float *q, float *Aq, void *stream) {
+    if (!b || E < 0) return FEM_EINVAL;
+    if (E == 0) return FEM_OK;
+    if (!G16 || !ginv || !q || !Aq || !aligned16(G16) || !aligned16(q) || !aligned16(Aq)) return FEM_EINVAL;
+    if ((const void *)Aq == (const void *)q || (E + 1) > (int64_t)0x7fffffff) return FEM_EINVAL;
+    cudaError_t e = fem::launch_bp30_f16g(b, E, (const __half *)G16, ginv, lambda, q, Aq, (cudaStream_t)stream);
     return e == cudaSuccess ? FEM_OK : cuda_fail(e);
 }
 

@@ -24,18 +24,6 @@
 namespace fem {
 namespace {
 
-// Minimum resident blocks per SM that the register allocation must allow
-// (0: the compiler's own heuristic); see bp35.cu.  Chosen per precision and
-// degree from the operator sweep on GB300.
-template <typename T, int N>
-constexpr int bp30_min_blocks() {
-    if (sizeof(T) == 8) return (N >= 9 && N <= 14) ? 2 : 0;
-    if (N >= 9 && N <= 12) return 4;
-    if (N == 13) return 3;
-    if (N == 15) return 2;
-    return 0;
-}
-
 template <typename T, int N, bool PCG>
 __device__ __forceinline__ void bp30_entry(int64_t E, const T *__restrict__ G, double lambda, const T *__restrict__ q,
                                            T *__restrict__ Aq, const T *__restrict__ z, T *__restrict__ p,

@@ -3,6 +3,8 @@
 // See bp30.cu for the algorithm and the GB300 design.
 #pragma once
 
+#include <type_traits>
+
 #include "eo.cuh"
 
 namespace fem {
@@ -40,12 +42,15 @@ struct Bp30Cfg : Bp30Layout<N, pick_epb(N + 2, 3 * Box<N + 2, N + 2, N + 2>::siz
 // bytes).  PCG = true: the input field is p <- z + beta p (stored back to p;
 // beta read from *beta, p not read when beta is 0), and thread 0 writes the
 // block's p . Ap to *part_out.
-template <int N, int EPB_, typename T = double, bool PCG = false>
-__device__ __forceinline__ void bp30_block(T *smem, int64_t e0, int nel, const T *__restrict__ G, double lambda,
+// TG: type of the factors (T, or FP16 scaled by a power of two that the
+// value at ginv undoes on the output).
+template <int N, int EPB_, typename T = double, bool PCG = false, typename TG = T>
+__device__ __forceinline__ void bp30_block(T *smem, int64_t e0, int nel, const TG *__restrict__ G, double lambda,
                                            const T *__restrict__ q, T *__restrict__ Aq,
                                            const T *__restrict__ z = nullptr, T *__restrict__ p = nullptr,
                                            const double *__restrict__ beta = nullptr,
-                                           double *__restrict__ part_out = nullptr) {
+                                           double *__restrict__ part_out = nullptr,
+                                           const double *__restrict__ ginv = nullptr) {
     using C = Bp30Layout<N, EPB_, T>;
     using B0 = typename C::B0;
     using B1 = typename C::B1;
@@ -55,7 +60,7 @@ __device__ __forceinline__ void bp30_block(T *smem, int64_t e0, int nel, const T
     constexpr int S = C::S, per = C::per;
     // per element: buffer A = smem + el*per, B = A + S, C = A + 2S
     if (C::PREFETCH && threadIdx.x == 0)
-        prefetch_l2(G + e0 * 7 * MP, (long long)nel * 7 * MP * (long long)sizeof(T));
+        prefetch_l2(G + e0 * 7 * MP, (long long)nel * 7 * MP * (long long)sizeof(TG));
     if (PCG) {
         const T bt = (T)(*beta);
         for (int t = threadIdx.x; t < nel * NP; t += blockDim.x) {
@@ -148,14 +153,14 @@ __device__ __forceinline__ void bp30_block(T *smem, int64_t e0, int nel, const T
 #pragma unroll
         for (int l = 0; l < m; l++) x[l] = QG[B3::at(ca, cb, l)];
         eo_apply<m, m, -1, C::oDt>(x, ut);
-        const T *Ge = G + (e0 + cel) * 7 * MP + cr;
+        const TG *Ge = G + (e0 + cel) * 7 * MP + cr;
 #pragma unroll
         for (int c = 0; c < m; c++) {
             const int s = B3::at(ca, cb, c);
             const T ur = UR[s], us = US[s];
             T g[7];
 #pragma unroll
-            for (int h = 0; h < 7; h++) g[h] = __ldg(Ge + h * MP + c * mm);
+            for (int h = 0; h < 7; h++) g[h] = factor_ldg<T>(Ge + h * MP + c * mm);
             UR[s] = g[0] * ur + g[1] * us + g[2] * ut[c];
             US[s] = g[1] * ur + g[3] * us + g[4] * ut[c];
             Rt[c] = g[2] * ur + g[4] * us + g[5] * ut[c];
@@ -218,6 +223,7 @@ __device__ __forceinline__ void bp30_block(T *smem, int64_t e0, int nel, const T
 
     // 9. r-projection (j, k): X4 (B) -> Aq
     T dot = T(0);  // p . Ap of the thread's lines (PCG), in the data's precision
+    const T gscale = std::is_same<TG, T>::value ? T(1) : factor_unscale<T>(ginv);
     for_tasks<n * n, EPB>(nel, [&](int el, int r) {
         const T *X4 = smem + el * per + S;
         const int j = r % n, k = r / n;
@@ -225,6 +231,10 @@ __device__ __forceinline__ void bp30_block(T *smem, int64_t e0, int nel, const T
 #pragma unroll
         for (int l = 0; l < m; l++) x[l] = X4[B1::at(l, j, k)];
         eo_apply<n, m, 1, C::oIT>(x, y);
+        if (!std::is_same<TG, T>::value) {
+#pragma unroll
+            for (int l = 0; l < n; l++) y[l] *= gscale;
+        }
         T *o = Aq + (e0 + el) * NP + r * n;
 #pragma unroll
         for (int l = 0; l < n; l++) o[l] = y[l];
@@ -239,6 +249,18 @@ __device__ __forceinline__ void bp30_block(T *smem, int64_t e0, int nel, const T
         const double tot = block_sum((double)dot, reinterpret_cast<double *>(smem));
         if (threadIdx.x == 0) *part_out = tot;
     }
+}
+
+// Minimum resident blocks per SM that the register allocation must allow
+// (0: the compiler's own heuristic); see bp35_min_blocks.  Chosen per precision and
+// degree from the operator sweep on GB300.
+template <typename T, int N>
+constexpr int bp30_min_blocks() {
+    if (sizeof(T) == 8) return (N >= 9 && N <= 14) ? 2 : 0;
+    if (N >= 9 && N <= 12) return 4;
+    if (N == 13) return 3;
+    if (N == 15) return 2;
+    return 0;
 }
 
 }  // namespace

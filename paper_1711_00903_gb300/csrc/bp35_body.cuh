@@ -3,6 +3,8 @@
 // bp35.cu for the algorithm and the GB300 design.
 #pragma once
 
+#include <type_traits>
+
 #include "eo.cuh"
 
 namespace fem {
@@ -34,12 +36,13 @@ struct Bp35Cfg : Bp35Layout<T, N, pick_epb(N + 1, 3 * Box<N + 1, N + 1, N + 1>::
 // already in the first box of each element (boxes: EPB x 3 boxes, filled
 // before a barrier): derivatives, chain rule with the factors, transposes,
 // output to Aq.  Gsrc points at the factors of element e0, in global memory
-// or (G_SMEM) in shared memory, 7 planes of n^3 values per element.
+// or (G_SMEM) in shared memory, 7 planes of n^3 values per element, of type
+// TG (T, or FP16 scaled by a power of two that gscale undoes on the output).
 // Returns the thread's share of q . Aq (PCG; 0 otherwise).  Ends without a
 // barrier.
-template <typename T, int N, int EPB_, bool PCG, bool G_SMEM>
-__device__ __forceinline__ T bp35_core(T *smem, int64_t e0, int nel, const T *__restrict__ Gsrc, double lambda,
-                                       T *__restrict__ Aq) {
+template <typename T, int N, int EPB_, bool PCG, bool G_SMEM, typename TG = T>
+__device__ __forceinline__ T bp35_core(T *smem, int64_t e0, int nel, const TG *__restrict__ Gsrc, double lambda,
+                                       T *__restrict__ Aq, T gscale = T(1)) {
     using C = Bp35Layout<T, N, EPB_>;
     using B = typename C::B;
     constexpr int n = C::n, nn = C::nn, NP = C::NP;
@@ -73,7 +76,7 @@ __device__ __forceinline__ T bp35_core(T *smem, int64_t e0, int nel, const T *__
     T acc[n];
     const T lam = (T)lambda;
     if (act) {
-        const T *Ge = Gsrc + el * 7 * NP + r;
+        const TG *Ge = Gsrc + el * 7 * NP + r;
         T Rt[n];
 #pragma unroll
         for (int k = 0; k < n; k++) {
@@ -81,7 +84,8 @@ __device__ __forceinline__ T bp35_core(T *smem, int64_t e0, int nel, const T *__
             const T qr = sR[s], qs = sS[s];
             T g[7];
 #pragma unroll
-            for (int h = 0; h < 7; h++) g[h] = G_SMEM ? Ge[h * NP + k * nn] : __ldg(Ge + h * NP + k * nn);
+            for (int h = 0; h < 7; h++)
+                g[h] = G_SMEM ? factor_ld<T>(Ge + h * NP + k * nn) : factor_ldg<T>(Ge + h * NP + k * nn);
             sR[s] = g[0] * qr + g[1] * qs + g[2] * qt[k];
             sS[s] = g[1] * qr + g[3] * qs + g[4] * qt[k];
             Rt[k] = g[2] * qr + g[4] * qs + g[5] * qt[k];
@@ -116,7 +120,8 @@ __device__ __forceinline__ T bp35_core(T *smem, int64_t e0, int nel, const T *__
 #pragma unroll
         for (int k = 0; k < n; k++) {
             const int s = B::at(u, v, k);
-            const T w = acc[k] + sR[s] + sS[s];
+            T w = acc[k] + sR[s] + sS[s];
+            if (!std::is_same<TG, T>::value) w *= gscale;
             Ae[k * nn] = w;
             if (PCG) dot = fmx(sQ[s], w, dot);
         }
@@ -129,17 +134,18 @@ __device__ __forceinline__ T bp35_core(T *smem, int64_t e0, int nel, const T *__
 // bytes).  PCG = true: the input field is p <- z + beta p (stored back to p;
 // beta read from *beta, p not read when beta is 0), and thread 0 writes the
 // block's p . Ap to *part_out.
-template <typename T, int N, int EPB_, bool PCG>
-__device__ __forceinline__ void bp35_block(unsigned char *smem_raw, int64_t e0, int nel, const T *__restrict__ G,
+template <typename T, int N, int EPB_, bool PCG, typename TG = T>
+__device__ __forceinline__ void bp35_block(unsigned char *smem_raw, int64_t e0, int nel, const TG *__restrict__ G,
                                            double lambda, const T *__restrict__ q, T *__restrict__ Aq,
                                            const T *__restrict__ z, T *__restrict__ p,
-                                           const double *__restrict__ beta, double *__restrict__ part_out) {
+                                           const double *__restrict__ beta, double *__restrict__ part_out,
+                                           const double *__restrict__ ginv = nullptr) {
     using C = Bp35Layout<T, N, EPB_>;
     using B = typename C::B;
     constexpr int n = C::n, nn = C::nn, NP = C::NP;
     T *smem = reinterpret_cast<T *>(smem_raw);
     if (C::PREFETCH && threadIdx.x == 0)
-        prefetch_l2(G + e0 * 7 * NP, (long long)nel * 7 * NP * (long long)sizeof(T));
+        prefetch_l2(G + e0 * 7 * NP, (long long)nel * 7 * NP * (long long)sizeof(TG));
 
     // stage the input field of the block's elements (contiguous in memory)
     if (PCG) {
@@ -158,12 +164,24 @@ __device__ __forceinline__ void bp35_block(unsigned char *smem_raw, int64_t e0, 
         }
     }
     __syncthreads();
-    const T dot = bp35_core<T, N, EPB_, PCG, false>(smem, e0, nel, G + e0 * 7 * NP, lambda, Aq);
+    const T dot = bp35_core<T, N, EPB_, PCG, false, TG>(smem, e0, nel, G + e0 * 7 * NP, lambda, Aq,
+                                                        factor_unscale<T>(ginv));
     if (PCG) {
         __syncthreads();  // the shared boxes are reused for the reduction
         const double tot = block_sum((double)dot, reinterpret_cast<double *>(smem_raw));
         if (threadIdx.x == 0) *part_out = tot;
     }
+}
+
+// Minimum resident blocks per SM that the register allocation must allow
+// (0: the compiler's own heuristic).  At high degree the fully unrolled line
+// kernels take up to 255 registers and leave one block per SM; capping them
+// trades a few spills for latency hiding.  Chosen per precision and degree
+// from the operator sweep on GB300.
+template <typename T, int N>
+constexpr int bp35_min_blocks() {
+    if (sizeof(T) == 8) return N >= 10 ? 3 : 0;
+    return N == 15 ? 3 : 0;
 }
 
 }  // namespace

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "../../include/fem.h"
@@ -85,6 +86,22 @@ cudaError_t launch_bp30_f32(const fem_basis *b, int64_t E, const float *G, doubl
                             float *Aq, cudaStream_t s);
 cudaError_t launch_bp30_pcg(const fem_basis *b, int64_t E, const double *G, double lambda, const double *z,
                             double *p, const double *beta, double *Ap, double *partials, cudaStream_t s);
+// half-precision factors (FEM_PCG_MIXED16): binary16 planes scaled by a
+// power of two, the inverse scale at ginv (device)
+cudaError_t launch_bp35_f16g(const fem_basis *b, int64_t E, const __half *G, const double *ginv, double lambda,
+                             const float *q, float *Aq, cudaStream_t s);
+cudaError_t launch_bp35_pcg_f16g(const fem_basis *b, int64_t E, const __half *G, const double *ginv, double lambda,
+                                 const float *z, float *p, const double *beta, float *Ap, double *partials,
+                                 cudaStream_t s);
+int64_t bp35_f16_blocks(int N, int64_t E);
+cudaError_t prepare_bp35_f16(int N, const double *fold_table);
+cudaError_t wait_timeouts_bp35_f16(unsigned long long *count, bool reset);
+cudaError_t launch_bp30_f16g(const fem_basis *b, int64_t E, const __half *G, const double *ginv, double lambda,
+                             const float *q, float *Aq, cudaStream_t s);
+cudaError_t launch_bp30_pcg_f16g(const fem_basis *b, int64_t E, const __half *G, const double *ginv, double lambda,
+                                 const float *z, float *p, const double *beta, float *Ap, double *partials,
+                                 cudaStream_t s);
+cudaError_t prepare_bp30_f16(int N, const double *fold_table);
 cudaError_t launch_bp30_pcg_f32(const fem_basis *b, int64_t E, const float *G, double lambda, const float *z,
                                 float *p, const double *beta, float *Ap, double *partials, cudaStream_t s);
 int64_t bp30_blocks(int N, int64_t E, bool f32);
@@ -112,6 +129,6 @@ cudaError_t pcg_begin(fem_pcg *s, const double *b, double *x, const fem_pcg_opts
 int pcg_advance(fem_pcg *s, bool blocking);
 int pcg_solve(fem_pcg *s, const double *b, double *x, const fem_pcg_opts *o, fem_pcg_info *info, cudaStream_t st);
 int pcg_status(const fem_pcg *s, fem_pcg_info *info);
-constexpr int kPcgScalars = 11;  // doubles of pinned host memory a solver context needs
+constexpr int kPcgScalars = 13;  // doubles of pinned host memory a solver context needs
 
 }  // namespace fem

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "fem_internal.h"
@@ -110,6 +111,22 @@ static __device__ unsigned long long g_wait_timeouts;
         }                                                                                    \
         return e;                                                                            \
     }
+
+// A geometric factor read as the arithmetic type T: FP64 and FP32 factors
+// as they are, FP16 factors (the half-precision inner operator) widened.
+template <typename T>
+__device__ __forceinline__ T factor_ldg(const T *p) { return __ldg(p); }
+template <typename T>
+__device__ __forceinline__ T factor_ldg(const __half *p) { return (T)__half2float(__ldg(p)); }
+template <typename T>
+__device__ __forceinline__ T factor_ld(const T *p) { return *p; }
+template <typename T>
+__device__ __forceinline__ T factor_ld(const __half *p) { return (T)__half2float(*p); }
+
+// Scale that undoes the power-of-two scaling of FP16 factors: read from
+// device memory when given (set by the solver on the device), else 1.
+template <typename T>
+__device__ __forceinline__ T factor_unscale(const double *ginv) { return ginv ? (T)(*ginv) : T(1); }
 
 // Fused multiply-add in the precision of the operands.
 __device__ __forceinline__ double fmx(double a, double b, double c) { return fma(a, b, c); }

@@ -39,6 +39,8 @@ enum {
     S_BREAK,     // 1 on p . Ap <= 0 or a non-finite value
     S_ITER,      // iterations completed
     S_RR_OUTER,  // FP64 residual norm^2 of the defect-correction loop
+    S_GMAX,      // FEM_PCG_MIXED16: largest |factor| (bits of a non-negative double)
+    S_GINV,      // FEM_PCG_MIXED16: inverse of the FP16 factor scale
     S_COUNT
 };
 
@@ -171,6 +173,35 @@ __global__ void __launch_bounds__(kVecThreads) cast_f32_kernel(int64_t n, const 
                                                                float *__restrict__ b) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         b[i] = (float)a[i];
+}
+
+// FP16 factors: the largest |a| (atomic maximum on the bit pattern, which
+// orders non-negative doubles like their values) ...
+__global__ void __launch_bounds__(kVecThreads) absmax_kernel(int64_t n, const double *__restrict__ a,
+                                                             unsigned long long *__restrict__ out) {
+    double m = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(a[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// ... then a[i] * s rounded to binary16 with s = 2^(14 - e), max|a| < 2^e:
+// the largest factor lands in [2^13, 2^14), far from the binary16 overflow
+// (65504), and the small off-diagonal factors stay normal numbers.  The
+// inverse 1/s goes to *ginv for the operator kernels.
+__global__ void __launch_bounds__(kVecThreads) cast_f16_kernel(int64_t n, const double *__restrict__ a,
+                                                               __half *__restrict__ b,
+                                                               const unsigned long long *__restrict__ gmax,
+                                                               double *__restrict__ ginv) {
+    const double mx = __longlong_as_double((long long)*gmax);
+    int ex = 0;
+    if (mx > 0.0) frexp(mx, &ex);  // mx = f 2^ex, f in [0.5, 1)
+    const double sc = ldexp(1.0, 14 - ex);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *ginv = ldexp(1.0, ex - 14);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = __double2half(a[i] * sc);
 }
 
 // partial sums of x . y per block (grid-stride, fixed order)
@@ -430,6 +461,7 @@ struct fem_pcg {
     int device;
     double *r, *z, *p, *q, *dinv;                   // FP64 recurrence (q also holds A x)
     float *G32, *dinv32, *d32, *r32, *z32, *p32, *q32;  // FP32 inner recurrence (mixed mode)
+    __half *G16;                                        // FP16 factors (FEM_PCG_MIXED16)
     double *part;
     int64_t nparts;
     double *scal;       // device scalars
@@ -475,6 +507,7 @@ cudaError_t op_apply64(fem_pcg *s, const double *x, double *out, cudaStream_t st
                                 : launch_bp35(s->basis, s->E, s->G, s->lambda, x, out, st);
 }
 int64_t op_blocks(const fem_pcg *s, bool f32) {
+    if (f32 && s->mode == FEM_PCG_MIXED16 && s->op == FEM_OP_BP35) return bp35_f16_blocks(s->basis->host.N, s->E);
     return s->op == FEM_OP_BP30 ? bp30_blocks(s->basis->host.N, s->E, f32) : bp35_blocks(s->basis->host.N, s->E, f32);
 }
 cudaError_t op_pcg(fem_pcg *s, const double *G, const double *z, double *p, double *Ap, cudaStream_t st) {
@@ -483,6 +516,11 @@ cudaError_t op_pcg(fem_pcg *s, const double *G, const double *z, double *p, doub
                : launch_bp35_pcg(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, s->part, st);
 }
 cudaError_t op_pcg(fem_pcg *s, const float *G, const float *z, float *p, float *Ap, cudaStream_t st) {
+    if (s->mode == FEM_PCG_MIXED16)
+        return s->op == FEM_OP_BP30 ? launch_bp30_pcg_f16g(s->basis, s->E, s->G16, s->scal + S_GINV, s->lambda, z, p,
+                                                           s->scal + S_BETA, Ap, s->part, st)
+                                    : launch_bp35_pcg_f16g(s->basis, s->E, s->G16, s->scal + S_GINV, s->lambda, z, p,
+                                                           s->scal + S_BETA, Ap, s->part, st);
     return s->op == FEM_OP_BP30
                ? launch_bp30_pcg_f32(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, s->part, st)
                : launch_bp35_pcg_f32(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, s->part, st);
@@ -619,7 +657,11 @@ cudaError_t pcg_create_on(fem_pcg *s, cudaStream_t st, double *lent_hscal) {
         if (e == cudaSuccess) e = alloc(&s->p, len, st);
         if (e == cudaSuccess) e = alloc(&s->dinv, len, st);
     } else {
-        if (e == cudaSuccess) e = alloc(&s->G32, 7 * s->E * s->gpts, st);
+        if (s->mode == FEM_PCG_MIXED16) {
+            if (e == cudaSuccess) e = alloc(&s->G16, 7 * s->E * s->gpts, st);
+        } else {
+            if (e == cudaSuccess) e = alloc(&s->G32, 7 * s->E * s->gpts, st);
+        }
         if (e == cudaSuccess) e = alloc(&s->dinv32, len, st);
         if (e == cudaSuccess) e = alloc(&s->d32, len, st);
         if (e == cudaSuccess) e = alloc(&s->r32, len, st);
@@ -644,8 +686,13 @@ cudaError_t pcg_create_on(fem_pcg *s, cudaStream_t st, double *lent_hscal) {
         e = dispatch_degree<Dinv30Launch>(s->basis->host.N, s->basis, s->E, s->G, s->lambda, s->dinv, s->dinv32, st);
     else
         e = dispatch_degree<DinvLaunch>(s->basis->host.N, s->basis, s->E, s->G, s->lambda, s->dinv, s->dinv32, st);
-    if (e == cudaSuccess && s->mode != FEM_PCG_FP64)
+    if (e == cudaSuccess && s->mode == FEM_PCG_MIXED)
         cast_f32_kernel<<<kVecBlocks, kVecThreads, 0, st>>>(7 * s->E * s->gpts, s->G, s->G32);
+    if (e == cudaSuccess && s->mode == FEM_PCG_MIXED16) {
+        unsigned long long *gmax = reinterpret_cast<unsigned long long *>(s->scal + S_GMAX);
+        absmax_kernel<<<kVecBlocks, kVecThreads, 0, st>>>(7 * s->E * s->gpts, s->G, gmax);
+        cast_f16_kernel<<<kVecBlocks, kVecThreads, 0, st>>>(7 * s->E * s->gpts, s->G, s->G16, gmax, s->scal + S_GINV);
+    }
     if (e == cudaSuccess) e = cudaGetLastError();
     return e;
 }
@@ -659,8 +706,8 @@ cudaError_t pcg_create(fem_pcg *s) {
 // Frees the workspace, stream-ordered on st (the workspace must not be in
 // use by work on other streams).
 void pcg_release_on(fem_pcg *s, cudaStream_t st) {
-    void *bufs[] = {s->r,   s->z,   s->p,   s->q,   s->dinv, s->G32, s->dinv32,
-                    s->d32, s->r32, s->z32, s->p32, s->q32,  s->part, s->scal};
+    void *bufs[] = {s->r,   s->z,   s->p,   s->q,    s->dinv, s->G32,  s->dinv32, s->d32,
+                    s->r32, s->z32, s->p32, s->q32, s->G16,  s->part, s->scal};
     for (void *b : bufs)
         if (b) cudaFreeAsync(b, st);
     if (s->ev) cudaEventDestroy(s->ev);
@@ -885,7 +932,8 @@ int fem_bp30_jacobi(const fem_basis *b, int64_t E, const double *G, double lambd
 namespace fem {
 
 int pcg_new(const fem_basis *b, int op, int64_t E, const double *G, double lambda, int mode, fem_pcg **out) {
-    if (!b || !out || E < 1 || !G || (mode != FEM_PCG_FP64 && mode != FEM_PCG_MIXED)) return FEM_EINVAL;
+    if (!b || !out || E < 1 || !G || (mode != FEM_PCG_FP64 && mode != FEM_PCG_MIXED && mode != FEM_PCG_MIXED16))
+        return FEM_EINVAL;
     if (op != FEM_OP_BP35 && op != FEM_OP_BP30) return FEM_EINVAL;
     if (!(lambda >= 0.0)) return FEM_EINVAL;
     *out = nullptr;

@@ -49,8 +49,8 @@ int64_t footprint(const fem_serve_request &r) {
     bytes += 8 * 3 * (r.E + 3 * 152 * 8);                        // partial sums (upper bound)
     if (r.mode == FEM_PCG_FP64)
         bytes += 8 * 5 * len;  // q, r, z, p, 1/diag
-    else
-        bytes += 8 * len + 4 * (7 * r.E * gpts + 6 * len);  // q (FP64); FP32 factors and 6 vectors
+    else  // q (FP64); FP32 (or FP16) factors and 6 FP32 vectors
+        bytes += 8 * len + (r.mode == FEM_PCG_MIXED16 ? 2 : 4) * 7 * r.E * gpts + 4 * 6 * len;
     return bytes + 64 * 1024;
 }
 
@@ -168,7 +168,8 @@ int fem_serve_submit(fem_server *s, const fem_serve_request *req, int64_t *id) {
     if (!s || !req || !id) return FEM_EINVAL;
     const fem_serve_request &q = *req;
     if ((q.op != FEM_OP_BP35 && q.op != FEM_OP_BP30) || q.N < 1 || q.N > FEM_MAX_N || q.E < 1) return FEM_EINVAL;
-    if (!q.verts || !q.rhs || !q.x || (q.mode != FEM_PCG_FP64 && q.mode != FEM_PCG_MIXED)) return FEM_EINVAL;
+    if (!q.verts || !q.rhs || !q.x || (q.mode != FEM_PCG_FP64 && q.mode != FEM_PCG_MIXED && q.mode != FEM_PCG_MIXED16))
+        return FEM_EINVAL;
     if (!(q.lambda >= 0.0) || !(q.tol > 0.0)) return FEM_EINVAL;
     Request R;
     std::memset((void *)&R, 0, sizeof R);

@@ -87,3 +87,40 @@ def test_bp30_manufactured_solution(N):
     x, it, rel = oracle.pcg_bp30(N, G, 1.0, b, tol=1e-12)
     assert rel <= 1e-12 and it > 0
     assert np.linalg.norm(x - u) / np.linalg.norm(u) <= 1e-9
+
+
+def _rounded_factors(G, kind):
+    """Factors rounded to binary16 after a power-of-two scaling that puts the
+    largest below 2^14 (and back), or to FP32."""
+    if kind == "fp32":
+        return G.astype(np.float32).astype(np.float64)
+    e = int(np.frexp(np.abs(G).max())[1])
+    s = 2.0 ** (14 - e)
+    return (G * s).astype(np.float16).astype(np.float64) / s
+
+
+@pytest.mark.parametrize("kind", ["fp32", "fp16"])
+def test_defect_correction_with_rounded_factors(kind):
+    """FP64 defect correction whose inner PCG applies the operator with
+    rounded factors (the inner operator of the mixed solver modes): every
+    outer step reduces the FP64 residual by about the inner tolerance, with
+    binary16 factors as with FP32 ones, and the outer loop reaches 1e-10."""
+    N = 5
+    v = fem_synth.box_mesh(4)
+    G, _ = oracle.geofacs(N, oracle.KIND_BP35, v)
+    X = oracle.gll_node_coordinates(N, v)
+    u = np.sin(np.pi * X[..., 0]) * np.sin(np.pi * X[..., 1]) * np.sin(np.pi * X[..., 2])
+    b = oracle.bp35(N, G, 1.0, u)
+    Gl = _rounded_factors(G, kind)
+    x = np.zeros_like(b)
+    hist = []
+    for _ in range(8):
+        r = b - oracle.bp35(N, G, 1.0, x)
+        hist.append(np.linalg.norm(r) / np.linalg.norm(b))
+        if hist[-1] <= 1e-10:
+            break
+        d, _, _ = oracle.pcg_bp35(N, Gl, 1.0, r, tol=1e-3)
+        x = x + d
+    assert hist[-1] <= 1e-10 and len(hist) <= 5
+    factors = [hist[k + 1] / hist[k] for k in range(len(hist) - 1)]
+    assert max(factors) <= 3e-3

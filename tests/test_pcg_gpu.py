@@ -101,6 +101,41 @@ def test_staged_f32_operator_ragged_blocks_and_no_wait_timeouts():
     assert fem.fem_wait_timeouts() == 0
 
 
+def _f16_factors(G):
+    """binary16 factors scaled by 2^(14 - e), max|G| < 2^e, as the solver
+    scales them, and the inverse scale."""
+    e = int(np.frexp(np.abs(G).max())[1])
+    s = 2.0 ** (14 - e)
+    G16 = (G * s).astype(np.float16)
+    return G16, 1.0 / s
+
+
+@pytest.mark.parametrize("op", ["bp35", "bp30"])
+@pytest.mark.parametrize("N", [1, 2, 3, 6, 7, 9, 12, 15])
+def test_f16_factor_operators(op, N):
+    """Half-precision-factor operators against the FP64 oracle applied to the
+    same rounded factors (unscaled) and the same FP32-rounded field: the
+    difference is FP32 arithmetic only.  Odd N up to 9 exercise the BP3.5
+    stream kernel with FP16 stages, the others the block kernels."""
+    fem, torch = _fem(), _torch()
+    v = fem_synth.box_mesh(3)[:23]
+    E = v.shape[0]
+    kind = oracle.KIND_BP35 if op == "bp35" else oracle.KIND_BP30
+    G, _ = oracle.geofacs(N, kind, v)
+    G16, ginv = _f16_factors(G)
+    q32 = fem_synth.field(7, E, (N + 1) ** 3).astype(np.float32)
+    Gr = G16.astype(np.float64) * ginv
+    ref = (oracle.bp35 if op == "bp35" else oracle.bp30)(N, Gr, 1.0, q32.astype(np.float64))
+    b = fem.fem_basis_setup(N)
+    gi = torch.tensor([ginv], dtype=torch.float64, device="cuda")
+    fn = fem.fem_bp35_apply_f16g if op == "bp35" else fem.fem_bp30_apply_f16g
+    got = fn(b, torch.from_numpy(G16).to("cuda"), gi, 1.0, _dev(q32)).cpu().numpy().astype(np.float64)
+    assert _rel(got, ref) < 2e-6 * (N + 2)
+    # the rounded factors are within binary16 precision of the FP64 ones
+    assert np.abs(Gr - G).max() <= 2.0 ** -11 * np.abs(G).max()
+    assert fem.fem_wait_timeouts() == 0
+
+
 def test_dot_deterministic_and_exact():
     fem, torch = _fem(), _torch()
     x = fem_synth.field(11, 1, 3_000_001)[0]
@@ -114,7 +149,7 @@ def test_dot_deterministic_and_exact():
     assert fem.fem_dot(xd[:0], yd[:0]).item() == 0.0
 
 
-@pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("mode", [0, 1, 2], ids=["fp64", "mixed", "mixed16"])
 @pytest.mark.parametrize("N", [2, 4, 7])
 def test_pcg_manufactured(N, mode):
     fem = _fem()
@@ -222,7 +257,7 @@ def test_bp30_jacobi_diagonal(N):
     assert _rel(got, ref) < 1e-12
 
 
-@pytest.mark.parametrize("mode", [0, 1], ids=["fp64", "mixed"])
+@pytest.mark.parametrize("mode", [0, 1, 2], ids=["fp64", "mixed", "mixed16"])
 @pytest.mark.parametrize("N", [2, 5])
 def test_bp30_pcg_manufactured(N, mode):
     fem = _fem()

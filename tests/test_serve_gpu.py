@@ -17,7 +17,9 @@ def _fem():
 
 def _requests():
     out = []
-    specs = [(2, 2, 2, 2, 0), (3, 3, 2, 2, 1), (3, 4, 2, 1, 0), (2, 5, 3, 2, 1), (3, 2, 1, 3, 1), (2, 6, 2, 2, 0)]
+    # last column: 0 FP64, 1 mixed (FP32 factors), 2 mixed with FP16 factors
+    specs = [(2, 2, 2, 2, 0), (3, 3, 2, 2, 1), (3, 4, 2, 1, 0), (2, 5, 3, 2, 2), (3, 2, 1, 3, 1), (2, 6, 2, 2, 0),
+             (3, 3, 2, 1, 2), (2, 7, 2, 2, 2)]
     for k, (op, N, nx, ny, mixed) in enumerate(specs):
         v = fem_synth.box_mesh(nx, ny, 2, jitter=0.1, seed=700 + k)
         rhs = fem_synth.field(800 + k, v.shape[0], (N + 1) ** 3)
@@ -29,8 +31,8 @@ def _run(server, reqs, one_at_a_time, tol=1e-9):
     fem = _fem()
     ids = []
     for op, N, v, rhs, lam, mixed in reqs:
-        rid, x = server.submit(op, N, v, rhs, lam=lam, mode=fem.FEM_PCG_MIXED if mixed else fem.FEM_PCG_FP64,
-                               tol=tol)
+        mode = (fem.FEM_PCG_FP64, fem.FEM_PCG_MIXED, fem.FEM_PCG_MIXED16)[mixed]
+        rid, x = server.submit(op, N, v, rhs, lam=lam, mode=mode, tol=tol)
         ids.append((rid, x))
         if one_at_a_time:
             server.drain()
