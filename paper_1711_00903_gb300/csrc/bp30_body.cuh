@@ -35,22 +35,23 @@ struct Bp30Layout {
 // Elements per block of the stand-alone kernel: as many as fit 256 threads
 // under the shared-memory budget.
 template <int N, typename T = double>
-struct Bp30Cfg : Bp30Layout<N, pick_epb(N + 2, 3 * Box<N + 2, N + 2, N + 2>::size * (int)sizeof(T)), T> {};
+struct Bp30Cfg : Bp30Layout<N, pick_epb(N + 2, 3 * Box<N + 2, N + 2, N + 2>::size * (int)sizeof(T), sizeof(T) == 8 ? FEM_EXP_T_BP30 : 256), T> {};
 
 // BP3.0 of elements [e0, e0 + nel) (nel <= EPB) by the whole block
 // (blockDim.x >= Layout::threads), shared memory at smem (Layout::smem
 // bytes).  PCG = true: the input field is p <- z + beta p (stored back to p;
 // beta read from *beta, p not read when beta is 0), and thread 0 writes the
 // block's p . Ap to *part_out.
-// TG: type of the factors (T, or FP16 scaled by a power of two that the
-// value at ginv undoes on the output).
-template <int N, int EPB_, typename T = double, bool PCG = false, typename TG = T>
-__device__ __forceinline__ void bp30_block(T *smem, int64_t e0, int nel, const TG *__restrict__ G, double lambda,
-                                           const T *__restrict__ q, T *__restrict__ Aq,
-                                           const T *__restrict__ z = nullptr, T *__restrict__ p = nullptr,
-                                           const double *__restrict__ beta = nullptr,
-                                           double *__restrict__ part_out = nullptr,
-                                           const double *__restrict__ ginv = nullptr) {
+// The operator on elements [e0, e0 + nel) whose input field is already in
+// buffer B of each element (filled before a barrier): phases 1-9 below.
+// Gsrc points at the factors of element e0, in global memory or (G_SMEM) in
+// shared memory, 7 planes of m^3 values per element, of type TG (T, or FP16
+// scaled by a power of two that gscale undoes on the output).  PCG: p holds
+// the input field in global memory (the staging wrote it) for the thread's
+// share of p . Ap, which is returned.  Ends without a barrier.
+template <int N, int EPB_, typename T, bool PCG, bool G_SMEM, typename TG>
+__device__ __forceinline__ T bp30_core(T *smem, int64_t e0, int nel, const TG *__restrict__ Gsrc, double lambda,
+                                       T *__restrict__ Aq, const T *__restrict__ p, T gscale) {
     using C = Bp30Layout<N, EPB_, T>;
     using B0 = typename C::B0;
     using B1 = typename C::B1;
@@ -58,25 +59,6 @@ __device__ __forceinline__ void bp30_block(T *smem, int64_t e0, int nel, const T
     using B3 = typename C::B3;
     constexpr int n = C::n, m = C::m, NP = C::NP, MP = C::MP, mm = C::mm, EPB = C::EPB;
     constexpr int S = C::S, per = C::per;
-    // per element: buffer A = smem + el*per, B = A + S, C = A + 2S
-    if (C::PREFETCH && threadIdx.x == 0)
-        prefetch_l2(G + e0 * 7 * MP, (long long)nel * 7 * MP * (long long)sizeof(TG));
-    if (PCG) {
-        const T bt = (T)(*beta);
-        for (int t = threadIdx.x; t < nel * NP; t += blockDim.x) {
-            const int el = t / NP, s = t - el * NP;
-            const int64_t g = e0 * NP + t;
-            const T v = (bt == T(0)) ? z[g] : fmx(bt, p[g], z[g]);
-            p[g] = v;
-            smem[el * per + S + B0::at(s % n, (s / n) % n, s / (n * n))] = v;
-        }
-    } else {
-        for (int t = threadIdx.x; t < nel * NP; t += blockDim.x) {
-            const int el = t / NP, s = t - el * NP;
-            smem[el * per + S + B0::at(s % n, (s / n) % n, s / (n * n))] = __ldg(q + e0 * NP + t);
-        }
-    }
-    __syncthreads();
 
     // 1. r-interpolation (j, k): q (buffer B) -> X1 (buffer C)
     for_tasks<n * n, EPB>(nel, [&](int el, int r) {
@@ -153,14 +135,14 @@ __device__ __forceinline__ void bp30_block(T *smem, int64_t e0, int nel, const T
 #pragma unroll
         for (int l = 0; l < m; l++) x[l] = QG[B3::at(ca, cb, l)];
         eo_apply<m, m, -1, C::oDt>(x, ut);
-        const TG *Ge = G + (e0 + cel) * 7 * MP + cr;
+        const TG *Ge = Gsrc + cel * 7 * MP + cr;
 #pragma unroll
         for (int c = 0; c < m; c++) {
             const int s = B3::at(ca, cb, c);
             const T ur = UR[s], us = US[s];
             T g[7];
 #pragma unroll
-            for (int h = 0; h < 7; h++) g[h] = factor_ldg<T>(Ge + h * MP + c * mm);
+            for (int h = 0; h < 7; h++) g[h] = G_SMEM ? factor_ld<T>(Ge + h * MP + c * mm) : factor_ldg<T>(Ge + h * MP + c * mm);
             UR[s] = g[0] * ur + g[1] * us + g[2] * ut[c];
             US[s] = g[1] * ur + g[3] * us + g[4] * ut[c];
             Rt[c] = g[2] * ur + g[4] * us + g[5] * ut[c];
@@ -223,7 +205,6 @@ __device__ __forceinline__ void bp30_block(T *smem, int64_t e0, int nel, const T
 
     // 9. r-projection (j, k): X4 (B) -> Aq
     T dot = T(0);  // p . Ap of the thread's lines (PCG), in the data's precision
-    const T gscale = std::is_same<TG, T>::value ? T(1) : factor_unscale<T>(ginv);
     for_tasks<n * n, EPB>(nel, [&](int el, int r) {
         const T *X4 = smem + el * per + S;
         const int j = r % n, k = r / n;
@@ -244,6 +225,43 @@ __device__ __forceinline__ void bp30_block(T *smem, int64_t e0, int nel, const T
             for (int l = 0; l < n; l++) dot = fmx(pp[l], y[l], dot);
         }
     });
+    return dot;
+}
+
+// TG: type of the factors (T, or FP16 scaled by a power of two that the
+// value at ginv undoes on the output).
+template <int N, int EPB_, typename T = double, bool PCG = false, typename TG = T>
+__device__ __forceinline__ void bp30_block(T *smem, int64_t e0, int nel, const TG *__restrict__ G, double lambda,
+                                           const T *__restrict__ q, T *__restrict__ Aq,
+                                           const T *__restrict__ z = nullptr, T *__restrict__ p = nullptr,
+                                           const double *__restrict__ beta = nullptr,
+                                           double *__restrict__ part_out = nullptr,
+                                           const double *__restrict__ ginv = nullptr) {
+    using C = Bp30Layout<N, EPB_, T>;
+    using B0 = typename C::B0;
+    constexpr int n = C::n, NP = C::NP, MP = C::MP;
+    constexpr int S = C::S, per = C::per;
+    // per element: buffer A = smem + el*per, B = A + S, C = A + 2S
+    if (C::PREFETCH && threadIdx.x == 0)
+        prefetch_l2(G + e0 * 7 * MP, (long long)nel * 7 * MP * (long long)sizeof(TG));
+    if (PCG) {
+        const T bt = (T)(*beta);
+        for (int t = threadIdx.x; t < nel * NP; t += blockDim.x) {
+            const int el = t / NP, s = t - el * NP;
+            const int64_t g = e0 * NP + t;
+            const T v = (bt == T(0)) ? z[g] : fmx(bt, p[g], z[g]);
+            p[g] = v;
+            smem[el * per + S + B0::at(s % n, (s / n) % n, s / (n * n))] = v;
+        }
+    } else {
+        for (int t = threadIdx.x; t < nel * NP; t += blockDim.x) {
+            const int el = t / NP, s = t - el * NP;
+            smem[el * per + S + B0::at(s % n, (s / n) % n, s / (n * n))] = __ldg(q + e0 * NP + t);
+        }
+    }
+    __syncthreads();
+    const T gscale = std::is_same<TG, T>::value ? T(1) : factor_unscale<T>(ginv);
+    const T dot = bp30_core<N, EPB_, T, PCG, false, TG>(smem, e0, nel, G + e0 * 7 * MP, lambda, Aq, p, gscale);
     if (PCG) {
         __syncthreads();  // the shared boxes are reused for the reduction
         const double tot = block_sum((double)dot, reinterpret_cast<double *>(smem));

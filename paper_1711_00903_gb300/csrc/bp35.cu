@@ -19,7 +19,7 @@
 //     column stays in registers, four barriers per element;
 //   * several elements per block (n^2 threads each), coalesced loads of q
 //     and of each geometric-factor plane, coalesced stores.
-// FP32 at odd degree up to 9 (the mixed solver's hot kernel) runs as a
+// FP32 at degree up to 9 (the mixed solver's hot kernel) runs as a
 // persistent, double-buffered TMA stream instead (see bp35_stream_kernel).
 #include "bp35_stream.cuh"
 

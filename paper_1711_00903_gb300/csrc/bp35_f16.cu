@@ -7,9 +7,9 @@
 // read from device memory.  Half the factor bytes of the FP32 operator: 22
 // instead of 36 bytes per degree of freedom at every N.
 //
-// Same two kernel forms as FP32: the persistent TMA stream kernel at odd
-// N <= 9 (bp35_stream.cuh) and the block-per-element-group kernel with an
-// L2 prefetch elsewhere.
+// Same two kernel forms as FP32: the persistent TMA stream kernel up to
+// N = 9 (bp35_stream.cuh) and the block-per-element-group kernel with an
+// L2 prefetch above.
 #include "bp35_stream.cuh"
 
 namespace fem {

@@ -1,5 +1,5 @@
 // The persistent, double-buffered TMA stream form of the FP32 BP3.5 operator
-// (odd degree up to 9), shared by the FP32-factor kernels (bp35.cu) and the
+// (degree up to 9), shared by the FP32-factor kernels (bp35.cu) and the
 // FP16-factor kernels of the half-precision inner operator (bp35_f16.cu).
 #pragma once
 
@@ -19,9 +19,11 @@ namespace {
 // planes and input field(s) (contiguous ranges) into one of two shared
 // stages, completing on that stage's mbarrier, one group ahead of the
 // compute, so each SM always has a group's bytes in flight while it
-// computes the previous one.  Needs n even (every element's ranges then
-// span multiples of 16 bytes): odd N, up to 9 (two stages must fit).
-constexpr bool bp35_streamed(int N) { return (N % 2) == 1 && N <= 9; }
+// computes the previous one.  For odd n (even N) an element's ranges are not
+// multiples of 16 bytes; each range is then copied as its enclosing
+// 16-byte-aligned range (range_copy_plan) and read at its offset.  Up to
+// N = 9 (two stages must fit in shared memory).
+constexpr bool bp35_streamed(int N) { return N <= 9; }
 constexpr int kStreamThreads35 = 128;
 
 template <int N, bool PCG, typename TG = float>
@@ -32,7 +34,12 @@ struct Bp35Stream {
     static constexpr int threads = L::threads;
     static constexpr int gElem = 7 * NP * (int)sizeof(TG);      // factor bytes per element
     static constexpr int vElem = NP * 4;                        // field bytes per element
-    static constexpr int stage = EPS * (gElem + (PCG ? 2 : 1) * vElem);
+    // element ranges on 16-byte boundaries (n even): plain bulk copies;
+    // otherwise room for each range's aligned enclosing range
+    static constexpr bool ALIGNED = gElem % 16 == 0 && vElem % 16 == 0;
+    static constexpr int gRegion = ALIGNED ? EPS * gElem : ((EPS * gElem + 32 + 15) / 16) * 16;
+    static constexpr int vRegion = ALIGNED ? EPS * vElem : ((EPS * vElem + 32 + 15) / 16) * 16;
+    static constexpr int stage = gRegion + (PCG ? 2 : 1) * vRegion;
     static constexpr int oStage = 16;                           // two mbarriers, then the stages
     static constexpr int oBox = oStage + 2 * stage;
     static constexpr int smem = oBox + (L::smem > 256 ? L::smem : 256);
@@ -41,7 +48,6 @@ struct Bp35Stream {
     // flight per SM
     static constexpr int per_sm_raw = (220 * 1024) / (smem + 1024);
     static constexpr int blocks_per_sm = per_sm_raw > 8 ? 8 : (per_sm_raw < 1 ? 1 : per_sm_raw);
-    static_assert(gElem % 16 == 0 && vElem % 16 == 0, "bulk copies move multiples of 16 bytes");
 };
 
 template <int N, bool PCG, typename TG>
@@ -60,17 +66,48 @@ bp35_stream_kernel(int64_t E, const TG *__restrict__ G, double lambda, const flo
     const float gscale = factor_unscale<float>(ginv);
     const bool read_p = PCG && bt != 0.0f;
 
+    const float *fld = PCG ? z : q;
+    const TG *G_end = G + E * 7 * NP;
+    const float *fld_end = fld + E * NP;
+    const float *p_end = PCG ? p + E * NP : nullptr;
+    // the copy plans of group g: factors, field, and (PCG, beta != 0) p
+    struct Plans {
+        RangeCopy g, v, p;
+    };
+    auto plans = [&](int64_t g) {
+        const int64_t e0 = g * EPS;
+        const int nel = (int)((E - e0) < EPS ? (E - e0) : EPS);
+        Plans pl;
+        if constexpr (S::ALIGNED) {
+            pl.g = RangeCopy{(unsigned)(nel * S::gElem), 0u};
+            pl.v = RangeCopy{(unsigned)(nel * S::vElem), 0u};
+            pl.p = RangeCopy{read_p ? (unsigned)(nel * S::vElem) : 0u, 0u};
+        } else {
+            pl.g = range_copy_plan(G + e0 * 7 * NP, (unsigned long long)nel * S::gElem, G_end);
+            pl.v = range_copy_plan(fld + e0 * NP, (unsigned long long)nel * S::vElem, fld_end);
+            pl.p = read_p ? range_copy_plan(p + e0 * NP, (unsigned long long)nel * S::vElem, p_end) : RangeCopy{0u, 0u};
+        }
+        return pl;
+    };
     // stage k of group g: [factors | field (q or z) | p]
     auto issue = [&](int64_t g, int k) {
         const int64_t e0 = g * EPS;
         const int nel = (int)((E - e0) < EPS ? (E - e0) : EPS);
         unsigned char *st = smem_raw + S::oStage + k * S::stage;
-        const unsigned gb = (unsigned)(nel * S::gElem), vb = (unsigned)(nel * S::vElem);
+        const Plans pl = plans(g);
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        mbar_arrive_expect_tx(&bar[k], gb + vb + (read_p ? vb : 0u));
-        bulk_g2s(st, G + e0 * 7 * NP, gb, &bar[k]);
-        bulk_g2s(st + EPS * S::gElem, (PCG ? z : q) + e0 * NP, vb, &bar[k]);
-        if (read_p) bulk_g2s(st + EPS * (S::gElem + S::vElem), p + e0 * NP, vb, &bar[k]);
+        mbar_arrive_expect_tx(&bar[k], pl.g.tma_bytes + pl.v.tma_bytes + (read_p ? pl.p.tma_bytes : 0u));
+        if constexpr (S::ALIGNED) {
+            bulk_g2s(st, G + e0 * 7 * NP, pl.g.tma_bytes, &bar[k]);
+            bulk_g2s(st + S::gRegion, fld + e0 * NP, pl.v.tma_bytes, &bar[k]);
+            if (read_p) bulk_g2s(st + S::gRegion + S::vRegion, p + e0 * NP, pl.p.tma_bytes, &bar[k]);
+        } else {
+            range_copy_issue(st, G + e0 * 7 * NP, (unsigned long long)nel * S::gElem, pl.g, &bar[k]);
+            range_copy_issue(st + S::gRegion, fld + e0 * NP, (unsigned long long)nel * S::vElem, pl.v, &bar[k]);
+            if (read_p)
+                range_copy_issue(st + S::gRegion + S::vRegion, p + e0 * NP, (unsigned long long)nel * S::vElem, pl.p,
+                                 &bar[k]);
+        }
     };
 
     if (threadIdx.x == 0) {
@@ -93,10 +130,11 @@ bp35_stream_kernel(int64_t E, const TG *__restrict__ G, double lambda, const flo
 
         const int64_t e0 = g * EPS;
         const int nel = (int)((E - e0) < EPS ? (E - e0) : EPS);
+        const Plans pl = plans(g);
         const unsigned char *st = smem_raw + S::oStage + k * S::stage;
-        const TG *sG = reinterpret_cast<const TG *>(st);
-        const float *sV = reinterpret_cast<const float *>(st + EPS * S::gElem);
-        const float *sP = reinterpret_cast<const float *>(st + EPS * (S::gElem + S::vElem));
+        const TG *sG = reinterpret_cast<const TG *>(st + pl.g.offset);
+        const float *sV = reinterpret_cast<const float *>(st + S::gRegion + pl.v.offset);
+        const float *sP = reinterpret_cast<const float *>(st + S::gRegion + S::vRegion + pl.p.offset);
         for (int t = threadIdx.x; t < nel * NP; t += blockDim.x) {
             const int el = t / NP, s = t - el * NP;
             float v = sV[t];

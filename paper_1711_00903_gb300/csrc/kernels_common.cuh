@@ -12,12 +12,25 @@ namespace fem {
 // Elements per block for a slab of q x q threads per element: enough
 // threads to keep several warps per block, bounded by the shared-memory
 // budget (bytes per element given).
-__host__ __device__ constexpr int pick_epb(int q, int smem_per_elem) {
-    int t = 256 / (q * q);
+__host__ __device__ constexpr int pick_epb(int q, int smem_per_elem, int target = 256) {
+    int t = target / (q * q);
     if (t < 1) t = 1;
     while (t > 1 && t * smem_per_elem > 96 * 1024) t--;
     return t;
 }
+
+#ifndef FEM_EXP_T_BP1
+#define FEM_EXP_T_BP1 256
+#endif
+#ifndef FEM_EXP_T_BP35
+#define FEM_EXP_T_BP35 256
+#endif
+#ifndef FEM_EXP_T_BP30
+#define FEM_EXP_T_BP30 256
+#endif
+#ifndef FEM_EXP_T_GEO
+#define FEM_EXP_T_GEO 256
+#endif
 
 // Rounds a count of doubles up to a multiple of 2 (16-byte alignment).
 __host__ __device__ constexpr int pad2(int x) { return (x + 1) & ~1; }
@@ -76,6 +89,38 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
             smem_u32(dst)),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
+}
+
+// Copies the byte range [src, src + bytes) of an array that ends at
+// arr_end into shared memory at dst (16-byte aligned, with room for
+// bytes + 32), for ranges that need not be 16-byte aligned: one TMA bulk
+// copy of the enclosing 16-byte-aligned range, clipped to the last 16-byte
+// boundary inside the array, and plain loads for the few bytes past that
+// boundary.  The range's first byte lands at dst + (src & 15); the caller
+// (one thread) adds the returned TMA byte count to the mbarrier's expected
+// transaction count before this call's copy can complete -- so the expect
+// is issued first, by the caller, with the total of all its copies.
+struct RangeCopy {
+    unsigned tma_bytes;  // bytes moved by the bulk copy (0: none)
+    unsigned offset;     // where the range starts in dst
+};
+__device__ __forceinline__ RangeCopy range_copy_plan(const void *src, unsigned long long bytes, const void *arr_end) {
+    const unsigned long long s = (unsigned long long)src, e = s + bytes, ae = (unsigned long long)arr_end;
+    const unsigned long long a0 = s & ~15ull, a1 = (e + 15) & ~15ull, lim = ae & ~15ull;
+    const unsigned long long t1 = a1 <= ae ? a1 : lim;
+    RangeCopy r;
+    r.tma_bytes = t1 > a0 ? (unsigned)(t1 - a0) : 0u;
+    r.offset = (unsigned)(s - a0);
+    return r;
+}
+__device__ __forceinline__ void range_copy_issue(unsigned char *dst, const void *src, unsigned long long bytes,
+                                                 const RangeCopy &r, uint64_t *bar) {
+    const unsigned long long s = (unsigned long long)src, a0 = s & ~15ull;
+    if (r.tma_bytes) bulk_g2s(dst, (const void *)a0, r.tma_bytes, bar);
+    // bytes past the bulk copy (only at the very end of the array): plain loads
+    const unsigned long long done = a0 + r.tma_bytes, e = s + bytes;
+    for (unsigned long long b = done; b < e; b++)
+        dst[b - a0] = *(const unsigned char *)b;
 }
 
 // Bounded wait for the completion of phase `parity` of bar: at most

@@ -82,6 +82,35 @@ def test_bp30_f32_matches_fp64_operator(N):
     assert _rel(got, ref) < 2e-6 * (N + 2)
 
 
+@pytest.mark.parametrize("op,N", [("bp35", 7), ("bp35", 5), ("bp35", 4), ("bp35", 8), ("bp30", 7), ("bp30", 4),
+                                  ("bp30", 9)])
+def test_stream_kernels_many_groups_per_block(op, N):
+    """The FP32 and FP16-factor operators on 1001 elements: for BP3.5 the TMA
+    stream kernel with several element groups per persistent block (stages
+    reused), and at even N element ranges off 16-byte boundaries (range
+    copies, with the plain-load tail at the end of the arrays); for BP3.0 the
+    block kernels.  Against the oracle on the same rounded inputs."""
+    fem, torch = _fem(), _torch()
+    v = fem_synth.box_mesh(11, 10, 10)[:1001]
+    E = v.shape[0]
+    kind = oracle.KIND_BP35 if op == "bp35" else oracle.KIND_BP30
+    G, _ = oracle.geofacs(N, kind, v)
+    q32 = fem_synth.field(9, E, (N + 1) ** 3).astype(np.float32)
+    b = fem.fem_basis_setup(N)
+    apply = oracle.bp35 if op == "bp35" else oracle.bp30
+    ref32 = apply(N, G.astype(np.float32).astype(np.float64), 1.0, q32.astype(np.float64))
+    f32 = fem.fem_bp35_apply_f32 if op == "bp35" else fem.fem_bp30_apply_f32
+    got = f32(b, _dev(G.astype(np.float32)), 1.0, _dev(q32)).cpu().numpy().astype(np.float64)
+    assert _rel(got, ref32) < 2e-6 * (N + 2)
+    G16, ginv = _f16_factors(G)
+    ref16 = apply(N, G16.astype(np.float64) * ginv, 1.0, q32.astype(np.float64))
+    f16 = fem.fem_bp35_apply_f16g if op == "bp35" else fem.fem_bp30_apply_f16g
+    gi = torch.tensor([ginv], dtype=torch.float64, device="cuda")
+    got = f16(b, torch.from_numpy(G16).to("cuda"), gi, 1.0, _dev(q32)).cpu().numpy().astype(np.float64)
+    assert _rel(got, ref16) < 2e-6 * (N + 2)
+    assert fem.fem_wait_timeouts() == 0
+
+
 def test_staged_f32_operator_ragged_blocks_and_no_wait_timeouts():
     """The FP32 BP3.5 kernel that stages the factors with TMA bulk copies
     (odd degrees): an element count that leaves the last block partly
