@@ -43,8 +43,8 @@ KERNELS = ["geofacs_bp35", "geofacs_bp30_bp1", "bp1", "bp35", "bp30"]
 # element at N = 7, with the sha256 of the kernel source it was taken from;
 # a kernel whose source changed since reports traffic null.
 NCU_TRAFFIC = {
-    # profiles/fp64_operators_N7_E4096.md: (184.07 + 10.55) MB over 4096 elements
-    "bp30": {"N": 7, "bytes_per_elem": 47516, "sha": "4767b770f5592311",
+    # profiles/fp64_operators_N7_E4096.md: (184.08 + 7.90) MB over 4096 elements
+    "bp30": {"N": 7, "bytes_per_elem": 46868, "sha": "61d567f0ec15ef77",
              "files": ["bp30.cu", "bp30_body.cuh", "eo.cuh", "kernels_common.cuh"]},
 }
 
@@ -493,6 +493,17 @@ def run_ours(args):
     tr = NCU_TRAFFIC.get(dom)
     traffic = tr["bytes_per_elem"] * E if tr and tr["sha"] == _src_hash(tr["files"]) and tr["N"] == N else None
     peak_alu = fp64_peak_tflops(2070.0)
+    # the FP64 ceiling measured on this GPU: independent FMA chains on every SM
+    probe_out, probe_flops = fem.fem_fma_probe(10000)
+    fem.fem_fma_probe(10000, out=probe_out)
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pe0.record(stream)
+    for _ in range(3):
+        fem.fem_fma_probe(10000, out=probe_out)
+    pe1.record(stream)
+    torch.cuda.synchronize()
+    probe_tflops = 3 * probe_flops / (pe0.elapsed_time(pe1) / 1e3) / 1e12
+    del probe_out
     roofline = {
         "kernel": dom, "bound": "alu", "unit": "TFLOP/s",
         "achieved": kern[dom]["fp64_tflops"], "peak": peak_alu,
@@ -501,6 +512,9 @@ def run_ours(args):
         "flop_count": "direct sum factorisation (multiply-add = 2); the even-odd folded kernels execute "
                       "about 0.65x of these at N=7, so frac can exceed 1",
         "fp64_issue_frac": kern[dom]["fp64_issue_frac"],
+        "fp64_probe_tflops": probe_tflops,
+        "fp64_probe": "measured FP64 FMA rate of this GPU (fem_fma_probe: 8 independent FMA chains per thread, "
+                      "8 x 256 threads per SM)",
         "traffic": traffic,
         "hbm": {"achieved_gbs": kern[dom]["alg_gbs"], "peak_gbs": hbm, "peak_source": hbm_src,
                 "frac": kern[dom]["hbm_frac"]},

@@ -155,6 +155,15 @@ int fem_bp30_apply(const fem_basis *b, int64_t E, const double *G, double lambda
 int fem_bp35_apply_f32(const fem_basis *b, int64_t E, const float *G, double lambda,
                        const float *q, float *Aq, void *stream);
 
+/* FP64 issue-rate probe (the FP64 ceiling of the operators is measured, not
+ * assumed): fem_fma_probe_threads() threads (8 blocks of 256 per SM of the
+ * current device) each run eight independent FP64 FMA chains of iters steps
+ * and store one double to out (device, fem_fma_probe_threads() doubles).
+ * One launch performs 2 * 8 * iters * threads flops; time it on stream.
+ * Errors: FEM_EINVAL, FEM_ECUDA. */
+int64_t fem_fma_probe_threads(void);
+int fem_fma_probe(int64_t iters, double *out, void *stream);
+
 /* Number of bounded device-side waits that gave up on the current device
  * since the library was loaded or last reset (reset != 0 clears it).  The
  * kernels that stage data with TMA bulk copies wait on mbarriers with an

@@ -20,7 +20,7 @@ __all__ = [
     "FemError", "lib", "Basis", "fem_version", "fem_basis_setup", "fem_basis_free",
     "fem_basis_tables", "fem_basis_host_tables", "fem_mesh_geofacs", "fem_bp1_apply",
     "fem_bp35_apply", "fem_bp30_apply", "FEM_GEO_BP1", "FEM_GEO_BP35", "FEM_GEO_BP30",
-    "geo_shape", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_bp30_apply_layout",
+    "geo_shape", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_bp30_apply_layout", "fem_fma_probe",
     "FEM_LAYOUT_LINES", "FEM_LAYOUT_POINTS", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot", "fem_dot_scratch_size", "Pcg",
     "fem_pcg_create", "fem_pcg_solve", "fem_pcg_destroy", "FEM_PCG_FP64", "FEM_PCG_MIXED", "FEM_PCG_MIXED16", "fem_bp35_apply_f16g", "fem_bp30_apply_f16g",
     "Batch", "fem_batch_create", "FEM_OP_BP35", "FEM_OP_BP30", "Server",
@@ -118,6 +118,8 @@ def lib():
             L.fem_stream_sum.argtypes = [i32, i64, dp, dp, i32, vp]
             L.fem_mesh_geofacs_set.argtypes = [vp, i64, dp, dp, dp, dp, vp]
             L.fem_wait_timeouts.argtypes = [C.POINTER(C.c_ulonglong), i32]
+            L.fem_fma_probe_threads.restype = i64
+            L.fem_fma_probe.argtypes = [i64, dp, vp]
             L.fem_bp30_apply_layout.argtypes = [vp, i64, dp, dbl, dp, dp, i32, vp]
             L.fem_bp35_apply_f16g.argtypes = [vp, i64, dp, dp, dbl, dp, dp, vp]
             L.fem_bp30_apply_f16g.argtypes = [vp, i64, dp, dp, dbl, dp, dp, vp]
@@ -158,7 +160,7 @@ def lib():
             L.fem_pcg_destroy.restype = None
             for f in ("fem_basis_setup", "fem_basis_tables", "fem_basis_host_tables",
                       "fem_mesh_geofacs", "fem_bp1_apply", "fem_bp35_apply", "fem_bp30_apply",
-                      "fem_basis_degree", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_bp30_apply_layout",
+                      "fem_basis_degree", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_bp30_apply_layout", "fem_fma_probe",
                       "fem_bp35_apply_f16g", "fem_bp30_apply_f16g", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot",
                       "fem_pcg_create", "fem_pcg_solve"):
                 getattr(L, f).restype = i32
@@ -390,6 +392,17 @@ def fem_bp35_apply_f32(b: Basis, G, lam: float, q, out=None, stream=None):
     _check(lib().fem_bp35_apply_f32(b.handle, E, G.data_ptr(), float(lam), q.data_ptr(), out.data_ptr(),
                                     _stream(stream, q.device)), "fem_bp35_apply_f32")
     return out
+
+
+def fem_fma_probe(iters: int, out=None, stream=None):
+    """One launch of the FP64 issue-rate probe; returns (out, flops)."""
+    import torch
+    nt = int(lib().fem_fma_probe_threads())
+    if out is None:
+        out = torch.empty(nt, dtype=torch.float64, device="cuda")
+    _dev(out, "out", nt)
+    _check(lib().fem_fma_probe(int(iters), out.data_ptr(), _stream(stream, out.device)), "fem_fma_probe")
+    return out, 2 * 8 * int(iters) * nt
 
 
 def fem_wait_timeouts(reset: bool = False) -> int:

@@ -239,6 +239,14 @@ int fem_wait_timeouts(unsigned long long *count, int reset) {
     return e == cudaSuccess ? FEM_OK : cuda_fail(e);
 }
 
+int64_t fem_fma_probe_threads(void) { return fem::fma_probe_threads(); }
+
+int fem_fma_probe(int64_t iters, double *out, void *stream) {
+    if (iters < 1 || !out || !aligned16(out)) return FEM_EINVAL;
+    cudaError_t e = fem::launch_fma_probe(iters, out, (cudaStream_t)stream);
+    return e == cudaSuccess ? FEM_OK : cuda_fail(e);
+}
+
 int fem_stream_sum(int planes, int64_t n, const void *src, void *dst, int word, void *stream) {
     if (planes < 1 || planes > fem::stream_max_planes() || n < 0 || (word != 4 && word != 8)) return FEM_EINVAL;
     if (n == 0) return FEM_OK;

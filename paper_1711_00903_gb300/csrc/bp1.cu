@@ -30,14 +30,14 @@ struct Bp1Cfg {
     static constexpr int SA = (B0::size > B2::size) ? B0::size : B2::size;
     static constexpr int SB = B1::size;
     static constexpr int per = SA + SB;
-    static constexpr int EPB = pick_epb(m, per * 8, FEM_EXP_T_BP1);
+    static constexpr int EPB = pick_epb(m, per * 8);
     static constexpr int threads = ((m * m * EPB + 31) / 32) * 32;
     static constexpr int smem = EPB * per * 8;
     static constexpr int oI = fold_offset(N, kFoldI), oIT = fold_offset(N, kFoldIT);
     // three resident blocks per SM let one block's barriers overlap the
     // others' FP64 work; the register cap this implies costs a few spills
     // at high degree but was measured faster at every degree
-    static constexpr int min_blocks = FEM_EXP_T_BP1 <= 128 ? 6 : (FEM_EXP_T_BP1 >= 512 ? 1 : 3);
+    static constexpr int min_blocks = 3;
 };
 
 template <int N>

@@ -35,7 +35,7 @@ struct Bp30Layout {
 // Elements per block of the stand-alone kernel: as many as fit 256 threads
 // under the shared-memory budget.
 template <int N, typename T = double>
-struct Bp30Cfg : Bp30Layout<N, pick_epb(N + 2, 3 * Box<N + 2, N + 2, N + 2>::size * (int)sizeof(T), sizeof(T) == 8 ? FEM_EXP_T_BP30 : 256), T> {};
+struct Bp30Cfg : Bp30Layout<N, pick_epb(N + 2, 3 * Box<N + 2, N + 2, N + 2>::size * (int)sizeof(T)), T> {};
 
 // BP3.0 of elements [e0, e0 + nel) (nel <= EPB) by the whole block
 // (blockDim.x >= Layout::threads), shared memory at smem (Layout::smem

@@ -22,7 +22,8 @@ struct GeoCfg {
     static constexpr int QP = qn * qn * qn, qq = qn * qn;
     static constexpr int SD = (qq > 36) ? qq : 36;  // per-thread minima, or the 36 map coefficients
     static constexpr int smem_elem = (24 + 9 * qq + SD) * 8;
-    static constexpr int EPB = pick_epb(qn, smem_elem, FEM_EXP_T_GEO);
+    // about 512 threads per block (measured faster than 256 and 128 at N = 7)
+    static constexpr int EPB = pick_epb(qn, smem_elem, 512);
     static constexpr int threads = qq * EPB;
     static constexpr int smem = (2 * pad2(qn) + EPB * pad2(24 + 9 * qq + SD)) * 8;
 };
@@ -184,10 +185,10 @@ __device__ __forceinline__ void geofacs_body(int64_t E, const double *__restrict
     }
 }
 
-// Five resident blocks per SM (a register cap of about 48) was measured
-// faster than the compiler's own choice (58 registers, four blocks) up to
-// 10 points per direction; above that the cap would spill.
-constexpr int geo_min_blocks(int qn) { return qn <= 10 ? (FEM_EXP_T_GEO <= 128 ? 10 : (FEM_EXP_T_GEO >= 512 ? 2 : 5)) : 0; }
+// Two resident blocks of about 512 threads per SM (a register cap of 64)
+// up to 10 points per direction, measured faster than the compiler's own
+// choice; above that the cap would spill.
+constexpr int geo_min_blocks(int qn) { return qn <= 10 ? 2 : 0; }
 
 template <int qn, int kind, bool MIN>
 __global__ void __launch_bounds__(GeoCfg<qn>::threads)

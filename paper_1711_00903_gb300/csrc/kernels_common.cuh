@@ -9,28 +9,15 @@
 
 namespace fem {
 
-// Elements per block for a slab of q x q threads per element: enough
-// threads to keep several warps per block, bounded by the shared-memory
-// budget (bytes per element given).
+// Elements per block for a slab of q x q threads per element: about
+// `target` threads per block, bounded by the shared-memory budget (bytes per
+// element given).
 __host__ __device__ constexpr int pick_epb(int q, int smem_per_elem, int target = 256) {
     int t = target / (q * q);
     if (t < 1) t = 1;
     while (t > 1 && t * smem_per_elem > 96 * 1024) t--;
     return t;
 }
-
-#ifndef FEM_EXP_T_BP1
-#define FEM_EXP_T_BP1 256
-#endif
-#ifndef FEM_EXP_T_BP35
-#define FEM_EXP_T_BP35 256
-#endif
-#ifndef FEM_EXP_T_BP30
-#define FEM_EXP_T_BP30 256
-#endif
-#ifndef FEM_EXP_T_GEO
-#define FEM_EXP_T_GEO 256
-#endif
 
 // Rounds a count of doubles up to a multiple of 2 (16-byte alignment).
 __host__ __device__ constexpr int pad2(int x) { return (x + 1) & ~1; }

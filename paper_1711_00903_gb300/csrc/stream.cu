@@ -67,4 +67,37 @@ cudaError_t launch_stream_sum(int planes, int64_t n, const void *src, void *dst,
 
 int stream_max_planes() { return kMaxPlanes; }
 
+// FP64 issue-rate probe: every thread runs eight independent FMA chains of
+// `iters` steps (x <- x * b + c), so the FP64 pipe, not latency, sets the
+// rate; one value per thread is stored so that nothing is optimised away.
+// Flops = 2 * 8 * iters * threads.
+namespace {
+__global__ void __launch_bounds__(256) fma_probe_kernel(int64_t iters, double b, double c, double *__restrict__ out) {
+    double x[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) x[i] = (double)(threadIdx.x + i) * 1e-3;
+    for (int64_t k = 0; k < iters; k++) {
+#pragma unroll
+        for (int i = 0; i < 8; i++) x[i] = fma(x[i], b, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) s += x[i];
+    out[blockIdx.x * (int64_t)blockDim.x + threadIdx.x] = s;
+}
+}  // namespace
+
+int64_t fma_probe_threads() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return (int64_t)(sms > 0 ? sms : 1) * 8 * 256;
+}
+
+cudaError_t launch_fma_probe(int64_t iters, double *out, cudaStream_t s) {
+    const int64_t threads = fma_probe_threads();
+    fma_probe_kernel<<<(unsigned)(threads / 256), 256, 0, s>>>(iters, 0.999999, 1e-6, out);
+    return cudaGetLastError();
+}
+
 }  // namespace fem

@@ -329,3 +329,21 @@ def test_geofacs_set_equals_single_kind_calls(N):
     assert torch.equal(g3, ref[2])
     wJo, _ = oracle.geofacs(N, oracle.KIND_BP1, v)
     assert _rel(outs[0].cpu().numpy(), wJo) < 1e-13
+
+
+def test_fma_probe_runs_and_is_deterministic():
+    """The FP64 issue-rate probe: one double per thread, the same bits on a
+    second launch, and the closed form of the chain x <- x b + c for the
+    first chain of thread 0 of block 0."""
+    import torch
+    fem = _fem()
+    out, flops = fem.fem_fma_probe(50)
+    a = out.clone()
+    fem.fem_fma_probe(50, out=out)
+    torch.cuda.synchronize()
+    assert torch.equal(a, out) and flops == 2 * 8 * 50 * out.numel()
+    b, c = 0.999999, 1e-6
+    xs = [i * 1e-3 for i in range(8)]
+    for _ in range(50):
+        xs = [x * b + c for x in xs]
+    assert abs(out[0].item() - sum(xs)) <= 1e-12
