@@ -513,6 +513,10 @@ def run_ours(args):
                       "about 0.65x of these at N=7, so frac can exceed 1",
         "fp64_issue_frac": kern[dom]["fp64_issue_frac"],
         "fp64_probe_tflops": probe_tflops,
+        # FP64 instructions per second of the kernel over those of the probe
+        # (2 flops per probe instruction): the fraction of the FP64 rate this
+        # GPU sustains
+        "fp64_issue_frac_of_probe": kern[dom]["fp64_issue_frac"] * fp64_peak_ginst(sm_mhz) / (probe_tflops * 1e3 / 2),
         "fp64_probe": "measured FP64 FMA rate of this GPU (fem_fma_probe: 8 independent FMA chains per thread, "
                       "8 x 256 threads per SM)",
         "traffic": traffic,
