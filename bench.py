@@ -818,9 +818,9 @@ def run_batch(fem, torch, device, args):
 def run_serve(fem, torch, args):
     """Poisson arrivals (mean 200 requests/s) of Helmholtz PCG solves, BP3.0
     or BP3.5 at random, N uniform in 3..9, E log-uniform in 512..32768, rhs
-    uniform in [-1, 1], tolerance 1e-8, FP64 or mixed precision at random,
-    120 GiB HBM budget; continuous batching with 8 slots against one request
-    at a time (first come, first served)."""
+    uniform in [-1, 1], tolerance 1e-8, FP64 or mixed precision (FP16
+    factors) at random, 120 GiB HBM budget; continuous batching with 8 slots
+    against one request at a time (first come, first served)."""
     reqs = fem_synth.serve_workload(args.serve_requests)
     data = []
     for r in reqs:
@@ -836,7 +836,7 @@ def run_serve(fem, torch, args):
             now = srv.clock() - t0
             while k < len(data) and data[k][0]["t"] <= now:
                 r, v, rhs = data[k]
-                mode = fem.FEM_PCG_MIXED if r["mixed"] else fem.FEM_PCG_FP64
+                mode = fem.FEM_PCG_MIXED16 if r["mixed"] else fem.FEM_PCG_FP64
                 rid, x = srv.submit(r["op"], r["N"], v, rhs, lam=1.0, mode=mode, tol=1e-8)
                 ids.append((rid, r, x))
                 k += 1
@@ -863,7 +863,7 @@ def run_serve(fem, torch, args):
     fifo, xs_fifo = play(1)
     same = all(np.array_equal(a, b) for a, b in zip(xs_cb, xs_fifo))
     return {"workload": f"{len(data)} requests, Poisson arrivals at 200/s, BP3.0|BP3.5, N 3..9, E 512..32768 "
-                        "log-uniform, rhs U[-1,1], tol 1e-8, FP64|mixed, 120 GiB budget",
+                        "log-uniform, rhs U[-1,1], tol 1e-8, FP64|mixed (FP16 factors), 120 GiB budget",
             "continuous_batching_8_slots": cb, "one_at_a_time": fifo,
             "results_identical_alone_and_in_mix": same}
 
