@@ -47,7 +47,6 @@ enum {
 constexpr int kVecBlocks = 152 * 8;  // grid of the vector kernels (grid-stride)
 constexpr int kVecThreads = 256;
 constexpr int kRedThreads = 1024;
-constexpr int64_t kFusedPqMax = 2048;  // matvec partials the update kernel may reduce itself
 
 namespace {
 
@@ -267,26 +266,6 @@ outer_kernel(int64_t n, const double *__restrict__ b, const double *__restrict__
     }
 }
 
-// The step from p . Ap to alpha (Algorithm 9.1 of Saad): alpha = rho / pq
-// unless the recurrence is done or broken; pq <= 0 or a non-finite pq marks
-// a breakdown.  `write`: record pq, alpha and the breakdown flag.
-__device__ __forceinline__ double pq_step(double *__restrict__ scal, double pq, bool write) {
-    double alpha = 0.0;
-    bool brk = false;
-    if (scal[S_DONE] == 0.0 && scal[S_BREAK] == 0.0) {
-        if (pq > 0.0 && isfinite(pq))
-            alpha = scal[S_RHO] / pq;
-        else
-            brk = true;
-    }
-    if (write) {
-        scal[S_PQ] = pq;
-        if (brk) scal[S_BREAK] = 1.0;
-        scal[S_ALPHA] = alpha;
-    }
-    return alpha;
-}
-
 // x += alpha p, r -= alpha Ap, z = dinv r; partials (r.z, r.r).  The
 // arithmetic is in the recurrence's own precision T (in FP32 the per-thread
 // partial sums too, so the FP32 inner solver issues no FP64 instruction per
@@ -323,29 +302,12 @@ update_kernel(int64_t n, const double *__restrict__ scal, XT *__restrict__ x, co
 
 // The FP32 update with 16-byte vector accesses (n a multiple of 4, every
 // array 16-byte aligned): four entries per thread and iteration.
-// FUSED_PQ: the block first forms p . Ap from the matvec's npq partial sums
-// itself (every block in the same order, so every block gets the same bits)
-// and alpha from it, which removes the separate reduction launch; block 0
-// records the scalars.
-template <bool FUSED_PQ>
 __global__ void __launch_bounds__(kVecThreads)
-update_f32x4_kernel(int64_t n4, double *__restrict__ scal, float4 *__restrict__ x, const float4 *__restrict__ p,
+update_f32x4_kernel(int64_t n4, const double *__restrict__ scal, float4 *__restrict__ x, const float4 *__restrict__ p,
                     float4 *__restrict__ r, const float4 *__restrict__ Ap, float4 *__restrict__ z,
-                    const float4 *__restrict__ dinv, double *__restrict__ part, const double *__restrict__ part_pq,
-                    int64_t npq) {
+                    const float4 *__restrict__ dinv, double *__restrict__ part) {
     __shared__ double sh[32];
-    __shared__ double s_alpha;
-    double alpha;
-    if (FUSED_PQ) {
-        double acc = 0.0;
-        for (int64_t i = threadIdx.x; i < npq; i += blockDim.x) acc += part_pq[i];
-        const double pq = block_sum(acc, sh);
-        if (threadIdx.x == 0) s_alpha = pq_step(scal, pq, blockIdx.x == 0);
-        __syncthreads();
-        alpha = s_alpha;
-    } else {
-        alpha = scal[S_ALPHA];
-    }
+    const double alpha = scal[S_ALPHA];
     const float a = (float)alpha;
     float rz = 0.0f, rr = 0.0f;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
@@ -403,7 +365,16 @@ reduce_kernel(int mode, int64_t nparts, const double *__restrict__ part, double 
     } else if (mode == R_TRUE) {  // residual norm of a finished solve
         scal[S_RR] = tot[1];
     } else if (mode == R_PQ) {
-        pq_step(scal, tot[0], true);
+        const double pq = tot[0];
+        scal[S_PQ] = pq;
+        double alpha = 0.0;
+        if (scal[S_DONE] == 0.0 && scal[S_BREAK] == 0.0) {
+            if (pq > 0.0 && isfinite(pq))
+                alpha = scal[S_RHO] / pq;
+            else
+                scal[S_BREAK] = 1.0;
+        }
+        scal[S_ALPHA] = alpha;
     } else if (mode == R_RZ) {
         const bool active = scal[S_DONE] == 0.0 && scal[S_BREAK] == 0.0;
         const double rz = tot[0], rr = tot[1];
@@ -539,21 +510,20 @@ int64_t op_blocks(const fem_pcg *s, bool f32) {
     if (f32 && s->mode == FEM_PCG_MIXED16 && s->op == FEM_OP_BP35) return bp35_f16_blocks(s->basis->host.N, s->E);
     return s->op == FEM_OP_BP30 ? bp30_blocks(s->basis->host.N, s->E, f32) : bp35_blocks(s->basis->host.N, s->E, f32);
 }
-cudaError_t op_pcg(fem_pcg *s, const double *G, const double *z, double *p, double *Ap, double *part,
-                   cudaStream_t st) {
+cudaError_t op_pcg(fem_pcg *s, const double *G, const double *z, double *p, double *Ap, cudaStream_t st) {
     return s->op == FEM_OP_BP30
-               ? launch_bp30_pcg(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, part, st)
-               : launch_bp35_pcg(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, part, st);
+               ? launch_bp30_pcg(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, s->part, st)
+               : launch_bp35_pcg(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, s->part, st);
 }
-cudaError_t op_pcg(fem_pcg *s, const float *G, const float *z, float *p, float *Ap, double *part, cudaStream_t st) {
+cudaError_t op_pcg(fem_pcg *s, const float *G, const float *z, float *p, float *Ap, cudaStream_t st) {
     if (s->mode == FEM_PCG_MIXED16)
         return s->op == FEM_OP_BP30 ? launch_bp30_pcg_f16g(s->basis, s->E, s->G16, s->scal + S_GINV, s->lambda, z, p,
-                                                           s->scal + S_BETA, Ap, part, st)
+                                                           s->scal + S_BETA, Ap, s->part, st)
                                     : launch_bp35_pcg_f16g(s->basis, s->E, s->G16, s->scal + S_GINV, s->lambda, z, p,
-                                                           s->scal + S_BETA, Ap, part, st);
+                                                           s->scal + S_BETA, Ap, s->part, st);
     return s->op == FEM_OP_BP30
-               ? launch_bp30_pcg_f32(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, part, st)
-               : launch_bp35_pcg_f32(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, part, st);
+               ? launch_bp30_pcg_f32(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, s->part, st)
+               : launch_bp35_pcg_f32(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, s->part, st);
 }
 
 template <typename P>
@@ -574,26 +544,15 @@ template <typename T, typename XT>
 cudaError_t enqueue_iterations(fem_pcg *s, const T *G, XT *x, T *p, T *r, T *Ap, T *z, const T *dinv, int chunk) {
     cudaError_t e = cudaSuccess;
     const int64_t len = s->len;
-    const int64_t npq = op_blocks(s, sizeof(T) == 4);
-    const bool vec4 = sizeof(T) == 4 && sizeof(XT) == 4 && len % 4 == 0;
-    // few matvec partials (the persistent stream kernels): every update
-    // block reduces them itself, and the matvec writes them past the update's
-    // own partials
-    const bool fused = vec4 && npq <= kFusedPqMax;
-    double *part_pq = fused ? s->part + 3 * kVecBlocks : s->part;
     for (int c = 0; c < chunk && e == cudaSuccess; c++) {
-        e = op_pcg(s, G, z, p, Ap, part_pq, s->st);
+        e = op_pcg(s, G, z, p, Ap, s->st);
         if (e != cudaSuccess) break;
-        if (!fused)
-            reduce_kernel<<<1, kRedThreads, 0, s->st>>>(R_PQ, npq, s->part, s->scal, nullptr, 0.0);
-        if (fused)
-            update_f32x4_kernel<true><<<kVecBlocks, kVecThreads, 0, s->st>>>(
+        reduce_kernel<<<1, kRedThreads, 0, s->st>>>(R_PQ, op_blocks(s, sizeof(T) == 4), s->part, s->scal, nullptr,
+                                                    0.0);
+        if (sizeof(T) == 4 && sizeof(XT) == 4 && len % 4 == 0)
+            update_f32x4_kernel<<<kVecBlocks, kVecThreads, 0, s->st>>>(
                 len / 4, s->scal, (float4 *)x, (const float4 *)p, (float4 *)r, (const float4 *)Ap, (float4 *)z,
-                (const float4 *)dinv, s->part, part_pq, npq);
-        else if (vec4)
-            update_f32x4_kernel<false><<<kVecBlocks, kVecThreads, 0, s->st>>>(
-                len / 4, s->scal, (float4 *)x, (const float4 *)p, (float4 *)r, (const float4 *)Ap, (float4 *)z,
-                (const float4 *)dinv, s->part, nullptr, 0);
+                (const float4 *)dinv, s->part);
         else
             update_kernel<T, XT><<<kVecBlocks, kVecThreads, 0, s->st>>>(len, s->scal, x, p, r, Ap, z, dinv, s->part);
         reduce_kernel<<<1, kRedThreads, 0, s->st>>>(R_RZ, kVecBlocks, s->part, s->scal, nullptr, 0.0);
