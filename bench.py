@@ -636,13 +636,23 @@ def run_sweep(fem, torch, device, verts, args, sm_mhz):
         smem = smem_counts(N)
         row = {"N": N, "dofs": E * n ** 3}
         for name, kind in (("bp1", 1), ("bp35", 2), ("bp30", 3), ("bp30_points", 3), ("bp35_f32", 2),
-                           ("bp30_f32", 3)):
-            f32 = name.endswith("_f32")
+                           ("bp30_f32", 3), ("bp35_f16", 2), ("bp30_f16", 3)):
+            f16 = name.endswith("_f16")
+            f32 = name.endswith("_f32") or f16
             base = name[:-4] if f32 else name
             ratio_base = "bp30" if base == "bp30_points" else base
             geo = torch.empty(fem.geo_shape(b, kind, E), dtype=torch.float64, device=device)
             fem.fem_mesh_geofacs(b, kind, verts, geo=geo, stream=stream)
-            if f32:
+            if f16:
+                # binary16 factors scaled by 2^(14 - e), max|G| < 2^e, as the solver stores them
+                ex = int(np.frexp(geo.abs().max().item())[1])
+                gi = torch.tensor([2.0 ** (ex - 14)], dtype=torch.float64, device=device)
+                geo, qx = (geo * 2.0 ** (14 - ex)).half(), q.float()
+                o = torch.empty_like(qx)
+                fn = fem.fem_bp35_apply_f16g if base == "bp35" else fem.fem_bp30_apply_f16g
+                ms = timed(lambda: fn(b, geo, gi, lam, qx, out=o, stream=stream), reps)
+                del qx, o, gi
+            elif f32:
                 geo, qx = geo.float(), q.float()
                 o = torch.empty_like(qx)
                 fn = fem.fem_bp35_apply_f32 if base == "bp35" else fem.fem_bp30_apply_f32
@@ -660,6 +670,8 @@ def run_sweep(fem, torch, device, verts, args, sm_mhz):
             del geo
             word = 4 if f32 else 8
             per_elem = byts[base] * word // 8
+            if f16:  # the factor planes move in two bytes per value
+                per_elem = 4 * (2 * n ** 3) + 2 * 7 * (n ** 3 if base == "bp35" else (N + 2) ** 3)
             T = E * per_elem
             # recalibrated copy roofline at this byte count
             half = torch.empty(T // 2 // 8, dtype=torch.float64, device=device)
@@ -692,9 +704,9 @@ def run_sweep(fem, torch, device, verts, args, sm_mhz):
         b.free()
     del q_all
     torch.cuda.empty_cache()
-    return {"workload": f"BP1.0/BP3.5/BP3.0 FP64 (BP3.0 also in the point-per-thread layout; BP3.5/BP3.0 FP32, "
-                        f"the mixed solver's inner operators) sweep, E={E} jittered hexes, lambda=1, mean of "
-                        f"{reps} launches per point",
+    return {"workload": f"BP1.0/BP3.5/BP3.0 FP64 (BP3.0 also in the point-per-thread layout; BP3.5/BP3.0 FP32 "
+                        f"with FP32 and FP16 factors, the mixed solvers' inner operators) sweep, E={E} jittered "
+                        f"hexes, lambda=1, mean of {reps} launches per point",
             "copy_roofline": "device-to-device copy of T/2 bytes moving T = the operator's algorithmic "
                              "bytes, recalibrated at every N (Section 5 of the paper)",
             "rows": rows}

@@ -111,14 +111,14 @@ def test_stream_kernels_many_groups_per_block(op, N):
     assert fem.fem_wait_timeouts() == 0
 
 
-def test_staged_f32_operator_ragged_blocks_and_no_wait_timeouts():
+def test_stream_f32_operator_ragged_groups_and_no_wait_timeouts():
     """The FP32 BP3.5 kernel that stages the factors with TMA bulk copies
-    (odd degrees): an element count that leaves the last block partly
-    filled, results equal to the oracle's on the same FP32 inputs, and no
-    bounded wait gave up."""
+    (N <= 9; N = 11 takes the block kernel): a single element, element
+    counts that leave the last group partly filled, results equal to the
+    oracle's on the same FP32 inputs, and no bounded wait gave up."""
     fem, torch = _fem(), _torch()
     fem.fem_wait_timeouts(reset=True)
-    for N, E in ((7, 1), (7, 37), (3, 33), (11, 3)):
+    for N, E in ((7, 1), (7, 37), (3, 33), (4, 7), (8, 5), (11, 3)):
         v = fem_synth.box_mesh(4)[:E]
         G, _ = oracle.geofacs(N, oracle.KIND_BP35, v)
         q = fem_synth.field(3, E, (N + 1) ** 3)
