@@ -29,11 +29,12 @@ struct Bp35Layout {
 
 // Elements per block of the stand-alone kernels: as many as fit 256 threads
 // under the shared-memory budget (512 for FP64 from N = 8 on, measured 9 %
-// faster at N = 9 and 11).
+// faster at N = 9 and 11; 128 for FP32 at N = 10, 6 % faster).
 template <typename T, int N>
 struct Bp35Cfg
     : Bp35Layout<T, N,
-                 pick_epb(N + 1, 3 * Box<N + 1, N + 1, N + 1>::size * (int)sizeof(T), (sizeof(T) == 8 && N >= 8) ? 512 : 256)> {
+                 pick_epb(N + 1, 3 * Box<N + 1, N + 1, N + 1>::size * (int)sizeof(T),
+                          sizeof(T) == 8 ? (N >= 8 ? 512 : 256) : (N == 10 ? 128 : 256))> {
 };
 
 // The operator on elements [e0, e0 + nel) (nel <= EPB) whose input field is
