@@ -173,6 +173,14 @@ int fem_fma_probe(int64_t iters, double *out, void *stream);
  * Errors: FEM_EINVAL (count NULL), FEM_ECUDA. */
 int fem_wait_timeouts(unsigned long long *count, int reset);
 
+/* Self-test of the bounded device waits: runs one block whose mbarrier
+ * wait can never complete (a barrier expecting an arrival that never comes)
+ * and reports in *gave_up how many warps gave up after the wait's limit
+ * (about a second): 2 when the limit works.  The context stays usable; this
+ * self-test's count is not added to fem_wait_timeouts.  Synchronous.
+ * Errors: FEM_EINVAL, FEM_ECUDA. */
+int fem_wait_selftest(unsigned long long *gave_up);
+
 /* Roofline calibration stream with a chosen read:write ratio (Section 5
  * calibrates the bandwidth roofline by a copy; the operators read several
  * planes per plane written): dst[i] = sum over p = 0..planes-1, in that

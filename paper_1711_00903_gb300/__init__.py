@@ -20,7 +20,7 @@ __all__ = [
     "FemError", "lib", "Basis", "fem_version", "fem_basis_setup", "fem_basis_free",
     "fem_basis_tables", "fem_basis_host_tables", "fem_mesh_geofacs", "fem_bp1_apply",
     "fem_bp35_apply", "fem_bp30_apply", "FEM_GEO_BP1", "FEM_GEO_BP35", "FEM_GEO_BP30",
-    "geo_shape", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_bp30_apply_layout", "fem_fma_probe",
+    "geo_shape", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_wait_selftest", "fem_bp30_apply_layout", "fem_fma_probe",
     "FEM_LAYOUT_LINES", "FEM_LAYOUT_POINTS", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot", "fem_dot_scratch_size", "Pcg",
     "fem_pcg_create", "fem_pcg_solve", "fem_pcg_destroy", "FEM_PCG_FP64", "FEM_PCG_MIXED", "FEM_PCG_MIXED16", "fem_bp35_apply_f16g", "fem_bp30_apply_f16g",
     "Batch", "fem_batch_create", "FEM_OP_BP35", "FEM_OP_BP30", "Server",
@@ -119,6 +119,7 @@ def lib():
             L.fem_mesh_geofacs_set.argtypes = [vp, i64, dp, dp, dp, dp, vp]
             L.fem_wait_timeouts.argtypes = [C.POINTER(C.c_ulonglong), i32]
             L.fem_fma_probe_threads.restype = i64
+            L.fem_wait_selftest.argtypes = [C.POINTER(C.c_ulonglong)]
             L.fem_fma_probe.argtypes = [i64, dp, vp]
             L.fem_bp30_apply_layout.argtypes = [vp, i64, dp, dbl, dp, dp, i32, vp]
             L.fem_bp35_apply_f16g.argtypes = [vp, i64, dp, dp, dbl, dp, dp, vp]
@@ -392,6 +393,14 @@ def fem_bp35_apply_f32(b: Basis, G, lam: float, q, out=None, stream=None):
     _check(lib().fem_bp35_apply_f32(b.handle, E, G.data_ptr(), float(lam), q.data_ptr(), out.data_ptr(),
                                     _stream(stream, q.device)), "fem_bp35_apply_f32")
     return out
+
+
+def fem_wait_selftest() -> int:
+    """Runs a kernel whose bounded wait cannot complete; returns how many
+    warps gave up (2 when the wait limit works)."""
+    c = C.c_ulonglong(0)
+    _check(lib().fem_wait_selftest(C.byref(c)), "fem_wait_selftest")
+    return int(c.value)
 
 
 def fem_fma_probe(iters: int, out=None, stream=None):

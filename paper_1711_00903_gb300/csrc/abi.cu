@@ -239,6 +239,12 @@ int fem_wait_timeouts(unsigned long long *count, int reset) {
     return e == cudaSuccess ? FEM_OK : cuda_fail(e);
 }
 
+int fem_wait_selftest(unsigned long long *gave_up) {
+    if (!gave_up) return FEM_EINVAL;
+    cudaError_t e = fem::run_wait_selftest(gave_up);
+    return e == cudaSuccess ? FEM_OK : cuda_fail(e);
+}
+
 int64_t fem_fma_probe_threads(void) { return fem::fma_probe_threads(); }
 
 int fem_fma_probe(int64_t iters, double *out, void *stream) {

@@ -111,6 +111,7 @@ cudaError_t wait_timeouts_bp35(unsigned long long *count, bool reset);
 cudaError_t launch_stream_sum(int planes, int64_t n, const void *src, void *dst, int word, cudaStream_t s);
 int stream_max_planes();
 int64_t fma_probe_threads();
+cudaError_t run_wait_selftest(unsigned long long *gave_up);
 cudaError_t launch_fma_probe(int64_t iters, double *out, cudaStream_t s);
 cudaError_t launch_bp35_f32(const fem_basis *b, int64_t E, const float *G, double lambda, const float *q,
                             float *Aq, cudaStream_t s);

@@ -87,6 +87,35 @@ __global__ void __launch_bounds__(256) fma_probe_kernel(int64_t iters, double b,
 }
 }  // namespace
 
+// Self-test of the bounded mbarrier wait: one block waits on a barrier
+// that expects two arrivals and gets one, so the phase never completes; every
+// wait must give up after its iteration limit and count itself, and the
+// kernel must return normally.
+namespace {
+__global__ void __launch_bounds__(64) wait_selftest_kernel() {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 2);
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&bar)) : "memory");
+    }
+    __syncthreads();
+    if (!mbar_wait(&bar, 0) && (threadIdx.x & 31) == 0) atomicAdd(&g_wait_timeouts, 1ull);
+}
+}  // namespace
+
+FEM_DEFINE_WAIT_COUNTER(wait_timeouts_selftest)
+
+cudaError_t run_wait_selftest(unsigned long long *gave_up) {
+    unsigned long long zero = 0;
+    cudaError_t e = wait_timeouts_selftest(&zero, true);
+    if (e != cudaSuccess) return e;
+    wait_selftest_kernel<<<1, 64>>>();
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = wait_timeouts_selftest(gave_up, true);
+    return e;
+}
+
 int64_t fma_probe_threads() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
