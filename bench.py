@@ -329,13 +329,22 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "E": 32768, "N": N, "lambda": lam, "sample_elements": Es},
+        "config": step_config(32768, N, lam, 1),
         "cpu_baseline": {"value": value, "unit": "GDOF/s", "cores": threads, "kind": "oracle",
                           "sample": sample},
         "e2e": {"value": value, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
+
+
+def step_config(E, N, lam, world):
+    """The workload description of the step, the same for both arms."""
+    return {"workload": WORKLOAD if E == 32768 else f"{WORKLOAD} [profiling size E={E}]",
+            "E": E, "N": N, "lambda": lam,
+            "mesh": "32^3 unit cube, interior vertices jittered U[-0.1h,0.1h], trilinear",
+            "l2": "inputs larger than L2 (no flush)",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
 
 
 def cpu_oracle_step(N, v, qq, lam):
@@ -552,11 +561,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if E == 32768 else f"{WORKLOAD} [profiling size E={E}]",
-                       "E": E, "N": N, "lambda": lam,
-                       "mesh": "32^3 unit cube, interior vertices jittered U[-0.1h,0.1h], trilinear",
-                       "l2": "inputs larger than L2 (no flush)",
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "config": step_config(E, N, lam, world),
             "e2e": {"value": world * dofs / (e2e_ms / 1e3) / 1e9, "unit": "GDOF/s",
                     "h2d_bytes_per_step": int(verts_h.nbytes + q_h.nbytes),
                     "d2h_bytes_per_step": int(3 * q_h.nbytes),
