@@ -347,3 +347,49 @@ def test_fma_probe_runs_and_is_deterministic():
     for _ in range(50):
         xs = [x * b + c for x in xs]
     assert abs(out[0].item() - sum(xs)) <= 1e-12
+
+
+@pytest.mark.parametrize("N", [1, 4, 9, 15])
+@pytest.mark.parametrize("E", [1, 7, 64])
+def test_affine_mesh_parity_from_vertices(bases, N, E):
+    """Undistorted (affine, axis-aligned) elements, from the vertices through
+    the factor-set call to the three operators, against the oracle at
+    several element counts."""
+    fem, torch = _fem(), _torch()
+    v = _mesh(E, jitter=0.0)
+    q = fem_synth.field(17, E, (N + 1) ** 3)
+    b = bases[N]
+    vd = _dev(v)
+    wJ = torch.empty(fem.geo_shape(b, 1, E), dtype=torch.float64, device="cuda")
+    G35 = torch.empty(fem.geo_shape(b, 2, E), dtype=torch.float64, device="cuda")
+    G30 = torch.empty(fem.geo_shape(b, 3, E), dtype=torch.float64, device="cuda")
+    fem.fem_mesh_geofacs_set(b, vd, wJ=wJ, G35=G35, G30=G30)
+    qd = _dev(q)
+    wJo, _ = oracle.geofacs(N, oracle.KIND_BP1, v)
+    G35o, _ = oracle.geofacs(N, oracle.KIND_BP35, v)
+    G30o, _ = oracle.geofacs(N, oracle.KIND_BP30, v)
+    assert _rel(fem.fem_bp1_apply(b, wJ, qd).cpu().numpy(), oracle.bp1(N, wJo, q)) < TOL
+    assert _rel(fem.fem_bp35_apply(b, G35, 1.0, qd).cpu().numpy(), oracle.bp35(N, G35o, 1.0, q)) < TOL
+    assert _rel(fem.fem_bp30_apply(b, G30, 1.0, qd).cpu().numpy(), oracle.bp30(N, G30o, 1.0, q)) < TOL
+
+
+@pytest.mark.parametrize("N", [3, 7])
+def test_512_element_mesh_all_operators(bases, N):
+    """The 8^3 mesh of the small configuration (512 jittered elements) for all
+    three operators, element by element against the oracle."""
+    fem, torch = _fem(), _torch()
+    v = fem_synth.box_mesh(8)
+    E = v.shape[0]
+    q = fem_synth.field(2, E, (N + 1) ** 3)
+    b = bases[N]
+    vd, qd = _dev(v), _dev(q)
+    for kind, apply_gpu, apply_o in ((oracle.KIND_BP1, lambda g: fem.fem_bp1_apply(b, g, qd),
+                                      lambda g: oracle.bp1(N, g, q)),
+                                     (oracle.KIND_BP35, lambda g: fem.fem_bp35_apply(b, g, 1.0, qd),
+                                      lambda g: oracle.bp35(N, g, 1.0, q)),
+                                     (oracle.KIND_BP30, lambda g: fem.fem_bp30_apply(b, g, 1.0, qd),
+                                      lambda g: oracle.bp30(N, g, 1.0, q))):
+        go, _ = oracle.geofacs(N, kind, v)
+        gd = fem.fem_mesh_geofacs(b, kind, vd)
+        assert _rel(gd.cpu().numpy(), go) < TOL
+        assert _rel(apply_gpu(gd).cpu().numpy(), apply_o(go)) < TOL
