@@ -73,6 +73,14 @@ struct F16Prepare30 {
     }
 };
 
+template <int N>
+struct F16Blocks30 {
+    static cudaError_t run(int64_t E, int64_t *out) {
+        *out = (E + Bp30Cfg<N, float>::EPB - 1) / Bp30Cfg<N, float>::EPB;
+        return cudaSuccess;
+    }
+};
+
 FEM_DEFINE_FOLD_UPLOAD(upload_fold_bp30_f16_tu)
 
 }  // namespace
@@ -88,6 +96,12 @@ cudaError_t launch_bp30_pcg_f16g(const fem_basis *b, int64_t E, const __half *G,
                                  cudaStream_t s) {
     return dispatch_degree<F16Launch30<true>::L>(b->host.N, E, G, ginv, lambda, (const float *)nullptr, Ap, z, p,
                                                  beta, partials, s);
+}
+
+int64_t bp30_f16_blocks(int N, int64_t E) {
+    int64_t out = 0;
+    dispatch_degree<F16Blocks30>(N, E, &out);
+    return out;
 }
 
 cudaError_t prepare_bp30_f16(int N, const double *fold_table) {

@@ -104,6 +104,7 @@ cudaError_t launch_bp30_pcg_f16g(const fem_basis *b, int64_t E, const __half *G,
 cudaError_t prepare_bp30_f16(int N, const double *fold_table);
 cudaError_t launch_bp30_pcg_f32(const fem_basis *b, int64_t E, const float *G, double lambda, const float *z,
                                 float *p, const double *beta, float *Ap, double *partials, cudaStream_t s);
+int64_t bp30_f16_blocks(int N, int64_t E);
 int64_t bp30_blocks(int N, int64_t E, bool f32);
 
 // FP32 BP3.5 matvec (the inner operator of the mixed-precision solver).

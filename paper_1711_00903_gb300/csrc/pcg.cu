@@ -507,7 +507,8 @@ cudaError_t op_apply64(fem_pcg *s, const double *x, double *out, cudaStream_t st
                                 : launch_bp35(s->basis, s->E, s->G, s->lambda, x, out, st);
 }
 int64_t op_blocks(const fem_pcg *s, bool f32) {
-    if (f32 && s->mode == FEM_PCG_MIXED16 && s->op == FEM_OP_BP35) return bp35_f16_blocks(s->basis->host.N, s->E);
+    if (f32 && s->mode == FEM_PCG_MIXED16)
+        return s->op == FEM_OP_BP30 ? bp30_f16_blocks(s->basis->host.N, s->E) : bp35_f16_blocks(s->basis->host.N, s->E);
     return s->op == FEM_OP_BP30 ? bp30_blocks(s->basis->host.N, s->E, f32) : bp35_blocks(s->basis->host.N, s->E, f32);
 }
 cudaError_t op_pcg(fem_pcg *s, const double *G, const double *z, double *p, double *Ap, cudaStream_t st) {
