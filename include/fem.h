@@ -334,8 +334,12 @@ int fem_pcg_create(const fem_basis *b, int op, int64_t E, const double *G, doubl
  * (host convergence checks every check_every iterations; all scalars of
  * the recurrence stay on the device).  The iterate is frozen on the device
  * at the first iteration that meets the tolerance, so the result does not
- * depend on check_every.  Returns FEM_OK, FEM_ENOCONV, FEM_EBREAKDOWN,
- * FEM_EINVAL or FEM_ECUDA. */
+ * depend on check_every.  FEM_OK means that the true FP64 residual of the
+ * returned x meets tol.  FP64 mode: when the recurrence's residual meets tol
+ * but the true one does not (rounding drift near FP64's attainable
+ * accuracy), the iteration restarts from the true residual, at most 8 times
+ * and only while each restart halves it; then FEM_ENOCONV.  Returns FEM_OK,
+ * FEM_ENOCONV, FEM_EBREAKDOWN, FEM_EINVAL or FEM_ECUDA. */
 int fem_pcg_solve(fem_pcg *s, const double *rhs, double *x, const fem_pcg_opts *opts,
                   fem_pcg_info *info, void *stream);
 

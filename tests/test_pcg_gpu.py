@@ -239,11 +239,9 @@ def test_pcg_edge_cases():
         assert np.all(np.isfinite(x.cpu().numpy()))
 
 
-def test_full_size_mixed_solve_config():
-    """N = 7 on the 32^3 mesh (E = 32768), manufactured right-hand side:
-    the mixed solve reaches the FP64 tolerance and the discrete solution."""
-    fem, torch = _fem(), _torch()
-    N = 7
+def _full_size_manufactured(fem, N):
+    """The 32^3 mesh (E = 32768) with its BP3.5 factors, u_I and b = A u_I,
+    on the device."""
     v = fem_synth.box_mesh(32)
     basis = fem.fem_basis_setup(N)
     vd = _dev(v)
@@ -262,6 +260,14 @@ def test_full_size_mixed_solve_config():
     u = np.sin(np.pi * Xall[..., 0]) * np.sin(np.pi * Xall[..., 1]) * np.sin(np.pi * Xall[..., 2])
     ud = _dev(u)
     bd = fem.fem_bp35_apply(basis, G, 1.0, ud)
+    return basis, G, ud, bd
+
+
+def test_full_size_mixed_solve_config():
+    """N = 7 on the 32^3 mesh (E = 32768), manufactured right-hand side:
+    the mixed solve reaches the FP64 tolerance and the discrete solution."""
+    fem, torch = _fem(), _torch()
+    basis, G, ud, bd = _full_size_manufactured(fem, 7)
     s = fem.fem_pcg_create(basis, G, 1.0, fem.FEM_PCG_MIXED)
     x, info, code = s.solve(bd, tol=1e-10)
     assert code == 0 and info["relres"] <= 1e-10
@@ -271,6 +277,35 @@ def test_full_size_mixed_solve_config():
     x64, info64, code64 = s64.solve(bd, tol=1e-10)
     assert code64 == 0
     assert (torch.linalg.norm(x - x64) / torch.linalg.norm(x64)).item() <= 1e-7
+
+
+def test_full_size_tight_tolerance():
+    """On the 32^3 mesh at N = 7 the FP64 recurrence's residual drifts below
+    the true one near 1e-12: FEM_OK still means a true residual within tol
+    (the solver restarts from the true residual), a tolerance below FP64's
+    reach ends in FEM_ENOCONV with a finite iterate, and at tol 1e-13 the
+    mixed solves agree with the FP64 solve, and with u_I, to 1e-10."""
+    fem, torch = _fem(), _torch()
+    basis, G, ud, bd = _full_size_manufactured(fem, 7)
+    rel = lambda a, b: (torch.linalg.norm(a - b) / torch.linalg.norm(b)).item()
+    s64 = fem.fem_pcg_create(basis, G, 1.0, fem.FEM_PCG_FP64)
+    x64, info, code = s64.solve(bd, tol=1e-12)
+    assert code == 0 and info["relres"] <= 1e-12
+    x64, info, code = s64.solve(bd, tol=1e-13, raise_on_error=False)
+    if code == 0:
+        assert info["relres"] <= 1e-13
+    else:
+        assert code == fem.FEM_ENOCONV and bool(torch.isfinite(x64).all())
+    assert info["relres"] <= 1e-11 and rel(x64, ud) <= 1e-10
+    x_ref = x64.clone()
+    x, info, code = s64.solve(bd, tol=1e-16, maxit=3000, raise_on_error=False)
+    assert code == fem.FEM_ENOCONV and bool(torch.isfinite(x).all()) and info["relres"] <= 1e-11
+    for mode in (fem.FEM_PCG_MIXED, fem.FEM_PCG_MIXED16):
+        s = fem.fem_pcg_create(basis, G, 1.0, mode)
+        x, info, code = s.solve(bd, tol=1e-13, inner_tol=1e-3)
+        assert code == 0 and info["relres"] <= 1e-13
+        assert rel(x, x_ref) <= 1e-10 and rel(x, ud) <= 1e-10
+        s.free()
 
 
 # ------------------------------------------------------------------ BP3.0
