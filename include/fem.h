@@ -225,6 +225,24 @@ int fem_bp30_apply_layout(const fem_basis *b, int64_t E, const double *G, double
 int fem_bp30_apply_f32(const fem_basis *b, int64_t E, const float *G, double lambda,
                        const float *q, float *Aq, void *stream);
 
+/* Precision selectors of the *_apply_ex entry points. */
+#define FEM_PREC_F64 0  /* FP64 factors, vectors and arithmetic (fem_bp35_apply, fem_bp30_apply) */
+#define FEM_PREC_F32 1  /* FP32 factors, vectors and arithmetic (fem_bp*_apply_f32) */
+#define FEM_PREC_F16G 2 /* binary16 factors scaled by a power of two, FP32 vectors and
+                         * arithmetic (fem_bp*_apply_f16g) */
+
+/* BP3.5 and BP3.0 matvecs with the precision chosen at run time: each call
+ * is the precision's own entry point above, with G, q and Aq of that
+ * precision's types (double; float; uint16_t binary16 bits for G and float
+ * for q, Aq).  ginv: device, one double, read by FEM_PREC_F16G only (may be
+ * NULL otherwise).  BP1.0 has only its FP64 form.  Layouts, alignment,
+ * asynchrony and ownership as for the entry point selected.
+ * Errors: FEM_EINVAL (also for an unknown prec), FEM_ECUDA. */
+int fem_bp35_apply_ex(const fem_basis *b, int64_t E, int prec, const void *G, const double *ginv,
+                      double lambda, const void *q, void *Aq, void *stream);
+int fem_bp30_apply_ex(const fem_basis *b, int64_t E, int prec, const void *G, const double *ginv,
+                      double lambda, const void *q, void *Aq, void *stream);
+
 /* Inverse of the diagonal of the BP3.5 operator D^T G D + lambda J (the
  * Jacobi preconditioner), in closed form:
  *   diag_ijk = sum_l (D_li^2 Grr_ljk + D_lj^2 Gss_ilk + D_lk^2 Gtt_ijl)

@@ -22,6 +22,7 @@ __all__ = [
     "fem_bp35_apply", "fem_bp30_apply", "FEM_GEO_BP1", "FEM_GEO_BP35", "FEM_GEO_BP30",
     "geo_shape", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_wait_selftest", "fem_bp30_apply_layout", "fem_fma_probe",
     "FEM_LAYOUT_LINES", "FEM_LAYOUT_POINTS", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot", "fem_dot_scratch_size", "Pcg",
+    "fem_bp35_apply_ex", "fem_bp30_apply_ex", "FEM_PREC_F64", "FEM_PREC_F32", "FEM_PREC_F16G",
     "fem_pcg_create", "fem_pcg_solve", "fem_pcg_destroy", "FEM_PCG_FP64", "FEM_PCG_MIXED", "FEM_PCG_MIXED16", "fem_bp35_apply_f16g", "fem_bp30_apply_f16g",
     "Batch", "fem_batch_create", "FEM_OP_BP35", "FEM_OP_BP30", "Server",
     "FEM_REQ_QUEUED", "FEM_REQ_RUNNING", "FEM_REQ_DONE", "FEM_REQ_FAILED",
@@ -33,6 +34,7 @@ FEM_PCG_FP64, FEM_PCG_MIXED, FEM_PCG_MIXED16 = 0, 1, 2
 FEM_GEO_BP1, FEM_GEO_BP35, FEM_GEO_BP30 = 1, 2, 3
 FEM_OP_BP35, FEM_OP_BP30 = 2, 3
 FEM_LAYOUT_LINES, FEM_LAYOUT_POINTS = 0, 1
+FEM_PREC_F64, FEM_PREC_F32, FEM_PREC_F16G = 0, 1, 2
 FEM_REQ_QUEUED, FEM_REQ_RUNNING, FEM_REQ_DONE, FEM_REQ_FAILED = 0, 1, 2, 3
 MAX_N = 15
 
@@ -124,6 +126,8 @@ def lib():
             L.fem_bp30_apply_layout.argtypes = [vp, i64, dp, dbl, dp, dp, i32, vp]
             L.fem_bp35_apply_f16g.argtypes = [vp, i64, dp, dp, dbl, dp, dp, vp]
             L.fem_bp30_apply_f16g.argtypes = [vp, i64, dp, dp, dbl, dp, dp, vp]
+            L.fem_bp35_apply_ex.argtypes = [vp, i64, i32, dp, dp, dbl, dp, dp, vp]
+            L.fem_bp30_apply_ex.argtypes = [vp, i64, i32, dp, dp, dbl, dp, dp, vp]
             L.fem_bp35_jacobi.argtypes = [vp, i64, dp, dbl, dp, vp]
             L.fem_dot_scratch_size.restype = i64
             L.fem_dot.argtypes = [i64, dp, dp, dp, dp, vp]
@@ -162,7 +166,8 @@ def lib():
             for f in ("fem_basis_setup", "fem_basis_tables", "fem_basis_host_tables",
                       "fem_mesh_geofacs", "fem_bp1_apply", "fem_bp35_apply", "fem_bp30_apply",
                       "fem_basis_degree", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_bp30_apply_layout", "fem_fma_probe",
-                      "fem_bp35_apply_f16g", "fem_bp30_apply_f16g", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot",
+                      "fem_bp35_apply_f16g", "fem_bp30_apply_f16g", "fem_bp35_apply_ex", "fem_bp30_apply_ex",
+                      "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot",
                       "fem_pcg_create", "fem_pcg_solve"):
                 getattr(L, f).restype = i32
             _lib = L
@@ -369,6 +374,44 @@ def fem_bp35_apply_f16g(b: Basis, G16, ginv, lam: float, q, out=None, stream=Non
 def fem_bp30_apply_f16g(b: Basis, G16, ginv, lam: float, q, out=None, stream=None):
     """BP3.0 matvec with binary16 factors and FP32 data (see fem_bp35_apply_f16g)."""
     return _apply_f16g("fem_bp30_apply_f16g", b, G16, ginv, lam, q, out, stream, b.m ** 3)
+
+
+def _apply_ex(name, b: Basis, prec, G, lam, q, ginv, out, stream, gpts):
+    import torch
+    if prec not in (FEM_PREC_F64, FEM_PREC_F32, FEM_PREC_F16G):
+        raise ValueError(f"unknown precision {prec}")
+    E = q.shape[0]
+    vec = _dev if prec == FEM_PREC_F64 else _dev32
+    vec(q, "q", E * b.n ** 3)
+    gptr = None
+    if prec == FEM_PREC_F16G:
+        if not isinstance(G, torch.Tensor) or not G.is_cuda or G.dtype != torch.float16 or \
+                not G.is_contiguous() or G.numel() != E * 7 * gpts:
+            raise TypeError("G must be a contiguous float16 CUDA tensor of E*7*points values")
+        if not isinstance(ginv, torch.Tensor) or not ginv.is_cuda or ginv.dtype != torch.float64 or \
+                ginv.numel() != 1:
+            raise TypeError("ginv must be a one-element float64 CUDA tensor")
+        gptr = ginv.data_ptr()
+    else:
+        vec(G, "G", E * 7 * gpts)
+    if out is None:
+        out = torch.empty_like(q)
+    vec(out, "out", E * b.n ** 3)
+    _check(getattr(lib(), name)(b.handle, E, int(prec), G.data_ptr(), gptr, float(lam), q.data_ptr(),
+                                out.data_ptr(), _stream(stream, q.device)), name)
+    return out
+
+
+def fem_bp35_apply_ex(b: Basis, prec: int, G, lam: float, q, ginv=None, out=None, stream=None):
+    """BP3.5 matvec with the precision chosen at run time: FEM_PREC_F64
+    (float64 G, q), FEM_PREC_F32 (float32 G, q) or FEM_PREC_F16G (float16 G
+    scaled by a power of two undone by ginv, float32 q)."""
+    return _apply_ex("fem_bp35_apply_ex", b, prec, G, lam, q, ginv, out, stream, b.n ** 3)
+
+
+def fem_bp30_apply_ex(b: Basis, prec: int, G, lam: float, q, ginv=None, out=None, stream=None):
+    """BP3.0 matvec with the precision chosen at run time (see fem_bp35_apply_ex)."""
+    return _apply_ex("fem_bp30_apply_ex", b, prec, G, lam, q, ginv, out, stream, b.m ** 3)
 
 
 def fem_bp30_apply_layout(b: Basis, G, lam: float, q, layout: int, out=None, stream=None):

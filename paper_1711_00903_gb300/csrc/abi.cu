@@ -223,9 +223,7 @@ int fem_bp35_apply_f32(const fem_basis *b, int64_t E, const float *G, double lam
     if (!b || E < 0) return FEM_EINVAL;
     if (E == 0) return FEM_OK;
     if (!G || !q || !Aq || !aligned16(G) || !aligned16(q) || !aligned16(Aq)) return FEM_EINVAL;
-    const int64_t np = cube(b->host.n);
     if ((const void *)Aq == (const void *)q || (E + 1) > (int64_t)0x7fffffff) return FEM_EINVAL;
-    (void)np;
     cudaError_t e = fem::launch_bp35_f32(b, E, G, lambda, q, Aq, (cudaStream_t)stream);
     return e == cudaSuccess ? FEM_OK : cuda_fail(e);
 }
@@ -310,6 +308,34 @@ int fem_bp30_apply(const fem_basis *b, int64_t E, const double *G, double lambda
     if (c != FEM_OK || E == 0) return c;
     cudaError_t e = fem::launch_bp30(b, E, G, lambda, q, Aq, (cudaStream_t)stream);
     return e == cudaSuccess ? FEM_OK : cuda_fail(e);
+}
+
+int fem_bp35_apply_ex(const fem_basis *b, int64_t E, int prec, const void *G, const double *ginv, double lambda,
+                      const void *q, void *Aq, void *stream) {
+    switch (prec) {
+        case FEM_PREC_F64:
+            return fem_bp35_apply(b, E, (const double *)G, lambda, (const double *)q, (double *)Aq, stream);
+        case FEM_PREC_F32:
+            return fem_bp35_apply_f32(b, E, (const float *)G, lambda, (const float *)q, (float *)Aq, stream);
+        case FEM_PREC_F16G:
+            return fem_bp35_apply_f16g(b, E, G, ginv, lambda, (const float *)q, (float *)Aq, stream);
+        default:
+            return FEM_EINVAL;
+    }
+}
+
+int fem_bp30_apply_ex(const fem_basis *b, int64_t E, int prec, const void *G, const double *ginv, double lambda,
+                      const void *q, void *Aq, void *stream) {
+    switch (prec) {
+        case FEM_PREC_F64:
+            return fem_bp30_apply(b, E, (const double *)G, lambda, (const double *)q, (double *)Aq, stream);
+        case FEM_PREC_F32:
+            return fem_bp30_apply_f32(b, E, (const float *)G, lambda, (const float *)q, (float *)Aq, stream);
+        case FEM_PREC_F16G:
+            return fem_bp30_apply_f16g(b, E, G, ginv, lambda, (const float *)q, (float *)Aq, stream);
+        default:
+            return FEM_EINVAL;
+    }
 }
 
 }  // extern "C"

@@ -165,6 +165,37 @@ def test_f16_factor_operators(op, N):
     assert fem.fem_wait_timeouts() == 0
 
 
+@pytest.mark.parametrize("op", ["bp35", "bp30"])
+@pytest.mark.parametrize("N", [2, 7])
+def test_apply_ex_selects_the_precision_entry_points(op, N):
+    """The run-time-precision entry points give, bit for bit, the results of
+    the entry point of each precision, and the FP64 one matches the oracle."""
+    fem, torch = _fem(), _torch()
+    v = fem_synth.box_mesh(3)[:23]
+    E = v.shape[0]
+    kind = oracle.KIND_BP35 if op == "bp35" else oracle.KIND_BP30
+    G, _ = oracle.geofacs(N, kind, v)
+    q = fem_synth.field(5, E, (N + 1) ** 3)
+    b = fem.fem_basis_setup(N)
+    ex = fem.fem_bp35_apply_ex if op == "bp35" else fem.fem_bp30_apply_ex
+    f64 = fem.fem_bp35_apply if op == "bp35" else fem.fem_bp30_apply
+    f32 = fem.fem_bp35_apply_f32 if op == "bp35" else fem.fem_bp30_apply_f32
+    f16 = fem.fem_bp35_apply_f16g if op == "bp35" else fem.fem_bp30_apply_f16g
+    Gd, qd = _dev(G), _dev(q)
+    got = ex(b, fem.FEM_PREC_F64, Gd, 1.0, qd)
+    assert torch.equal(got, f64(b, Gd, 1.0, qd))
+    assert _rel(got.cpu().numpy(), (oracle.bp35 if op == "bp35" else oracle.bp30)(N, G, 1.0, q)) <= 1e-12
+    G32, q32 = Gd.float(), qd.float()
+    assert torch.equal(ex(b, fem.FEM_PREC_F32, G32, 1.0, q32), f32(b, G32, 1.0, q32))
+    G16, ginv = _f16_factors(G)
+    G16d, gi = torch.from_numpy(G16).to("cuda"), torch.tensor([ginv], dtype=torch.float64, device="cuda")
+    assert torch.equal(ex(b, fem.FEM_PREC_F16G, G16d, 1.0, q32, ginv=gi), f16(b, G16d, gi, 1.0, q32))
+    with pytest.raises(ValueError):
+        ex(b, 3, Gd, 1.0, qd)
+    with pytest.raises(TypeError):
+        ex(b, fem.FEM_PREC_F32, Gd, 1.0, qd)  # float64 tensors for the FP32 path
+
+
 def test_dot_deterministic_and_exact():
     fem, torch = _fem(), _torch()
     x = fem_synth.field(11, 1, 3_000_001)[0]
