@@ -863,7 +863,8 @@ def run_serve(fem, torch, args):
     or BP3.5 at random, N uniform in 3..9, E log-uniform in 512..32768, rhs
     uniform in [-1, 1], tolerance 1e-8, FP64 or mixed precision (FP16
     factors) at random, 120 GiB HBM budget; continuous batching with 8 slots
-    against one request at a time (first come, first served)."""
+    (first come first served, and least estimated work first) against one
+    request at a time (first come, first served)."""
     reqs = fem_synth.serve_workload(args.serve_requests)
     data = []
     for r in reqs:
@@ -871,8 +872,8 @@ def run_serve(fem, torch, args):
         rhs = fem_synth.field(r["rhs_seed"], r["E"], (r["N"] + 1) ** 3)
         data.append((r, v, rhs))
 
-    def play(max_active):
-        srv = fem.Server(hbm_budget=120 << 30, max_active=max_active)
+    def play(max_active, policy=0):
+        srv = fem.Server(hbm_budget=120 << 30, max_active=max_active, policy=policy)
         t0 = srv.clock()
         k, ids = 0, []
         while True:
@@ -903,11 +904,13 @@ def run_serve(fem, torch, args):
         return out, [x for _, _, x in res]
 
     cb, xs_cb = play(8)
+    sjf, xs_sjf = play(8, fem.FEM_SERVE_SHORTEST)
     fifo, xs_fifo = play(1)
-    same = all(np.array_equal(a, b) for a, b in zip(xs_cb, xs_fifo))
+    same = all(np.array_equal(a, b) and np.array_equal(a, c) for a, b, c in zip(xs_cb, xs_fifo, xs_sjf))
     return {"workload": f"{len(data)} requests, Poisson arrivals at 200/s, BP3.0|BP3.5, N 3..9, E 512..32768 "
                         "log-uniform, rhs U[-1,1], tol 1e-8, FP64|mixed (FP16 factors), 120 GiB budget",
-            "continuous_batching_8_slots": cb, "one_at_a_time": fifo,
+            "continuous_batching_8_slots": cb, "continuous_batching_8_slots_shortest_first": sjf,
+            "one_at_a_time": fifo,
             "results_identical_alone_and_in_mix": same}
 
 

@@ -430,18 +430,29 @@ void fem_batch_destroy(fem_batch *b);
  * Continuous-batching server of Helmholtz solves on one GPU.  Each request
  * is a BP3.5 or BP3.0 system on its own mesh (vertices and right-hand side
  * in host memory), solved by the Jacobi-PCG above in FP64 or mixed
- * precision with all of its state on the device.  Requests wait in a FIFO
- * queue and are admitted while a slot is free and their device footprint
- * fits the HBM budget; admitted solves run on separate streams and
+ * precision with all of its state on the device.  Requests wait in a queue
+ * (FIFO, or least estimated work first) and are admitted while a slot is
+ * free and their device footprint fits the HBM budget; admitted solves run
+ * on separate streams and
  * overlap on the GPU.  A request's result is bit-identical alone and in
  * the mix (deterministic per-request reductions).
  * --------------------------------------------------------------------- */
 typedef struct fem_server fem_server; /* opaque */
 
+/* Admission order of queued requests. */
+#define FEM_SERVE_FIFO 0     /* first come, first served (default)                    */
+#define FEM_SERVE_SHORTEST 1 /* least estimated work first: E^(4/3) (N+1)^3 N ln(1/tol),
+                              * times 2.5 for BP3.0 and 0.15 for the mixed modes (the
+                              * per-iteration cost and the growth of Jacobi-PCG's
+                              * iteration count with N and the mesh size); ties by
+                              * arrival.  A large request can wait behind a stream of
+                              * smaller ones.                                          */
+
 typedef struct {
     int64_t hbm_budget; /* device bytes admitted requests may hold (default 120 GiB) */
     int max_active;     /* requests in flight at once, 1..256 (default 8)          */
     int check_every;    /* PCG iterations between host checks (default 8)          */
+    int policy;         /* FEM_SERVE_FIFO or FEM_SERVE_SHORTEST                     */
 } fem_serve_opts;
 
 typedef struct {
@@ -482,7 +493,9 @@ int fem_serve_submit(fem_server *s, const fem_serve_request *req, int64_t *id);
 
 /* Moves the server on without blocking: retires finished solves, moves every
  * solve in flight on by one step when its previous step has finished, and
- * admits queued requests (FIFO) while a slot and budget allow.  Call it in a
+ * admits queued requests (in the server's policy order) while a slot and the
+ * budget allow; a request at the head of that order that does not fit the
+ * remaining budget holds back the ones behind it.  Call it in a
  * loop.  *active / *queued (may be NULL) receive the counts afterwards.
  * Errors: FEM_EINVAL. */
 int fem_serve_progress(fem_server *s, int *active, int *queued);

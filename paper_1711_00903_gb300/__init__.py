@@ -25,7 +25,7 @@ __all__ = [
     "fem_bp35_apply_ex", "fem_bp30_apply_ex", "FEM_PREC_F64", "FEM_PREC_F32", "FEM_PREC_F16G",
     "fem_pcg_create", "fem_pcg_solve", "fem_pcg_destroy", "FEM_PCG_FP64", "FEM_PCG_MIXED", "FEM_PCG_MIXED16", "fem_bp35_apply_f16g", "fem_bp30_apply_f16g",
     "Batch", "fem_batch_create", "FEM_OP_BP35", "FEM_OP_BP30", "Server",
-    "FEM_REQ_QUEUED", "FEM_REQ_RUNNING", "FEM_REQ_DONE", "FEM_REQ_FAILED",
+    "FEM_REQ_QUEUED", "FEM_REQ_RUNNING", "FEM_REQ_DONE", "FEM_REQ_FAILED", "FEM_SERVE_FIFO", "FEM_SERVE_SHORTEST",
 ]
 
 FEM_OK, FEM_EINVAL, FEM_ECUDA, FEM_ENOMEM, FEM_ENODEV = 0, -1, -2, -3, -4
@@ -36,6 +36,7 @@ FEM_OP_BP35, FEM_OP_BP30 = 2, 3
 FEM_LAYOUT_LINES, FEM_LAYOUT_POINTS = 0, 1
 FEM_PREC_F64, FEM_PREC_F32, FEM_PREC_F16G = 0, 1, 2
 FEM_REQ_QUEUED, FEM_REQ_RUNNING, FEM_REQ_DONE, FEM_REQ_FAILED = 0, 1, 2, 3
+FEM_SERVE_FIFO, FEM_SERVE_SHORTEST = 0, 1
 MAX_N = 15
 
 _lock = threading.Lock()
@@ -67,7 +68,8 @@ class BatchConfig(C.Structure):
 
 class ServeOpts(C.Structure):
     """fem_serve_opts (include/fem.h)."""
-    _fields_ = [("hbm_budget", C.c_int64), ("max_active", C.c_int), ("check_every", C.c_int)]
+    _fields_ = [("hbm_budget", C.c_int64), ("max_active", C.c_int), ("check_every", C.c_int),
+                ("policy", C.c_int)]
 
 
 class ServeRequest(C.Structure):
@@ -672,8 +674,9 @@ class Server:
     solves).  Host arrays of a request are kept referenced here until the
     request has finished."""
 
-    def __init__(self, hbm_budget=120 << 30, max_active=8, check_every=8):
-        o = ServeOpts(int(hbm_budget), int(max_active), int(check_every))
+    def __init__(self, hbm_budget=120 << 30, max_active=8, check_every=8, policy=0):
+        """policy: FEM_SERVE_FIFO (0) or FEM_SERVE_SHORTEST (1)."""
+        o = ServeOpts(int(hbm_budget), int(max_active), int(check_every), int(policy))
         h = C.c_void_p()
         _check(lib().fem_serve_create(C.byref(o), C.byref(h)), "fem_serve_create")
         self.handle = h

@@ -1,7 +1,8 @@
 // Continuous-batching server of Helmholtz solves (BP3.5 or BP3.0 operator,
 // FP64 or mixed-precision Jacobi-PCG) on one GPU.
 //
-// Requests arrive at any time (fem_serve_submit) and wait in a FIFO queue.
+// Requests arrive at any time (fem_serve_submit) and wait in a queue, served
+// first come first served or least estimated work first.
 // fem_serve_progress, called in the caller's loop, never blocks: it admits
 // queued requests while a slot is free and their device footprint fits the
 // HBM budget, moves every admitted solve on by one step when its previous
@@ -14,6 +15,7 @@
 // the iterate freezes on the device at convergence), so its result is
 // bit-identical alone and in the mix.
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -27,6 +29,7 @@ namespace {
 struct Request {
     fem_serve_request req;
     fem_serve_result res;
+    double work;  // est_work(req)
     // device state while running
     int slot;
     fem_pcg *pcg;
@@ -52,6 +55,19 @@ int64_t footprint(const fem_serve_request &r) {
     else  // q (FP64); FP32 (or FP16) factors and 6 FP32 vectors
         bytes += 8 * len + (r.mode == FEM_PCG_MIXED16 ? 2 : 4) * 7 * r.E * gpts + 4 * 6 * len;
     return bytes + 64 * 1024;
+}
+
+// Estimated device work of a solve, for FEM_SERVE_SHORTEST: the per-iteration
+// cost (E (N+1)^3, 2.5 times more for BP3.0, about 0.15 of it for the FP32
+// inner iterations of the mixed modes) times the Jacobi-PCG iteration count,
+// which grows like the square root of the condition number, roughly
+// N E^(1/3) on these meshes, and like ln(1/tol).
+double est_work(const fem_serve_request &r) {
+    const double n = r.N + 1.0;
+    double w = std::pow((double)r.E, 4.0 / 3.0) * n * n * n * r.N * std::log(1.0 / r.tol);
+    if (r.op == FEM_OP_BP30) w *= 2.5;
+    if (r.mode != FEM_PCG_FP64) w *= 0.15;
+    return w;
 }
 
 double now_s(const std::chrono::steady_clock::time_point &t0) {
@@ -137,7 +153,8 @@ int fem_serve_create(const fem_serve_opts *opts, fem_server **out) {
     o.hbm_budget = (opts && opts->hbm_budget > 0) ? opts->hbm_budget : (int64_t)120 << 30;
     o.max_active = (opts && opts->max_active > 0) ? opts->max_active : 8;
     o.check_every = (opts && opts->check_every > 0) ? opts->check_every : 8;
-    if (o.max_active > 256) return FEM_EINVAL;
+    o.policy = opts ? opts->policy : FEM_SERVE_FIFO;
+    if (o.max_active > 256 || (o.policy != FEM_SERVE_FIFO && o.policy != FEM_SERVE_SHORTEST)) return FEM_EINVAL;
     fem_server *s = new (std::nothrow) fem_server();
     if (!s) return FEM_ENOMEM;
     s->opts = o;
@@ -179,6 +196,7 @@ int fem_serve_submit(fem_server *s, const fem_serve_request *req, int64_t *id) {
     R.res.status = FEM_OK;
     R.res.t_submit = now_s(s->t0);
     R.res.bytes = footprint(q);
+    R.work = est_work(q);
     *id = s->next_id++;
     s->reqs[*id] = R;
     s->queue.push_back(*id);
@@ -237,8 +255,19 @@ int fem_serve_progress(fem_server *s, int *active, int *queued) {
             k++;
         }
     }
-    // 2. admit from the head of the queue (first come, first served)
+    // 2. admit from the head of the queue (first come, first served), or
+    // the least estimated work first (ties by arrival)
     while (!s->queue.empty()) {
+        if (s->opts.policy == FEM_SERVE_SHORTEST) {
+            auto best = s->queue.begin();
+            for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
+                if (s->reqs[*it].work < s->reqs[*best].work) best = it;
+            if (best != s->queue.begin()) {
+                const int64_t id = *best;
+                s->queue.erase(best);
+                s->queue.push_front(id);
+            }
+        }
         Request &R = s->reqs[s->queue.front()];
         if (R.res.bytes > s->opts.hbm_budget) {  // can never fit
             R.res.state = FEM_REQ_FAILED;

@@ -77,6 +77,8 @@ def test_argument_errors_need_no_gpu():
     assert L.fem_basis_degree(None) == fem.FEM_EINVAL
     assert L.fem_basis_tables(None, *([None] * 7)) == fem.FEM_EINVAL
     L.fem_basis_free(None)  # accepted
+    bad = fem.ServeOpts(1 << 30, 4, 8, 7)  # unknown admission policy
+    assert L.fem_serve_create(C.byref(bad), C.byref(C.c_void_p())) == fem.FEM_EINVAL
     assert L.fem_bp35_apply_f32(None, 1, p, 1.0, p, p, None) == fem.FEM_EINVAL
     assert L.fem_bp30_apply_f32(None, 1, p, 1.0, p, p, None) == fem.FEM_EINVAL
     # calibration stream: plane count, word size, vector alignment, overlap

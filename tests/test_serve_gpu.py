@@ -87,3 +87,30 @@ def test_admission_under_the_budget():
     assert s.in_use() == 0
     with pytest.raises(fem.FemError):
         s.poll(12345)
+
+
+def _est_work(op, N, E, mixed, tol):
+    """The server's work estimate for least-work-first admission (restated
+    from its documented formula)."""
+    w = E ** (4.0 / 3.0) * (N + 1) ** 3 * N * np.log(1.0 / tol)
+    return w * (2.5 if op == 3 else 1.0) * (0.15 if mixed else 1.0)
+
+
+def test_shortest_first_admission_order_and_same_bits():
+    """With one slot and every request queued before the first progress
+    call, FEM_SERVE_SHORTEST admits in increasing estimated work (ties by
+    arrival), and each result is the same bits as under FIFO."""
+    fem = _fem()
+    reqs = _requests()
+    fifo = _run(fem.Server(max_active=8), reqs, one_at_a_time=False)
+    srv = fem.Server(max_active=1, policy=fem.FEM_SERVE_SHORTEST)
+    sjf = _run(srv, reqs, one_at_a_time=False)
+    for (xa, ra), (xs, rs) in zip(fifo, sjf):
+        assert rs["state"] == fem.FEM_REQ_DONE
+        assert np.array_equal(xa, xs)
+    work = [_est_work(op, N, v.shape[0], mixed, 1e-9) for op, N, v, rhs, lam, mixed in reqs]
+    order = sorted(range(len(reqs)), key=lambda k: (work[k], k))
+    admitted = sorted(range(len(reqs)), key=lambda k: sjf[k][1]["t_admit"])
+    assert admitted == order
+    with pytest.raises(fem.FemError):
+        fem.Server(policy=7)
