@@ -552,6 +552,19 @@ def run_ours(args):
     sweep = None if (args.no_sweep or rank != 0) else run_sweep(fem, torch, device, verts, args, sm_mhz)
     pcg = None if args.no_pcg else run_pcg(fem, torch, device, verts_h, args)
     batch = None if args.no_batch else run_batch(fem, torch, device, args)
+    if batch and sweep:
+        # the batch's lower bound at the stand-alone operators' full-GPU rates
+        # (the per-N sweep on the 32^3 mesh): every mesh's DOFs at its
+        # degree's GDOF/s, summed over the two operators
+        rates = {r["N"]: (r["bp35"]["gdofs"], r["bp30"]["gdofs"]) for r in sweep["rows"]}
+        w = fem_synth.batch_workload()
+        if all(s_["N"] in rates for s_ in w):
+            ms_ideal = sum(s_["E"] * (s_["N"] + 1) ** 3 * (1 / rates[s_["N"]][0] + 1 / rates[s_["N"]][1])
+                           for s_ in w) / 1e6
+            batch["at_standalone_full_gpu_rates"] = {
+                "ms": ms_ideal, "tuned_frac": ms_ideal / batch["persistent_tuned"]["ms"],
+                "note": "every mesh at the sweep's GDOF/s for its degree and operator; the tuned "
+                        "persistent launch's time against it"}
     serve = None if args.serve_requests <= 0 else run_serve(fem, torch, args)
 
     cpu = None
