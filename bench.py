@@ -566,6 +566,7 @@ def run_ours(args):
                 "note": "every mesh at the sweep's GDOF/s for its degree and operator; the tuned "
                         "persistent launch's time against it"}
     serve = None if args.serve_requests <= 0 else run_serve(fem, torch, args)
+    small = None if (args.no_sweep or rank != 0) else run_small_case(fem, torch, device)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -599,6 +600,7 @@ def run_ours(args):
             "clocks": clocks,
             "kernels": kern,
             "sweep": sweep,
+            "small_case": small,
             "pcg": pcg,
             "batch": batch,
             "serve": serve,
@@ -741,6 +743,48 @@ def run_sweep(fem, torch, device, verts, args, sm_mhz):
             "copy_roofline": "device-to-device copy of T/2 bytes moving T = the operator's algorithmic "
                              "bytes, recalibrated at every N (Section 5 of the paper)",
             "rows": rows}
+
+
+def run_small_case(fem, torch, device):
+    """The small configuration: BP1.0 at N = 3 on the 8^3 jittered mesh (E =
+    512, 32768 DOFs, 1.04 MB of algorithmic traffic, resident in L2).  It is
+    bound by launch latency, so the figure is microseconds per launch: back
+    to back on one stream, and replayed from a CUDA graph of 100 launches."""
+    N, reps = 3, 100
+    b = fem.fem_basis_setup(N)
+    v = torch.from_numpy(fem_synth.box_mesh(8)).to(device)
+    E = v.shape[0]
+    wJ = fem.fem_mesh_geofacs(b, fem.FEM_GEO_BP1, v)
+    q = torch.from_numpy(fem_synth.field(fem_synth.SEED_Q, E, (N + 1) ** 3)).to(device)
+    out = torch.empty_like(q)
+    st = torch.cuda.Stream(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(st):
+        for _ in range(10):
+            fem.fem_bp1_apply(b, wJ, q, out=out, stream=st)
+        st.synchronize()
+        e0.record(st)
+        for _ in range(reps):
+            fem.fem_bp1_apply(b, wJ, q, out=out, stream=st)
+        e1.record(st)
+        st.synchronize()
+        us_stream = e0.elapsed_time(e1) * 1e3 / reps
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            for _ in range(reps):
+                fem.fem_bp1_apply(b, wJ, q, out=out, stream=st)
+        g.replay()
+        st.synchronize()
+        e0.record(st)
+        g.replay()
+        e1.record(st)
+        st.synchronize()
+        us_graph = e0.elapsed_time(e1) * 1e3 / reps
+    dofs = E * (N + 1) ** 3
+    b.free()
+    return {"workload": "BP1.0 FP64, N=3, E=512 (8^3 jittered mesh), inputs resident in L2",
+            "us_per_launch_stream": us_stream, "us_per_launch_graph": us_graph,
+            "gdofs_graph": dofs / (us_graph * 1e-6) / 1e9}
 
 
 def manufactured_u(fem, basis, verts_h):

@@ -20,7 +20,9 @@
 namespace fem {
 namespace {
 
-template <int N>
+// TARGET: the block's thread target (256; 32 for meshes too small to give
+// every SM two blocks, where one element per block spreads the work)
+template <int N, int TARGET = 256>
 struct Bp1Cfg {
     static constexpr int n = N + 1, m = N + 2;
     static constexpr int NP = n * n * n, MP = m * m * m;
@@ -30,7 +32,7 @@ struct Bp1Cfg {
     static constexpr int SA = (B0::size > B2::size) ? B0::size : B2::size;
     static constexpr int SB = B1::size;
     static constexpr int per = SA + SB;
-    static constexpr int EPB = pick_epb(m, per * 8);
+    static constexpr int EPB = pick_epb(m, per * 8, TARGET);
     static constexpr int threads = ((m * m * EPB + 31) / 32) * 32;
     static constexpr int smem = EPB * per * 8;
     static constexpr int oI = fold_offset(N, kFoldI), oIT = fold_offset(N, kFoldIT);
@@ -40,10 +42,10 @@ struct Bp1Cfg {
     static constexpr int min_blocks = 3;
 };
 
-template <int N>
-__global__ void __launch_bounds__(Bp1Cfg<N>::threads, Bp1Cfg<N>::min_blocks)
+template <int N, int TARGET>
+__global__ void __launch_bounds__(Bp1Cfg<N, TARGET>::threads, Bp1Cfg<N, TARGET>::min_blocks)
 bp1_f64_kernel(int64_t E, const double *__restrict__ wJ, const double *__restrict__ q, double *__restrict__ Mq) {
-    using C = Bp1Cfg<N>;
+    using C = Bp1Cfg<N, TARGET>;
     using B0 = typename C::B0;
     using B1 = typename C::B1;
     using B2 = typename C::B2;
@@ -138,9 +140,15 @@ struct Bp1Launch {
     static cudaError_t run(const fem_basis *b, int64_t E, const double *wJ, const double *q, double *Mq,
                            cudaStream_t s) {
         using C = Bp1Cfg<N>;
+        using Cs = Bp1Cfg<N, 32>;
         (void)b;
         const int64_t blocks = (E + C::EPB - 1) / C::EPB;
-        bp1_f64_kernel<N><<<(unsigned)blocks, C::threads, C::smem, s>>>(E, wJ, q, Mq);
+        if (blocks < 2 * 152) {  // small mesh: one element (or a few) per block
+            bp1_f64_kernel<N, 32><<<(unsigned)((E + Cs::EPB - 1) / Cs::EPB), Cs::threads, Cs::smem, s>>>(E, wJ, q,
+                                                                                                      Mq);
+            return cudaGetLastError();
+        }
+        bp1_f64_kernel<N, 256><<<(unsigned)blocks, C::threads, C::smem, s>>>(E, wJ, q, Mq);
         return cudaGetLastError();
     }
 };
@@ -148,8 +156,12 @@ struct Bp1Launch {
 template <int N>
 struct Bp1Prepare {
     static cudaError_t run() {
-        return cudaFuncSetAttribute(bp1_f64_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    Bp1Cfg<N>::smem);
+        cudaError_t e = cudaFuncSetAttribute(bp1_f64_kernel<N, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             Bp1Cfg<N>::smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(bp1_f64_kernel<N, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     Bp1Cfg<N, 32>::smem);
+        return e;
     }
 };
 
