@@ -226,11 +226,12 @@ def big_mesh():
     return fem_synth.box_mesh(32)  # E = 32768 jittered hexes of the unit cube
 
 
-@pytest.mark.parametrize("N", [7])
+@pytest.mark.parametrize("N", range(1, 16))
 def test_full_size_sampled(bases, big_mesh, N):
-    """The 32^3 mesh at N = 7 in the bench's launch configuration; the oracle
-    recomputes 48 sampled elements (the operator is block diagonal, so each
-    element's output depends on that element's data alone)."""
+    """The 32^3 mesh at every degree of the sweep (N = 7 is the step's), in
+    the launch configuration bench.py times; the oracle recomputes 48
+    sampled elements (the operator is block diagonal, so each element's
+    output depends on that element's data alone)."""
     fem, torch = _fem(), _torch()
     b = bases[N]
     v = big_mesh
@@ -255,6 +256,41 @@ def test_full_size_sampled(bases, big_mesh, N):
         assert _rel(got, ref) < TOL
         del g, out
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("N", [1, 3, 4, 7, 9, 10, 15])
+def test_full_size_sampled_reduced_precision(bases, big_mesh, N):
+    """The FP32 and FP16-factor BP3.5 and BP3.0 operators of the sweep on the
+    32^3 mesh (stream kernels up to N = 9, block kernels above), 48 sampled
+    elements against the oracle applied to the same rounded factors and
+    field: the difference is FP32 arithmetic only."""
+    fem, torch = _fem(), _torch()
+    b = bases[N]
+    vd = _dev(big_mesh)
+    E = vd.shape[0]
+    q32 = _dev(fem_synth.field(fem_synth.SEED_Q, E, (N + 1) ** 3)).float()
+    rng = np.random.default_rng(1)
+    pick = np.unique(np.concatenate([rng.choice(E, 46, replace=False), [0, E - 1]]))
+    tp = torch.from_numpy(pick).cuda()
+    qs = q32[tp].cpu().numpy().astype(np.float64)
+    for kind, f32, f16, ref_op in ((2, fem.fem_bp35_apply_f32, fem.fem_bp35_apply_f16g, oracle.bp35),
+                                   (3, fem.fem_bp30_apply_f32, fem.fem_bp30_apply_f16g, oracle.bp30)):
+        g = fem.fem_mesh_geofacs(b, kind, vd)
+        g32 = g.float()
+        got = f32(b, g32, 1.0, q32)[tp].cpu().numpy().astype(np.float64)
+        ref = ref_op(N, g32[tp].cpu().numpy().astype(np.float64), 1.0, qs)
+        assert _rel(got, ref) < 2e-6 * (N + 2), ("f32", kind)
+        del g32
+        ex = int(np.frexp(g.abs().max().item())[1])
+        gi = torch.tensor([2.0 ** (ex - 14)], dtype=torch.float64, device="cuda")
+        g16 = (g * 2.0 ** (14 - ex)).half()
+        del g
+        got = f16(b, g16, gi, 1.0, q32)[tp].cpu().numpy().astype(np.float64)
+        ref = ref_op(N, g16[tp].cpu().numpy().astype(np.float64) * 2.0 ** (ex - 14), 1.0, qs)
+        assert _rel(got, ref) < 2e-6 * (N + 2), ("f16", kind)
+        del g16
+        torch.cuda.empty_cache()
+    assert fem.fem_wait_timeouts() == 0
 
 
 def test_full_size_invariants(bases, big_mesh):
