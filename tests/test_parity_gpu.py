@@ -293,6 +293,47 @@ def test_full_size_sampled_reduced_precision(bases, big_mesh, N):
     assert fem.fem_wait_timeouts() == 0
 
 
+def test_factor_arrays_beyond_2_31_entries(bases):
+    """N = 15 on an 80000-element mesh (50 x 40 x 40): the BP3.5 and BP3.0
+    factor arrays hold 2.29e9 and 2.75e9 entries, beyond 32-bit indexing.
+    Elements near the end, whose factors lie past entry 2^31, and a few at
+    the start are checked against the oracle in FP64, FP32 and FP16 factors."""
+    fem, torch = _fem(), _torch()
+    N = 15
+    b = bases[N]
+    v = fem_synth.box_mesh(50, 40, 40)
+    E = v.shape[0]
+    assert E == 80000 and E * 7 * (N + 1) ** 3 > 2 ** 31
+    vd = _dev(v)
+    q = _dev(fem_synth.field(fem_synth.SEED_Q, E, (N + 1) ** 3))
+    pick = np.array([0, 1, 17, E - 4000, E - 777, E - 2, E - 1])
+    tp = torch.from_numpy(pick).cuda()
+    qs = q[tp].cpu().numpy()
+    q32 = q.float()
+    qs32 = q32[tp].cpu().numpy().astype(np.float64)
+    for kind, f64, f32, f16, ref_op in ((2, fem.fem_bp35_apply, fem.fem_bp35_apply_f32, fem.fem_bp35_apply_f16g,
+                                         oracle.bp35),
+                                        (3, fem.fem_bp30_apply, fem.fem_bp30_apply_f32, fem.fem_bp30_apply_f16g,
+                                         oracle.bp30)):
+        g = fem.fem_mesh_geofacs(b, kind, vd)
+        gs_oracle, _ = oracle.geofacs(N, kind, v[pick])
+        assert _rel(g[tp].cpu().numpy(), gs_oracle) < TOL
+        assert _rel(f64(b, g, 1.0, q)[tp].cpu().numpy(), ref_op(N, gs_oracle, 1.0, qs)) < TOL
+        g32 = g.float()
+        got = f32(b, g32, 1.0, q32)[tp].cpu().numpy().astype(np.float64)
+        assert _rel(got, ref_op(N, g32[tp].cpu().numpy().astype(np.float64), 1.0, qs32)) < 2e-6 * (N + 2)
+        del g32
+        ex = int(np.frexp(g.abs().max().item())[1])
+        gi = torch.tensor([2.0 ** (ex - 14)], dtype=torch.float64, device="cuda")
+        g16 = (g * 2.0 ** (14 - ex)).half()
+        del g
+        got = f16(b, g16, gi, 1.0, q32)[tp].cpu().numpy().astype(np.float64)
+        gr = g16[tp].cpu().numpy().astype(np.float64) * 2.0 ** (ex - 14)
+        assert _rel(got, ref_op(N, gr, 1.0, qs32)) < 2e-6 * (N + 2)
+        del g16
+        torch.cuda.empty_cache()
+
+
 def test_full_size_invariants(bases, big_mesh):
     """Properties that hold at any size, checked on the whole 32^3 mesh:
     1^T M 1 = 1 (unit-cube volume) and A 1 = 0 for lambda = 0."""
