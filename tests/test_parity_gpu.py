@@ -95,7 +95,7 @@ def test_bp1_parity(bases, N):
     assert _rel(got, ref) < TOL
 
 
-@pytest.mark.parametrize("lam", [0.0, 1.0])
+@pytest.mark.parametrize("lam", [0.0, 1.0, 0.37])
 @pytest.mark.parametrize("N", range(1, 16))
 def test_bp35_parity(bases, N, lam):
     fem = _fem()
@@ -106,7 +106,7 @@ def test_bp35_parity(bases, N, lam):
     assert _rel(got, ref) < TOL
 
 
-@pytest.mark.parametrize("lam", [0.0, 1.0])
+@pytest.mark.parametrize("lam", [0.0, 1.0, 0.37])
 @pytest.mark.parametrize("N", range(1, 16))
 def test_bp30_parity(bases, N, lam):
     fem = _fem()
@@ -117,7 +117,7 @@ def test_bp30_parity(bases, N, lam):
     assert _rel(got, ref) < TOL
 
 
-@pytest.mark.parametrize("lam", [0.0, 1.0])
+@pytest.mark.parametrize("lam", [0.0, 1.0, 0.37])
 @pytest.mark.parametrize("N", range(1, 16))
 def test_bp30_point_layout_parity(bases, N, lam):
     """The point-per-thread layout of BP3.0 against the oracle, with a
