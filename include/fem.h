@@ -225,6 +225,18 @@ int fem_bp30_apply_layout(const fem_basis *b, int64_t E, const double *G, double
 int fem_bp30_apply_f32(const fem_basis *b, int64_t E, const float *G, double lambda,
                        const float *q, float *Aq, void *stream);
 
+/* BP1.0 and BP3.0 of one field in one pass (Algorithms 3 and 5): the
+ * interpolation of q to the Gauss points is computed once for both, and
+ * BP1.0's wJ is the seventh plane of G (the same w |J| at the same points,
+ * which fem_mesh_geofacs_set writes identically to its wJ output).
+ * G: device E*7*m^3 doubles (fem_bp30_apply's layout); q, Mq, Aq: device
+ * E*n^3 doubles, 16-byte aligned, Mq, Aq, q pairwise disjoint.  Mq and Aq
+ * are bit for bit what fem_bp1_apply (with that wJ) and fem_bp30_apply
+ * return.  Asynchronous on stream, allocates nothing.
+ * Errors: FEM_EINVAL, FEM_ECUDA. */
+int fem_bp1_bp30_apply(const fem_basis *b, int64_t E, const double *G, double lambda,
+                       const double *q, double *Mq, double *Aq, void *stream);
+
 /* Precision selectors of the *_apply_ex entry points. */
 #define FEM_PREC_F64 0  /* FP64 factors, vectors and arithmetic (fem_bp35_apply, fem_bp30_apply) */
 #define FEM_PREC_F32 1  /* FP32 factors, vectors and arithmetic (fem_bp*_apply_f32) */

@@ -22,7 +22,7 @@ __all__ = [
     "fem_bp35_apply", "fem_bp30_apply", "FEM_GEO_BP1", "FEM_GEO_BP35", "FEM_GEO_BP30",
     "geo_shape", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_wait_selftest", "fem_bp30_apply_layout", "fem_fma_probe",
     "FEM_LAYOUT_LINES", "FEM_LAYOUT_POINTS", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot", "fem_dot_scratch_size", "Pcg",
-    "fem_bp35_apply_ex", "fem_bp30_apply_ex", "FEM_PREC_F64", "FEM_PREC_F32", "FEM_PREC_F16G",
+    "fem_bp35_apply_ex", "fem_bp30_apply_ex", "fem_bp1_bp30_apply", "FEM_PREC_F64", "FEM_PREC_F32", "FEM_PREC_F16G",
     "fem_pcg_create", "fem_pcg_solve", "fem_pcg_destroy", "FEM_PCG_FP64", "FEM_PCG_MIXED", "FEM_PCG_MIXED16", "fem_bp35_apply_f16g", "fem_bp30_apply_f16g",
     "Batch", "fem_batch_create", "FEM_OP_BP35", "FEM_OP_BP30", "Server",
     "FEM_REQ_QUEUED", "FEM_REQ_RUNNING", "FEM_REQ_DONE", "FEM_REQ_FAILED", "FEM_SERVE_FIFO", "FEM_SERVE_SHORTEST",
@@ -129,6 +129,7 @@ def lib():
             L.fem_bp35_apply_f16g.argtypes = [vp, i64, dp, dp, dbl, dp, dp, vp]
             L.fem_bp30_apply_f16g.argtypes = [vp, i64, dp, dp, dbl, dp, dp, vp]
             L.fem_bp35_apply_ex.argtypes = [vp, i64, i32, dp, dp, dbl, dp, dp, vp]
+            L.fem_bp1_bp30_apply.argtypes = [vp, i64, dp, dbl, dp, dp, dp, vp]
             L.fem_bp30_apply_ex.argtypes = [vp, i64, i32, dp, dp, dbl, dp, dp, vp]
             L.fem_bp35_jacobi.argtypes = [vp, i64, dp, dbl, dp, vp]
             L.fem_dot_scratch_size.restype = i64
@@ -169,6 +170,7 @@ def lib():
                       "fem_mesh_geofacs", "fem_bp1_apply", "fem_bp35_apply", "fem_bp30_apply",
                       "fem_basis_degree", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_bp30_apply_layout", "fem_fma_probe",
                       "fem_bp35_apply_f16g", "fem_bp30_apply_f16g", "fem_bp35_apply_ex", "fem_bp30_apply_ex",
+                      "fem_bp1_bp30_apply",
                       "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot",
                       "fem_pcg_create", "fem_pcg_solve"):
                 getattr(L, f).restype = i32
@@ -414,6 +416,17 @@ def fem_bp35_apply_ex(b: Basis, prec: int, G, lam: float, q, ginv=None, out=None
 def fem_bp30_apply_ex(b: Basis, prec: int, G, lam: float, q, ginv=None, out=None, stream=None):
     """BP3.0 matvec with the precision chosen at run time (see fem_bp35_apply_ex)."""
     return _apply_ex("fem_bp30_apply_ex", b, prec, G, lam, q, ginv, out, stream, b.m ** 3)
+
+
+def fem_bp1_bp30_apply(b: Basis, G, lam: float, q, out_m=None, out_a=None, stream=None):
+    """BP1.0 and BP3.0 of one field in one pass: returns (Mq, Aq), with
+    BP1.0's wJ the seventh plane of the BP3.0 factors G."""
+    E, out_a = _apply_out(q, out_a, b)
+    _, out_m = _apply_out(q, out_m, b)
+    _dev(G, "G", E * 7 * b.m ** 3)
+    _check(lib().fem_bp1_bp30_apply(b.handle, E, G.data_ptr(), float(lam), q.data_ptr(), out_m.data_ptr(),
+                                    out_a.data_ptr(), _stream(stream, q.device)), "fem_bp1_bp30_apply")
+    return out_m, out_a
 
 
 def fem_bp30_apply_layout(b: Basis, G, lam: float, q, layout: int, out=None, stream=None):

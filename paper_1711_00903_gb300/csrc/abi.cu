@@ -310,6 +310,17 @@ int fem_bp30_apply(const fem_basis *b, int64_t E, const double *G, double lambda
     return e == cudaSuccess ? FEM_OK : cuda_fail(e);
 }
 
+int fem_bp1_bp30_apply(const fem_basis *b, int64_t E, const double *G, double lambda, const double *q,
+                       double *Mq, double *Aq, void *stream) {
+    int c = check_apply(b, E, G, b ? 7 * cube(b->host.m) : 0, q, Aq);
+    if (c == FEM_OK) c = check_apply(b, E, G, b ? 7 * cube(b->host.m) : 0, q, Mq);
+    if (c != FEM_OK || E == 0) return c;
+    const int64_t np = cube(b->host.n);
+    if (overlap(Mq, E * np, Aq, E * np)) return FEM_EINVAL;
+    cudaError_t e = fem::launch_bp1_bp30(b, E, G, lambda, q, Mq, Aq, (cudaStream_t)stream);
+    return e == cudaSuccess ? FEM_OK : cuda_fail(e);
+}
+
 int fem_bp35_apply_ex(const fem_basis *b, int64_t E, int prec, const void *G, const double *ginv, double lambda,
                       const void *q, void *Aq, void *stream) {
     switch (prec) {

@@ -60,6 +60,67 @@ constexpr auto bp30_fn() {
         return &bp30_kernel<T, N, PCG>;
 }
 
+// BP1.0 and BP3.0 of one field in one pass (bp30_core with MASS): the
+// interpolation to the Gauss points is done once for both, and BP1.0's wJ is
+// the seventh BP3.0 factor.  Mq and Aq are bit for bit the outputs of the
+// separate BP1.0 (with that wJ) and BP3.0 kernels.
+template <int N>
+struct Bp1Bp30Cfg
+    : Bp30Layout<N, pick_epb(N + 2, 4 * Box<N + 2, N + 2, N + 2>::size * 8, 256), double, 4> {};
+
+template <int N>
+__device__ __forceinline__ void bp1_bp30_entry(int64_t E, const double *__restrict__ G, double lambda,
+                                               const double *__restrict__ q, double *__restrict__ Mq,
+                                               double *__restrict__ Aq) {
+    using C = Bp1Bp30Cfg<N>;
+    using B0 = typename C::B0;
+    constexpr int n = C::n, NP = C::NP, MP = C::MP, S = C::S, per = C::per, EPB = C::EPB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *smem = reinterpret_cast<double *>(smem_raw);
+    const int64_t e0 = (int64_t)blockIdx.x * EPB;
+    const int nel = (int)((E - e0) < EPB ? (E - e0) : EPB);
+    for (int t = threadIdx.x; t < nel * NP; t += blockDim.x) {
+        const int el = t / NP, s = t - el * NP;
+        smem[el * per + S + B0::at(s % n, (s / n) % n, s / (n * n))] = __ldg(q + e0 * NP + t);
+    }
+    __syncthreads();
+    bp30_core<N, EPB, double, false, false, double, true>(smem, e0, nel, G + e0 * 7 * MP, lambda, Aq, nullptr, 1.0,
+                                                           Mq);
+}
+
+template <int N>
+__global__ void __launch_bounds__(Bp1Bp30Cfg<N>::threads)
+bp1_bp30_kernel(int64_t E, const double *__restrict__ G, double lambda, const double *__restrict__ q,
+                double *__restrict__ Mq, double *__restrict__ Aq) {
+    bp1_bp30_entry<N>(E, G, lambda, q, Mq, Aq);
+}
+
+template <int N>
+__global__ void __launch_bounds__(Bp1Bp30Cfg<N>::threads, bp30_min_blocks<double, N>())
+bp1_bp30_kernel_capped(int64_t E, const double *__restrict__ G, double lambda, const double *__restrict__ q,
+                       double *__restrict__ Mq, double *__restrict__ Aq) {
+    bp1_bp30_entry<N>(E, G, lambda, q, Mq, Aq);
+}
+
+template <int N>
+constexpr auto bp1_bp30_fn() {
+    if constexpr (bp30_min_blocks<double, N>() > 0)
+        return &bp1_bp30_kernel_capped<N>;
+    else
+        return &bp1_bp30_kernel<N>;
+}
+
+template <int N>
+struct Bp1Bp30Launch {
+    static cudaError_t run(int64_t E, const double *G, double lambda, const double *q, double *Mq, double *Aq,
+                           cudaStream_t s) {
+        using C = Bp1Bp30Cfg<N>;
+        const int64_t blocks = (E + C::EPB - 1) / C::EPB;
+        bp1_bp30_fn<N>()<<<(unsigned)blocks, C::threads, C::smem, s>>>(E, G, lambda, q, Mq, Aq);
+        return cudaGetLastError();
+    }
+};
+
 FEM_DEFINE_FOLD_UPLOAD(upload_fold_bp30_tu)
 
 template <typename T, bool PCG>
@@ -98,6 +159,9 @@ struct Bp30Prepare {
         if (e == cudaSuccess) e = one<double, true>();
         if (e == cudaSuccess) e = one<float, false>();
         if (e == cudaSuccess) e = one<float, true>();
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(bp1_bp30_fn<N>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     Bp1Bp30Cfg<N>::smem);
         return e;
     }
 };
@@ -128,6 +192,11 @@ cudaError_t launch_bp30_pcg_f32(const fem_basis *b, int64_t E, const float *G, d
                                 float *p, const double *beta, float *Ap, double *partials, cudaStream_t s) {
     return dispatch_degree<Bp30LaunchT<float, true>::L>(b->host.N, E, G, lambda, (const float *)nullptr, Ap, z, p,
                                                          beta, partials, s);
+}
+
+cudaError_t launch_bp1_bp30(const fem_basis *b, int64_t E, const double *G, double lambda, const double *q,
+                            double *Mq, double *Aq, cudaStream_t s) {
+    return dispatch_degree<Bp1Bp30Launch>(b->host.N, E, G, lambda, q, Mq, Aq, s);
 }
 
 int64_t bp30_blocks(int N, int64_t E, bool f32) {

@@ -13,7 +13,7 @@ namespace {
 // Layout of one block of EPB elements (three m^3 shared boxes each), data
 // type T (double for the paper's FP64 operator, float for the inner operator
 // of the mixed-precision solver).
-template <int N, int EPB_, typename T = double>
+template <int N, int EPB_, typename T = double, int BOXES = 3>
 struct Bp30Layout {
     static constexpr int n = N + 1, m = N + 2;
     static constexpr int NP = n * n * n, MP = m * m * m, mm = m * m;
@@ -22,7 +22,7 @@ struct Bp30Layout {
     using B2 = Box<m, m, n>;
     using B3 = Box<m, m, m>;
     static constexpr int S = B3::size;  // every buffer holds one m^3 box
-    static constexpr int per = 3 * S;
+    static constexpr int per = BOXES * S;
     static constexpr int EPB = EPB_;
     static constexpr int threads = ((mm * EPB + 31) / 32) * 32;  // the block needs at least this many
     static constexpr int bytes = EPB * per * (int)sizeof(T);
@@ -54,10 +54,15 @@ struct Bp30Cfg : Bp30Layout<N,
 // scaled by a power of two that gscale undoes on the output).  PCG: p holds
 // the input field in global memory (the staging wrote it) for the thread's
 // share of p . Ap, which is returned.  Ends without a barrier.
-template <int N, int EPB_, typename T, bool PCG, bool G_SMEM, typename TG>
+// MASS = true: also BP1.0 of the same field, Mq = I^T wJ I q with wJ the
+// seventh factor, from the interpolated field the operator computes anyway
+// (four boxes per element, the fourth, D, for BP1.0's t-projection); its
+// projections run in phases 5, 6 and 8 beside the operator's.
+template <int N, int EPB_, typename T, bool PCG, bool G_SMEM, typename TG, bool MASS = false>
 __device__ __forceinline__ T bp30_core(T *smem, int64_t e0, int nel, const TG *__restrict__ Gsrc, double lambda,
-                                       T *__restrict__ Aq, const T *__restrict__ p, T gscale) {
-    using C = Bp30Layout<N, EPB_, T>;
+                                       T *__restrict__ Aq, const T *__restrict__ p, T gscale,
+                                       T *__restrict__ Mq = nullptr) {
+    using C = Bp30Layout<N, EPB_, T, MASS ? 4 : 3>;
     using B0 = typename C::B0;
     using B1 = typename C::B1;
     using B2 = typename C::B2;
@@ -141,6 +146,7 @@ __device__ __forceinline__ T bp30_core(T *smem, int64_t e0, int nel, const TG *_
         for (int l = 0; l < m; l++) x[l] = QG[B3::at(ca, cb, l)];
         eo_apply<m, m, -1, C::oDt>(x, ut);
         const TG *Ge = Gsrc + cel * 7 * MP + cr;
+        T w1[m];  // MASS: wJ qg of the column
 #pragma unroll
         for (int c = 0; c < m; c++) {
             const int s = B3::at(ca, cb, c);
@@ -152,11 +158,19 @@ __device__ __forceinline__ T bp30_core(T *smem, int64_t e0, int nel, const TG *_
             US[s] = g[1] * ur + g[3] * us + g[4] * ut[c];
             Rt[c] = g[2] * ur + g[4] * us + g[5] * ut[c];
             acc[c] = (lambda != 0.0) ? ((T)lambda * g[6]) * x[c] : T(0);
+            if (MASS) w1[c] = g[6] * x[c];
         }
         T y[m];
         eo_apply<m, m, -1, C::oDtT>(Rt, y);
 #pragma unroll
         for (int c = 0; c < m; c++) acc[c] += y[c];
+        if constexpr (MASS) {  // BP1.0: t-projection of wJ qg -> D
+            T y1[n];
+            eo_apply<n, m, 1, C::oIT>(w1, y1);
+            T *D = smem + cel * per + 3 * S;
+#pragma unroll
+            for (int l = 0; l < n; l++) D[B2::at(ca, cb, l)] = y1[l];
+        }
     }
     __syncthreads();
 
@@ -176,12 +190,26 @@ __device__ __forceinline__ T bp30_core(T *smem, int64_t e0, int nel, const TG *_
 #pragma unroll
         for (int l = 0; l < m; l++) US[B3::at(u, l, v)] = y[l];
     });
+    if constexpr (MASS) {  // BP1.0: s-projection (a, k), D -> A (the interpolated field is no longer read)
+        for_tasks<m * n, EPB>(nel, [&](int el, int r) {
+            const int a = r % m, k = r / m;
+            const T *D = smem + el * per + 3 * S;
+            T *X = smem + el * per;
+            T x[m], y[n];
+#pragma unroll
+            for (int l = 0; l < m; l++) x[l] = D[B2::at(a, l, k)];
+            eo_apply<n, m, 1, C::oIT>(x, y);
+#pragma unroll
+            for (int l = 0; l < n; l++) X[B1::at(a, l, k)] = y[l];
+        });
+    }
     __syncthreads();
 
-    // 7. column (a, b): sum of the three directions, t-projection -> X3 (A)
+    // 7. column (a, b): sum of the three directions, t-projection -> X3 (A;
+    // D when MASS, where A holds BP1.0's field)
     if (cact) {
         const T *UR = smem + cel * per + S, *US = smem + cel * per + 2 * S;
-        T *X3 = smem + cel * per;
+        T *X3 = smem + cel * per + (MASS ? 3 * S : 0);
         T y[n];
 #pragma unroll
         for (int c = 0; c < m; c++) {
@@ -194,10 +222,24 @@ __device__ __forceinline__ T bp30_core(T *smem, int64_t e0, int nel, const TG *_
     }
     __syncthreads();
 
-    // 8. s-projection (a, k): X3 (A) -> X4 (B)
+    // 8. s-projection (a, k): X3 (A, or D) -> X4 (B); MASS: BP1.0's
+    // r-projection (j, k), A -> Mq
+    if constexpr (MASS) {
+        for_tasks<n * n, EPB>(nel, [&](int el, int r) {
+            const T *X = smem + el * per;
+            const int j = r % n, k = r / n;
+            T x[m], y[n];
+#pragma unroll
+            for (int l = 0; l < m; l++) x[l] = X[B1::at(l, j, k)];
+            eo_apply<n, m, 1, C::oIT>(x, y);
+            T *o = Mq + (e0 + el) * NP + r * n;
+#pragma unroll
+            for (int l = 0; l < n; l++) o[l] = y[l];
+        });
+    }
     for_tasks<m * n, EPB>(nel, [&](int el, int r) {
         const int a = r % m, k = r / m;
-        const T *X3 = smem + el * per;
+        const T *X3 = smem + el * per + (MASS ? 3 * S : 0);
         T *X4 = smem + el * per + S;
         T x[m], y[n];
 #pragma unroll

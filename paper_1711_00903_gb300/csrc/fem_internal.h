@@ -59,6 +59,8 @@ cudaError_t launch_bp1(const fem_basis *b, int64_t E, const double *wJ, const do
                        double *Mq, cudaStream_t s);
 cudaError_t launch_bp35(const fem_basis *b, int64_t E, const double *G, double lambda,
                         const double *q, double *Aq, cudaStream_t s);
+cudaError_t launch_bp1_bp30(const fem_basis *b, int64_t E, const double *G, double lambda, const double *q,
+                            double *Mq, double *Aq, cudaStream_t s);
 cudaError_t launch_bp30(const fem_basis *b, int64_t E, const double *G, double lambda,
                         const double *q, double *Aq, cudaStream_t s);
 

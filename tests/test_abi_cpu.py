@@ -70,6 +70,7 @@ def test_argument_errors_need_no_gpu():
     assert L.fem_bp1_apply(None, 1, p, p, p, None) == fem.FEM_EINVAL
     assert L.fem_bp35_apply(None, 1, p, 1.0, p, p, None) == fem.FEM_EINVAL
     assert L.fem_bp30_apply(None, 1, p, 1.0, p, p, None) == fem.FEM_EINVAL
+    assert L.fem_bp1_bp30_apply(None, 1, p, 1.0, p, p, p, None) == fem.FEM_EINVAL
     for prec in (fem.FEM_PREC_F64, fem.FEM_PREC_F32, fem.FEM_PREC_F16G, 3, -1):
         assert L.fem_bp35_apply_ex(None, 1, prec, p, p, 1.0, p, p, None) == fem.FEM_EINVAL
         assert L.fem_bp30_apply_ex(None, 1, prec, p, p, 1.0, p, p, None) == fem.FEM_EINVAL

@@ -119,6 +119,27 @@ def test_bp30_parity(bases, N, lam):
 
 @pytest.mark.parametrize("lam", [0.0, 1.0, 0.37])
 @pytest.mark.parametrize("N", range(1, 16))
+def test_bp1_bp30_fused(bases, N, lam):
+    """BP1.0 and BP3.0 of one field in one pass: bit for bit the separate
+    kernels' outputs (BP1.0 with the seventh BP3.0 plane as wJ), and the
+    oracle's to 1e-12; Mq, Aq and q must be distinct buffers."""
+    fem, torch = _fem(), _torch()
+    v, q = _ops(N, E_RAGGED, lam)
+    b = bases[N]
+    G, _ = oracle.geofacs(N, oracle.KIND_BP30, v)
+    Gd, qd = _dev(G), _dev(q)
+    Mq, Aq = fem.fem_bp1_bp30_apply(b, Gd, lam, qd)
+    wJ = Gd[:, 6, :].contiguous()
+    assert torch.equal(Mq, fem.fem_bp1_apply(b, wJ, qd))
+    assert torch.equal(Aq, fem.fem_bp30_apply(b, Gd, lam, qd))
+    assert _rel(Mq.cpu().numpy(), oracle.bp1(N, np.ascontiguousarray(G[:, 6, :]), q)) < TOL
+    assert _rel(Aq.cpu().numpy(), oracle.bp30(N, G, lam, q)) < TOL
+    with pytest.raises(fem.FemError):
+        fem.fem_bp1_bp30_apply(b, Gd, lam, qd, out_m=Aq, out_a=Aq)
+
+
+@pytest.mark.parametrize("lam", [0.0, 1.0, 0.37])
+@pytest.mark.parametrize("N", range(1, 16))
 def test_bp30_point_layout_parity(bases, N, lam):
     """The point-per-thread layout of BP3.0 against the oracle, with a
     ragged element count (one element per block; above m^3 = 1024 points a
