@@ -5,7 +5,10 @@ One step = one pass of the whole path over the synthetic 32^3 jittered
 hex mesh (E = 32768, degree N = 7, lambda = 1):
   geometric factors for BP1.0 (wJ at Gauss points), BP3.5 (7 planes at GLL
   nodes) and BP3.0 (7 planes at Gauss points) from the element vertices,
-  then the BP1.0, BP3.5 and BP3.0 matvecs of one field q.
+  then the BP1.0, BP3.5 and BP3.0 matvecs of one field q, BP1.0 and BP3.0
+  in one pass that interpolates q to the Gauss points once for both
+  (fem_bp1_bp30_apply; the step with separate BP1.0 and BP3.0 launches is
+  timed as well and reported beside it).
 The degree-N basis (a few KB of tables) is built once before timing.
 value = 3 E (N+1)^3 DOFs per step (one field through each operator) / time.
 
@@ -37,16 +40,16 @@ import fem_synth  # noqa: E402
 
 WORKLOAD = "BP1.0+BP3.5+BP3.0 FP64 with geometric factors, 32x32x32 jittered hex mesh (E=32768), N=7, lambda=1"
 METRIC = "GDOF/s (BP1.0+BP3.5+BP3.0 step, FP64, N=7, E=32768)"
-KERNELS = ["geofacs_bp35", "geofacs_bp30_bp1", "bp1", "bp35", "bp30"]
+KERNELS = ["geofacs_bp35", "geofacs_bp30_bp1", "bp35", "bp1_bp30"]
 
 # Measured DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) per
 # element at N = 7, with the sha256 of the kernel source it was taken from;
 # a kernel whose source changed since reports traffic null.
 NCU_TRAFFIC = {
     # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on E = 4096:
-    # (184.08 + 10.54) MB over 4096 elements (profiles/fp64_operators_N7_E4096.md)
-    "bp30": {"N": 7, "bytes_per_elem": 47514, "sha": "9ad3f08aa3c59d9f",
-             "files": ["bp30.cu", "bp30_body.cuh", "eo.cuh", "kernels_common.cuh"]},
+    # (184.24 + 19.45) MB over 4096 elements (profiles/bp1_bp30_N7_E4096.md)
+    "bp1_bp30": {"N": 7, "bytes_per_elem": 49727, "sha": "17013c70541ae50d",
+                 "files": ["bp30.cu", "bp30_body.cuh", "eo.cuh", "kernels_common.cuh"]},
 }
 
 
@@ -107,6 +110,9 @@ def alg_counts(N: int):
         "bp1": (nn + m * n + mm) * (i_mn + i_nm) + m3,
         "bp35": 6 * nn * i_dd + n3 * (9 + lam_i + 2),
         "bp30": (nn + m * n + mm) * (i_mn + i_nm) + 6 * mm * i_gg + m3 * (9 + lam_i + 2),
+        # BP3.0 plus BP1.0's wJ scaling and its three projections (the
+        # interpolation is shared)
+        "bp1_bp30": (nn + m * n + mm) * (i_mn + 2 * i_nm) + 6 * mm * i_gg + m3 * (9 + lam_i + 2 + 1),
         "geofacs_bp30_bp1": 52 * m3 + 27 * mm,
         "geofacs_bp35": 52 * n3 + 27 * nn,
     }
@@ -115,6 +121,7 @@ def alg_counts(N: int):
         "bp1": 2 * interp + m3,
         "bp35": 12 * n ** 4 + 18 * n3,
         "bp30": 2 * interp + 12 * m ** 4 + 18 * m3,
+        "bp1_bp30": 3 * interp + 12 * m ** 4 + 18 * m3 + m3,
         "geofacs_bp30_bp1": 79 * m3 + 54 * mm,
         "geofacs_bp35": 79 * n3 + 54 * nn,
     }
@@ -125,6 +132,7 @@ def alg_counts(N: int):
         "bp1": 8 * (2 * n3 + m3),
         "bp35": 8 * (9 * n3),
         "bp30": 8 * (2 * n3 + 7 * m3),
+        "bp1_bp30": 8 * (3 * n3 + 7 * m3),  # q and the factors once, Mq and Aq
     }
     return std, inst, byts
 
@@ -151,6 +159,9 @@ def smem_counts(N: int, word: int = 8):
         "bp1": word * (2 * n ** 3 + 3 * m * n * n + 4 * m * m * n),
         "bp35": word * 17 * n ** 3,
         "bp30": word * (2 * n ** 3 + 3 * m * n * n + 4 * m * m * n + 16 * m ** 3),
+        # plus BP1.0's t-projection (stored, read back) and s-projection
+        # (stored, read back)
+        "bp1_bp30": word * (2 * n ** 3 + 5 * m * n * n + 6 * m * m * n + 16 * m ** 3),
     }
 
 
@@ -397,12 +408,18 @@ def run_ours(args):
         mark(1)
         fem.fem_mesh_geofacs_set(b, verts, wJ=wJ, G30=G30, stream=stream)
         mark(2)
-        fem.fem_bp1_apply(b, wJ, q, out=o1, stream=stream)
-        mark(3)
         fem.fem_bp35_apply(b, G35, lam, q, out=o35, stream=stream)
+        mark(3)
+        fem.fem_bp1_bp30_apply(b, G30, lam, q, out_m=o1, out_a=o30, stream=stream)
         mark(4)
+
+    def step_unfused():
+        # the same step with BP1.0 and BP3.0 as separate launches
+        fem.fem_mesh_geofacs_set(b, verts, G35=G35, stream=stream)
+        fem.fem_mesh_geofacs_set(b, verts, wJ=wJ, G30=G30, stream=stream)
+        fem.fem_bp1_apply(b, wJ, q, out=o1, stream=stream)
+        fem.fem_bp35_apply(b, G35, lam, q, out=o35, stream=stream)
         fem.fem_bp30_apply(b, G30, lam, q, out=o30, stream=stream)
-        mark(5)
 
     for _ in range(args.warmup):
         step()
@@ -427,6 +444,20 @@ def run_ours(args):
     ms = reduce_max(ms_local, world, device)
     per_kernel = {name: statistics.fmean(events[k][i].elapsed_time(events[k][i + 1]) for k in range(args.steps))
                   for i, name in enumerate(KERNELS)}
+
+    # the same step with separate BP1.0 and BP3.0 launches, for comparison
+    uf_steps = max(3, min(args.steps, 20))
+    for _ in range(3):
+        step_unfused()
+    torch.cuda.synchronize()
+    barrier(world, device)
+    u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    u0.record(stream)
+    for _ in range(uf_steps):
+        step_unfused()
+    u1.record(stream)
+    torch.cuda.synchronize()
+    ms_unfused = reduce_max(u0.elapsed_time(u1) / uf_steps, world, device)
 
     # end to end through the same calls: pinned host input -> device ->
     # step -> host output, every step.  Three streams: the host-to-device
@@ -462,9 +493,8 @@ def run_ours(args):
             stream.wait_event(d["out_done"])  # the outputs of step k-2 have left
         fem.fem_mesh_geofacs_set(b, d["verts"], G35=d["G35"], stream=stream)
         fem.fem_mesh_geofacs_set(b, d["verts"], wJ=d["wJ"], G30=d["G30"], stream=stream)
-        fem.fem_bp1_apply(b, d["wJ"], d["q"], out=d["o"][0], stream=stream)
         fem.fem_bp35_apply(b, d["G35"], lam, d["q"], out=d["o"][1], stream=stream)
-        fem.fem_bp30_apply(b, d["G30"], lam, d["q"], out=d["o"][2], stream=stream)
+        fem.fem_bp1_bp30_apply(b, d["G30"], lam, d["q"], out_m=d["o"][0], out_a=d["o"][2], stream=stream)
         d["computed"].record(stream)
         d2h_s.wait_event(d["computed"])
         with torch.cuda.stream(d2h_s):
@@ -500,9 +530,10 @@ def run_ours(args):
     kern = {}
     for name in KERNELS:
         t = per_kernel[name] / 1e3
+        ops = {"bp1": 1, "bp35": 1, "bp30": 1, "bp1_bp30": 2}.get(name)
         kern[name] = {
             "ms": per_kernel[name],
-            "gdofs": E * n ** 3 / t / 1e9 if name in ("bp1", "bp35", "bp30") else None,
+            "gdofs": ops * E * n ** 3 / t / 1e9 if ops else None,
             "alg_gbs": E * byts[name] / t / 1e9,
             "hbm_frac": E * byts[name] / t / 1e9 / hbm,
             "fp64_tflops": E * std[name] / t / 1e12,
@@ -595,6 +626,9 @@ def run_ours(args):
                                   "over two buffer sets: step k+1's inputs and step k-1's outputs move "
                                   "while step k's kernels run", "outputs_match_device_step": e2e_ok},
             "gpu_launches": len(KERNELS) * args.steps,
+            "step_unfused": {"ms_per_step": ms_unfused, "value": world * dofs / (ms_unfused / 1e3) / 1e9,
+                             "unit": "GDOF/s", "steps": uf_steps,
+                             "kernels": "the two factor sets, then BP1.0, BP3.5 and BP3.0 as separate launches"},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "clocks": clocks,

@@ -80,6 +80,11 @@ def test_direct_flop_counts():
     assert std["bp35"] == 2 * deriv_gll + 18 * n ** 3
     deriv_gauss = 3 * contract(m, m, m * m)
     assert std["bp30"] == 2 * interp + 2 * deriv_gauss + 18 * m ** 3
+    # BP1.0 and BP3.0 in one pass share the interpolation
+    assert std["bp1_bp30"] == std["bp1"] + std["bp30"] - interp
+    _, inst, byts = bench.alg_counts(N)
+    assert inst["bp1_bp30"] < inst["bp1"] + inst["bp30"]
+    assert byts["bp1_bp30"] == byts["bp1"] + byts["bp30"] - 8 * (n ** 3 + m ** 3)  # q and wJ read once
 
 
 def test_parse_degrees():
