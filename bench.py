@@ -702,12 +702,12 @@ def run_sweep(fem, torch, device, verts, args, sm_mhz):
         std, inst, byts = alg_counts(N)
         smem = smem_counts(N)
         row = {"N": N, "dofs": E * n ** 3}
-        for name, kind in (("bp1", 1), ("bp35", 2), ("bp30", 3), ("bp30_points", 3), ("bp35_f32", 2),
-                           ("bp30_f32", 3), ("bp35_f16", 2), ("bp30_f16", 3)):
+        for name, kind in (("bp1", 1), ("bp35", 2), ("bp30", 3), ("bp1_bp30", 3), ("bp30_points", 3),
+                           ("bp35_f32", 2), ("bp30_f32", 3), ("bp35_f16", 2), ("bp30_f16", 3)):
             f16 = name.endswith("_f16")
             f32 = name.endswith("_f32") or f16
             base = name[:-4] if f32 else name
-            ratio_base = "bp30" if base == "bp30_points" else base
+            ratio_base = "bp30" if base in ("bp30_points", "bp1_bp30") else base
             geo = torch.empty(fem.geo_shape(b, kind, E), dtype=torch.float64, device=device)
             fem.fem_mesh_geofacs(b, kind, verts, geo=geo, stream=stream)
             if f16:
@@ -725,6 +725,11 @@ def run_sweep(fem, torch, device, verts, args, sm_mhz):
                 fn = fem.fem_bp35_apply_f32 if base == "bp35" else fem.fem_bp30_apply_f32
                 ms = timed(lambda: fn(b, geo, lam, qx, out=o, stream=stream), reps)
                 del qx, o
+            elif name == "bp1_bp30":
+                out2 = torch.empty_like(q)
+                ms = timed(lambda: fem.fem_bp1_bp30_apply(b, geo, lam, q, out_m=out2, out_a=out, stream=stream),
+                           reps)
+                del out2
             elif name == "bp30_points":
                 ms = timed(lambda: fem.fem_bp30_apply_layout(b, geo, lam, q, fem.FEM_LAYOUT_POINTS, out=out,
                                                              stream=stream), reps)
@@ -756,11 +761,12 @@ def run_sweep(fem, torch, device, verts, args, sm_mhz):
             t = ms / 1e3
             gbs = T / t / 1e9
             copy_gbs = T / (copy_ms / 1e3) / 1e9
+            ops = 2 if name == "bp1_bp30" else 1  # the fused pass applies two operators
             row[name] = {
-                "ms": ms, "gdofs": E * n ** 3 / t / 1e9, "alg_gbs": gbs,
+                "ms": ms, "gdofs": ops * E * n ** 3 / t / 1e9, "alg_gbs": gbs,
                 "hbm_frac": gbs / hbm, "copy_gbs_at_size": copy_gbs, "copy_frac_at_size": gbs / copy_gbs,
                 "ratio_stream_gbs": ratio_gbs, "ratio_read_planes": k,
-                "hbm_bound_gdofs": copy_gbs / (per_elem / n ** 3),
+                "hbm_bound_gdofs": ops * copy_gbs / (per_elem / n ** 3),
                 "smem_frac": E * smem[base] * word // 8 / t / 1e9 / smem_peak_gbs(sm_mhz),
             }
             if not f32:
@@ -771,7 +777,8 @@ def run_sweep(fem, torch, device, verts, args, sm_mhz):
         b.free()
     del q_all
     torch.cuda.empty_cache()
-    return {"workload": f"BP1.0/BP3.5/BP3.0 FP64 (BP3.0 also in the point-per-thread layout; BP3.5/BP3.0 FP32 "
+    return {"workload": f"BP1.0/BP3.5/BP3.0 FP64 (BP3.0 also in the point-per-thread layout, and BP1.0 + BP3.0 "
+                        f"in one pass, whose GDOF/s count both operators' DOFs; BP3.5/BP3.0 FP32 "
                         f"with FP32 and FP16 factors, the mixed solvers' inner operators) sweep, E={E} jittered "
                         f"hexes, lambda=1, mean of {reps} launches per point",
             "copy_roofline": "device-to-device copy of T/2 bytes moving T = the operator's algorithmic "
