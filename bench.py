@@ -47,8 +47,8 @@ KERNELS = ["geofacs_bp35", "geofacs_bp30_bp1", "bp35", "bp1_bp30"]
 # a kernel whose source changed since reports traffic null.
 NCU_TRAFFIC = {
     # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on E = 4096:
-    # (184.24 + 19.45) MB over 4096 elements (profiles/bp1_bp30_N7_E4096.md)
-    "bp1_bp30": {"N": 7, "bytes_per_elem": 49727, "sha": "17013c70541ae50d",
+    # (184.09 + 19.08) MB over 4096 elements (profiles/bp1_bp30_N7_E4096.md)
+    "bp1_bp30": {"N": 7, "bytes_per_elem": 49602, "sha": "69854bce29b68910",
                  "files": ["bp30.cu", "bp30_body.cuh", "eo.cuh", "kernels_common.cuh"]},
 }
 
@@ -103,16 +103,16 @@ def alg_counts(N: int):
     i_nm, f_nm = eo_cost(n, m, 1)      # projection line
     i_dd, f_dd = eo_cost(n, n, -1)     # GLL derivative line
     i_gg, f_gg = eo_cost(m, m, -1)     # Gauss derivative line
-    lam_i, lam_f = 3, 3                # lambda * wJ * q and its accumulation
+    lam_i, lam_f = 2, 3                # wJ q, then one FMA with lambda into the sum
     fma_pts = 2 * (m * n3 + m * m * n * n + m3 * n) + 6 * m ** 4  # direct contractions of the point layout
     inst = {
-        "bp30_points": fma_pts + m3 * (9 + lam_i + 2),
+        "bp30_points": fma_pts + m3 * (9 + 3 + 2),  # (lambda wJ) q as two products
         "bp1": (nn + m * n + mm) * (i_mn + i_nm) + m3,
         "bp35": 6 * nn * i_dd + n3 * (9 + lam_i + 2),
         "bp30": (nn + m * n + mm) * (i_mn + i_nm) + 6 * mm * i_gg + m3 * (9 + lam_i + 2),
-        # BP3.0 plus BP1.0's wJ scaling and its three projections (the
-        # interpolation is shared)
-        "bp1_bp30": (nn + m * n + mm) * (i_mn + 2 * i_nm) + 6 * mm * i_gg + m3 * (9 + lam_i + 2 + 1),
+        # BP3.0 plus BP1.0's three projections (the interpolation and the
+        # wJ scaling are shared)
+        "bp1_bp30": (nn + m * n + mm) * (i_mn + 2 * i_nm) + 6 * mm * i_gg + m3 * (9 + lam_i + 2),
         "geofacs_bp30_bp1": 52 * m3 + 27 * mm,
         "geofacs_bp35": 52 * n3 + 27 * nn,
     }

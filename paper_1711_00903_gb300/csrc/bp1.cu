@@ -98,7 +98,7 @@ bp1_f64_kernel(int64_t E, const double *__restrict__ wJ, const double *__restric
         for (int l = 0; l < n; l++) x[l] = X2[B2::at(a, b, l)];
         eo_apply<m, n, 1, C::oI>(x, g);
 #pragma unroll
-        for (int c = 0; c < m; c++) g[c] *= __ldg(we + c * m * m);
+        for (int c = 0; c < m; c++) g[c] = mul_rn(g[c], __ldg(we + c * m * m));
         eo_apply<n, m, 1, C::oIT>(g, y);
 #pragma unroll
         for (int l = 0; l < n; l++) X2[B2::at(a, b, l)] = y[l];

@@ -146,7 +146,7 @@ __device__ __forceinline__ T bp30_core(T *smem, int64_t e0, int nel, const TG *_
         for (int l = 0; l < m; l++) x[l] = QG[B3::at(ca, cb, l)];
         eo_apply<m, m, -1, C::oDt>(x, ut);
         const TG *Ge = Gsrc + cel * 7 * MP + cr;
-        T w1[m];  // MASS: wJ qg of the column
+        T w1[m];  // MASS: wJ qg of the column (BP1.0's field)
 #pragma unroll
         for (int c = 0; c < m; c++) {
             const int s = B3::at(ca, cb, c);
@@ -157,13 +157,15 @@ __device__ __forceinline__ T bp30_core(T *smem, int64_t e0, int nel, const TG *_
             UR[s] = g[0] * ur + g[1] * us + g[2] * ut[c];
             US[s] = g[1] * ur + g[3] * us + g[4] * ut[c];
             Rt[c] = g[2] * ur + g[4] * us + g[5] * ut[c];
-            acc[c] = (lambda != 0.0) ? ((T)lambda * g[6]) * x[c] : T(0);
-            if (MASS) w1[c] = g[6] * x[c];
+            acc[c] = (T)lambda * g[6];  // lambda wJ, applied below
+            if (MASS) w1[c] = mul_rn(g[6], x[c]);
         }
         T y[m];
         eo_apply<m, m, -1, C::oDtT>(Rt, y);
+        // t-transpose plus the lambda wJ qg term (qg re-read from the box)
 #pragma unroll
-        for (int c = 0; c < m; c++) acc[c] += y[c];
+        for (int c = 0; c < m; c++)
+            acc[c] = (lambda != 0.0) ? fmx(acc[c], QG[B3::at(ca, cb, c)], y[c]) : y[c];
         if constexpr (MASS) {  // BP1.0: t-projection of wJ qg -> D
             T y1[n];
             eo_apply<n, m, 1, C::oIT>(w1, y1);

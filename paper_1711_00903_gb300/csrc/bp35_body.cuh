@@ -94,12 +94,12 @@ __device__ __forceinline__ T bp35_core(T *smem, int64_t e0, int nel, const TG *_
             sR[s] = g[0] * qr + g[1] * qs + g[2] * qt[k];
             sS[s] = g[1] * qr + g[3] * qs + g[4] * qt[k];
             Rt[k] = g[2] * qr + g[4] * qs + g[5] * qt[k];
-            acc[k] = (lambda != 0.0) ? (lam * g[6]) * sQ[s] : T(0);
+            acc[k] = g[6] * sQ[s];  // wJ q
         }
         T y[n];
         eo_apply<n, n, -1, C::oDT>(Rt, y);
 #pragma unroll
-        for (int k = 0; k < n; k++) acc[k] += y[k];
+        for (int k = 0; k < n; k++) acc[k] = (lambda != 0.0) ? fmx(lam, acc[k], y[k]) : y[k];
     }
     __syncthreads();
 

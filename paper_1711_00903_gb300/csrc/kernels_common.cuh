@@ -164,6 +164,13 @@ __device__ __forceinline__ T factor_unscale(const double *ginv) { return ginv ? 
 __device__ __forceinline__ double fmx(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmx(float a, float b, float c) { return fmaf(a, b, c); }
 
+// A product rounded on its own, never contracted into a later addition: the
+// kernels that must give bit-identical results (BP1.0 alone and inside the
+// one-pass BP1.0 + BP3.0 kernel) round wJ q the same way whatever the
+// compiler fuses around it.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+
 // Copies `count` doubles from global to shared with all threads of the block.
 __device__ __forceinline__ void block_copy(double *dst, const double *__restrict__ src, int count) {
     for (int t = threadIdx.x; t < count; t += blockDim.x) dst[t] = __ldg(src + t);
