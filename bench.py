@@ -507,16 +507,22 @@ def run_ours(args):
         e2e_step(k)
     torch.cuda.synchronize()
     barrier(world, device)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    h2d_s.wait_event(e0)
-    d2h_s.wait_event(e0)
-    for k in range(e2e_steps):
-        e2e_step(k)
-    stream.wait_event(sets[(e2e_steps - 1) % 2]["out_done"])
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = reduce_max(e0.elapsed_time(e1) / e2e_steps, world, device)
+    # five windows of e2e_steps steps each; the host copies share the host's
+    # memory system with other work on the machine and now and then stall
+    # for a few ms, so the median window is reported (all five are listed)
+    windows = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h2d_s.wait_event(e0)
+        d2h_s.wait_event(e0)
+        for k in range(e2e_steps):
+            e2e_step(k)
+        stream.wait_event(sets[(e2e_steps - 1) % 2]["out_done"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        windows.append(reduce_max(e0.elapsed_time(e1) / e2e_steps, world, device))
+    e2e_ms = statistics.median(windows)
     # the step's output agrees with the single-stream step (same kernels)
     e2e_ok = all(torch.equal(a.to(device), c) for a, c in zip(sets[(e2e_steps - 1) % 2]["out"], (o1, o35, o30)))
     del sets
@@ -622,6 +628,7 @@ def run_ours(args):
                     "h2d_bytes_per_step": int(verts_h.nbytes + q_h.nbytes),
                     "d2h_bytes_per_step": int(3 * q_h.nbytes),
                     "ms_per_step": e2e_ms, "steps": e2e_steps,
+                    "windows_ms_per_step": windows, "reported": "median of the five windows",
                     "pipelining": "host-to-device copies, kernels and device-to-host copies on three streams "
                                   "over two buffer sets: step k+1's inputs and step k-1's outputs move "
                                   "while step k's kernels run", "outputs_match_device_step": e2e_ok},
