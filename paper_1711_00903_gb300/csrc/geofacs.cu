@@ -28,13 +28,26 @@ struct GeoCfg {
     static constexpr int smem = (2 * pad2(qn) + EPB * pad2(24 + 9 * qq + SD)) * 8;
 };
 
-// 1 / d in FP64: an FP32 reciprocal seed (24 bits) refined by two Newton
-// steps r <- r + r (1 - d r), each doubling the correct bits (48, then the
-// full 53).  Falls back to a division when d is outside the FP32 range.
+// 1 / d in FP64: an FP32 reciprocal seed refined by two Newton steps
+// r <- r + r (1 - d r), each doubling the correct bits (about 22, 44, then
+// the full 53).  The seed's conversions between the IEEE binary64 and
+// binary32 formats are done on the bit fields with integer operations
+// (sign; exponent rebiased from 1023 to 127; the top 23 mantissa bits,
+// truncated), so the FP64 pipe, the part's bottleneck, executes only the
+// four FMAs.  Falls back to a division when |d| is outside 2^-120..2^121,
+// where the seed or its reciprocal would leave the binary32 normal range.
 __device__ __forceinline__ double recip(double d) {
-    const float df = __double2float_rn(d);
-    if (!(fabsf(df) > 1e-37f && fabsf(df) < 1e37f)) return 1.0 / d;
-    double r = (double)__frcp_rn(df);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned hi = (unsigned)(b >> 32);
+    const int ex = (int)((hi >> 20) & 0x7FFu) - 1023;  // unbiased binary64 exponent
+    if (ex < -120 || ex > 120) return 1.0 / d;
+    const unsigned fb = (hi & 0x80000000u) | ((unsigned)(ex + 127) << 23) | ((hi & 0xFFFFFu) << 3) |
+                        (unsigned)((b >> 29) & 0x7u);
+    const unsigned rb = __float_as_uint(__frcp_rn(__uint_as_float(fb)));
+    const int rex = (int)((rb >> 23) & 0xFFu) - 127;   // unbiased binary32 exponent of the seed
+    const unsigned rhi = (rb & 0x80000000u) | ((unsigned)(rex + 1023) << 20) | ((rb & 0x7FFFFFu) >> 3);
+    double r = __longlong_as_double((long long)(((unsigned long long)rhi << 32) |
+                                                ((unsigned long long)(rb & 0x7u) << 29)));
     double e = fma(-d, r, 1.0);
     r = fma(r, e, r);
     e = fma(-d, r, 1.0);
