@@ -675,26 +675,32 @@ def run_sweep(fem, torch, device, verts, args, sm_mhz):
     the paper does (Section 5): a device-to-device copy of half the
     operator's algorithmic bytes (a copy of T/2 bytes moves T), and the
     library's calibration stream with the operator's read:write ratio (k
-    planes read, their sum written).  Each figure is the mean of `reps` launches timed with CUDA
-    events after two warm-up launches; every input is larger than L2 from
-    N = 2 on (at N = 1 the BP3.5 factors, 14.7 MB, fit in L2 and the figure
-    is an upper bound)."""
+    planes read, their sum written).  Each figure is the median of `reps`
+    launches timed with CUDA events after two warm-up launches, each launch
+    preceded (outside its events) by a 258 MB write that evicts L2, so that
+    the low degrees, whose arrays would fit in L2, are timed cold too."""
     stream = torch.cuda.current_stream(device)
     E = verts.shape[0]
     lam, reps = 1.0, args.sweep_reps
     hbm, _, _ = _peaks()
     rows = []
 
+    # a write of twice the L2 size before every timed launch, outside its
+    # events: each launch starts from a cold L2, also at the low degrees
+    # whose arrays would otherwise stay resident between launches
+    flush = torch.empty(2 * 129 * 2 ** 20, dtype=torch.uint8, device=device)
+
     def timed(fn, count):
         for _ in range(2):
             fn()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(count + 1)]
-        ev[0].record(stream)
-        for i in range(count):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(count)]
+        for a, b_ in ev:
+            flush.zero_()
+            a.record(stream)
             fn()
-            ev[i + 1].record(stream)
+            b_.record(stream)
         torch.cuda.synchronize()
-        return statistics.fmean(ev[i].elapsed_time(ev[i + 1]) for i in range(count))
+        return statistics.median(a.elapsed_time(b_) for a, b_ in ev)
 
     degrees = parse_degrees(args.sweep)
     if not degrees:
@@ -787,7 +793,7 @@ def run_sweep(fem, torch, device, verts, args, sm_mhz):
     return {"workload": f"BP1.0/BP3.5/BP3.0 FP64 (BP3.0 also in the point-per-thread layout, and BP1.0 + BP3.0 "
                         f"in one pass, whose GDOF/s count both operators' DOFs; BP3.5/BP3.0 FP32 "
                         f"with FP32 and FP16 factors, the mixed solvers' inner operators) sweep, E={E} jittered "
-                        f"hexes, lambda=1, mean of {reps} launches per point",
+                        f"hexes, lambda=1, median of {reps} launches per point, L2 evicted before each",
             "copy_roofline": "device-to-device copy of T/2 bytes moving T = the operator's algorithmic "
                              "bytes, recalibrated at every N (Section 5 of the paper)",
             "rows": rows}
@@ -1045,7 +1051,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sweep", default="1-15",
                     help="degrees of the per-N operator sweep (e.g. 1-15 or 3,7,11)")
-    ap.add_argument("--sweep-reps", type=int, default=5)
+    ap.add_argument("--sweep-reps", type=int, default=20)
     ap.add_argument("--no-sweep", action="store_true", help="skip the per-N operator sweep")
     ap.add_argument("--no-pcg", action="store_true", help="skip the Helmholtz solve measurement")
     ap.add_argument("--pcg-solves", type=int, default=3)
