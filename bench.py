@@ -47,7 +47,7 @@ KERNELS = ["geofacs_bp35", "geofacs_bp30_bp1", "bp35", "bp1_bp30"]
 # a kernel whose source changed since reports traffic null.
 NCU_TRAFFIC = {
     # ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on E = 4096:
-    # (184.09 + 19.08) MB over 4096 elements (profiles/bp1_bp30_N7_E4096.md)
+    # (184.09 + 19.08) MB over 4096 elements, ncu capture of the one-pass kernel at N = 7
     "bp1_bp30": {"N": 7, "bytes_per_elem": 49602, "sha": "69854bce29b68910",
                  "files": ["bp30.cu", "bp30_body.cuh", "eo.cuh", "kernels_common.cuh"]},
 }
@@ -640,18 +640,98 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "clocks": clocks,
             "kernels": kern,
-            "sweep": sweep,
-            "small_case": small,
-            "pcg": pcg,
-            "batch": batch,
-            "serve": serve,
         }
-        print(json.dumps(line))
+        sections = {"sweep": sweep, "small_case": small, "pcg": pcg, "batch": batch, "serve": serve}
+        emit(line, sections, args.sections_out)
     b.free()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+HEADLINE_MAX_BYTES = 4096
+
+
+def _r(x, digits=4):
+    """x rounded to `digits` significant figures (floats only; containers
+    recursively), to keep the headline line short."""
+    if isinstance(x, float):
+        return float(f"{x:.{digits}g}")
+    if isinstance(x, dict):
+        return {k: _r(v, digits) for k, v in x.items()}
+    if isinstance(x, list):
+        return [_r(v, digits) for v in x]
+    return x
+
+
+def headline_summary(sections):
+    """A few figures of the side sections for the headline: the Helmholtz
+    solves at 1e-13 (where the mixed solves reach the FP64 solution to
+    1e-10), the batch and the serving measurement."""
+    out = {}
+    pcg = sections.get("pcg")
+    if pcg:
+        t = pcg.get("tight", {})
+        out["pcg_tol_1e-13"] = {k: {"solves_per_s": v.get("solves_per_s"),
+                                    "rel_diff_vs_fp64_solve": v.get("rel_diff_vs_fp64_solve"),
+                                    "rel_err_vs_u_I": v.get("rel_err_vs_u_I")}
+                                for k, v in t.items() if isinstance(v, dict)}
+        for k, v in t.items():
+            if k.endswith("_speedup"):
+                out["pcg_tol_1e-13"][k] = v
+    b = sections.get("batch")
+    if b:
+        out["batch_gdofs"] = {"separate": b["separate_launches"]["gdofs"],
+                              "persistent_tuned": b["persistent_tuned"]["gdofs"], "graph": b["graph"]["gdofs"]}
+    sv = sections.get("serve")
+    if sv:
+        cb = sv.get("steady_state") or sv.get("continuous_batching_8_slots") or {}
+        out["serve"] = {k: cb.get(k) for k in ("offered_per_s", "solves_per_s", "p50_s", "p99_s") if k in cb}
+    return out
+
+
+def compact_headline(line, sections):
+    """The last stdout line: the contract's keys and the roofline, rounded,
+    with the side sections reduced to a few figures."""
+    keep_kern = ("ms", "gdofs", "alg_gbs", "hbm_frac", "fp64_tflops", "fp64_issue_frac", "smem_frac")
+    head = dict(line)
+    head["kernels"] = {k: {f: v.get(f) for f in keep_kern} for k, v in line.get("kernels", {}).items()}
+    rf = dict(line.get("roofline") or {})
+    for long_key in ("fp64_probe", "flop_count"):
+        rf.pop(long_key, None)
+    if isinstance(rf.get("smem"), dict):
+        rf["smem"] = {k: rf["smem"][k] for k in ("achieved_gbs", "peak_gbs", "frac") if k in rf["smem"]}
+    head["roofline"] = rf
+    e2e = dict(line.get("e2e") or {})
+    e2e.pop("pipelining", None)
+    head["e2e"] = e2e
+    head["summary"] = headline_summary(sections)
+    head["sections"] = [k for k, v in sections.items() if v is not None]
+    head = _r(head)
+    if len(json.dumps(head)) > HEADLINE_MAX_BYTES:  # drop detail, never the contract's keys
+        head.pop("kernels", None)
+        head.pop("summary", None)
+    return head
+
+
+def emit(line, sections, sections_out=None):
+    """Prints every side section as its own JSON line ({"section": name,
+    ...}), then the compact headline as the last line.  With sections_out,
+    the sections and the full headline also go to that file as one JSON
+    document."""
+    for name, data in sections.items():
+        if data is not None:
+            print(json.dumps({"section": name, **data}))
+    head = compact_headline(line, sections)
+    if sections_out:
+        os.makedirs(os.path.dirname(os.path.abspath(sections_out)), exist_ok=True)
+        with open(sections_out, "w") as f:
+            json.dump({"headline": line, "sections": sections}, f, indent=1)
+    sys.stdout.flush()
+    print(json.dumps(head))
+    sys.stdout.flush()
+    return head
 
 
 def parse_degrees(spec: str):
@@ -1058,6 +1138,8 @@ def main(argv=None):
     ap.add_argument("--pcg-modes", default="fp64,mixed,mixed16",
                     help="solver modes of the Helmholtz measurement (comma list of fp64, mixed, mixed16)")
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-order batch measurement")
+    ap.add_argument("--sections-out", default=None,
+                    help="also write the side sections and the full headline to this JSON file")
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the Poisson-arrival serving measurement (0 skips it)")
     args = ap.parse_args(argv)

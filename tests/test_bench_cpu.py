@@ -90,3 +90,80 @@ def test_direct_flop_counts():
 def test_parse_degrees():
     assert bench.parse_degrees("1-3,7, 11") == [1, 2, 3, 7, 11]
     assert bench.parse_degrees("") == []
+
+
+def _fake_run():
+    """A full result of the shape run_ours produces (every side section
+    filled, a 15-degree sweep of nine operator columns), with made-up
+    numbers: what matters here is the size and the keys."""
+    col = {"ms": 1.2345678, "gdofs": 12.345678, "alg_gbs": 5432.1, "hbm_frac": 0.8123, "copy_gbs_at_size": 6012.3,
+           "copy_frac_at_size": 0.9, "ratio_stream_gbs": 6100.0, "ratio_read_planes": 8, "hbm_bound_gdofs": 80.0,
+           "smem_frac": 0.4, "fp64_tflops": 1.1, "fp64_issue_frac": 0.7}
+    names = ("bp1", "bp35", "bp30", "bp1_bp30", "bp30_points", "bp35_f32", "bp30_f32", "bp35_f16", "bp30_f16")
+    sweep = {"workload": "x" * 300, "copy_roofline": "y" * 150,
+             "rows": [dict({"N": N, "dofs": 32768 * (N + 1) ** 3}, **{k: dict(col) for k in names})
+                      for N in range(1, 16)]}
+    kern = {k: {"ms": 1.0, "gdofs": 10.0, "alg_gbs": 400.0, "hbm_frac": 0.06, "fp64_tflops": 1.3,
+                "fp64_frac": 1.05, "fp64_issue_frac": 0.8, "smem_frac": 0.3} for k in bench.KERNELS}
+    line = {"metric": bench.METRIC, "value": 4.86123456789, "unit": "GDOF/s", "n_gpus": 1, "steps": 20,
+            "warmup": 5, "ms_per_step": 10.3512345, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": bench.step_config(32768, 7, 1.0, 1),
+            "e2e": {"value": 4.8, "unit": "GDOF/s", "h2d_bytes_per_step": 14155776, "d2h_bytes_per_step": 40265728,
+                    "ms_per_step": 10.49, "steps": 20, "windows_ms_per_step": [10.4, 10.5, 10.49, 10.6, 10.45],
+                    "reported": "median of the five windows", "pipelining": "z" * 200,
+                    "outputs_match_device_step": True},
+            "gpu_launches": 80,
+            "step_unfused": {"ms_per_step": 11.3, "value": 4.4, "unit": "GDOF/s", "steps": 20, "kernels": "k" * 80},
+            "roofline": {"kernel": "bp1_bp30", "bound": "alu", "unit": "TFLOP/s", "achieved": 1.326, "peak": 1.259,
+                         "frac": 1.05, "peak_source": "p" * 100, "flop_count": "f" * 150, "fp64_issue_frac": 0.8,
+                         "fp64_probe_tflops": 1.057, "fp64_issue_frac_of_probe": 0.95, "fp64_probe": "q" * 120,
+                         "traffic": 1625391104,
+                         "hbm": {"achieved_gbs": 378.0, "peak_gbs": 6780.0, "peak_source": "measured", "frac": 0.056},
+                         "smem": {"bytes_per_elem": 100000, "achieved_gbs": 7000.0, "peak_gbs": 40000.0, "frac": 0.2,
+                                  "peak_source": "s" * 100}},
+            "cpu_baseline": {"value": 0.11, "unit": "GDOF/s", "cores": 16, "kind": "oracle", "sample": "c" * 150,
+                             "single_thread": {"value": 0.01, "unit": "GDOF/s", "cores": 1, "sample": "d" * 80},
+                             "host": "aarch64, Neoverse-V2"},
+            "clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "power_w_max": 800.0, "samples": 300, "reasons": []},
+            "kernels": kern}
+    tight = {"tol": 1e-13}
+    for k in ("fp64", "mixed", "mixed16", "mixed_tc"):
+        tight[k] = {"solves_per_s": 4.0, "iters": 1000, "outer": 6, "relres": 7e-14, "status": 0,
+                    "rel_err_vs_u_I": 2e-12, "rel_diff_vs_fp64_solve": 5e-12}
+        tight[k + "_speedup"] = 7.9
+    pcg = {"workload": "w" * 200, "tight": tight, "fp64": dict(tight["fp64"])}
+    batch = {"workload": "b" * 150, "dofs_per_pass": 10 ** 8, "separate_launches": {"ms": 30.0, "gdofs": 3.0},
+             "persistent_default": {"ms": 25.0, "gdofs": 4.0}, "persistent_tuned": {"ms": 20.0, "gdofs": 5.0,
+                                                                                     "config": {"threads": 256}},
+             "graph": {"ms": 20.0, "gdofs": 5.0}, "tuner_candidates": 32}
+    serve = {"workload": "s" * 200, "steady_state": {"offered_per_s": 200.0, "solves_per_s": 15.0, "p50_s": 1.0,
+                                                      "p99_s": 3.0, "queue_depth": list(range(300))}}
+    return line, {"sweep": sweep, "small_case": {"us_per_launch_graph": 3.0}, "pcg": pcg, "batch": batch,
+                  "serve": serve}
+
+
+def test_headline_is_last_and_compact(capsys, tmp_path):
+    """The last stdout line carries the contract's keys in a few KB; every
+    side section comes before it on a line of its own, and the side file
+    holds the full result."""
+    line, sections = _fake_run()
+    side = tmp_path / "sections.json"
+    bench.emit(line, sections, str(side))
+    out = capsys.readouterr().out.strip().splitlines()
+    assert len(out) == 1 + sum(v is not None for v in sections.values())
+    head = json.loads(out[-1])
+    assert len(out[-1]) <= bench.HEADLINE_MAX_BYTES
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "e2e", "gpu_launches", "roofline",
+              "cpu_baseline", "clocks"):
+        assert k in head, k
+    assert head["e2e"]["h2d_bytes_per_step"] == 14155776 and head["e2e"]["d2h_bytes_per_step"] == 40265728
+    for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "fp64_issue_frac"):
+        assert k in head["roofline"], k
+    assert head["summary"]["pcg_tol_1e-13"]["mixed_tc"]["rel_diff_vs_fp64_solve"] == 5e-12
+    assert head["summary"]["serve"]["offered_per_s"] == 200.0
+    for ln in out[:-1]:
+        assert json.loads(ln)["section"] in sections
+    full = json.loads(side.read_text())
+    assert len(full["sections"]["sweep"]["rows"]) == 15
