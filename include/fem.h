@@ -225,6 +225,20 @@ int fem_bp30_apply_layout(const fem_basis *b, int64_t E, const double *G, double
 int fem_bp30_apply_f32(const fem_basis *b, int64_t E, const float *G, double lambda,
                        const float *q, float *Aq, void *stream);
 
+/* BP3.0 matvec (Algorithm 5) with its twelve 1D contractions on the tensor
+ * cores: mma.sync m16n8k16 with f16 operands and FP32 accumulation, FP32
+ * factors and vectors; the inner operator of FEM_PCG_MIXED_TC.  Every
+ * contraction line is scaled by a power of two into the f16 range and
+ * split into a high and a low f16 part, and the operator entries likewise,
+ * so that three products on one K axis give about 2^-22 relative accuracy
+ * (one f16 product gives 2^-11, too coarse for the solver's correction
+ * equation).  Layouts as fem_bp30_apply_f32: G device E*7*m^3 floats, q
+ * and Aq device E*n^3 floats, 16-byte aligned, Aq != q; E <= 2^31 - 1 (one
+ * block per element).  Asynchronous on stream, allocates nothing.
+ * Errors: FEM_EINVAL, FEM_ECUDA. */
+int fem_bp30_apply_tc(const fem_basis *b, int64_t E, const float *G, double lambda,
+                      const float *q, float *Aq, void *stream);
+
 /* BP1.0 and BP3.0 of one field in one pass (Algorithms 3 and 5): the
  * interpolation of q to the Gauss points is computed once for both, and
  * BP1.0's wJ is the seventh plane of G (the same w |J| at the same points,
@@ -242,6 +256,8 @@ int fem_bp1_bp30_apply(const fem_basis *b, int64_t E, const double *G, double la
 #define FEM_PREC_F32 1  /* FP32 factors, vectors and arithmetic (fem_bp*_apply_f32) */
 #define FEM_PREC_F16G 2 /* binary16 factors scaled by a power of two, FP32 vectors and
                          * arithmetic (fem_bp*_apply_f16g) */
+#define FEM_PREC_F16TC 3 /* FP32 factors and vectors, contractions on the tensor cores
+                          * (fem_bp30_apply_tc; BP3.0 only) */
 
 /* BP3.5 and BP3.0 matvecs with the precision chosen at run time: each call
  * is the precision's own entry point above, with G, q and Aq of that

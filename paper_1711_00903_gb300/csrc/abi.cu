@@ -106,6 +106,19 @@ int fem_basis_setup(int N, fem_basis **out) {
         return e == cudaErrorMemoryAllocation ? FEM_ENOMEM : cuda_fail(e);
     }
     e = cudaMemcpy(b->d_ops, table, sizeof(double) * L.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {  // B fragments of the tensor-core operators
+        const int64_t words = fem::tc_table_words(N);
+        uint32_t *tc = new (std::nothrow) uint32_t[words];
+        if (!tc) {
+            cudaFree(b->d_ops);
+            delete b;
+            return FEM_ENOMEM;
+        }
+        fem::build_tc_table(h, tc);
+        e = cudaMalloc(&b->d_tc, sizeof(uint32_t) * words);
+        if (e == cudaSuccess) e = cudaMemcpy(b->d_tc, tc, sizeof(uint32_t) * words, cudaMemcpyHostToDevice);
+        delete[] tc;
+    }
     if (e == cudaSuccess) e = fem::prepare_bp1(N, fem::fold_table());
     if (e == cudaSuccess) e = fem::prepare_bp35(N, fem::fold_table());
     if (e == cudaSuccess) e = fem::prepare_bp30(N, fem::fold_table());
@@ -113,8 +126,10 @@ int fem_basis_setup(int N, fem_basis **out) {
     if (e == cudaSuccess) e = fem::prepare_bp30_point(N);
     if (e == cudaSuccess) e = fem::prepare_bp35_f16(N, fem::fold_table());
     if (e == cudaSuccess) e = fem::prepare_bp30_f16(N, fem::fold_table());
+    if (e == cudaSuccess) e = fem::prepare_bp30_tc(N);
     if (e != cudaSuccess) {
         cudaFree(b->d_ops);
+        if (b->d_tc) cudaFree(b->d_tc);
         delete b;
         return cuda_fail(e);
     }
@@ -125,6 +140,7 @@ int fem_basis_setup(int N, fem_basis **out) {
 void fem_basis_free(fem_basis *b) {
     if (!b) return;
     if (b->d_ops) cudaFree(b->d_ops);
+    if (b->d_tc) cudaFree(b->d_tc);
     delete b;
 }
 
@@ -302,6 +318,16 @@ int fem_bp30_apply_f32(const fem_basis *b, int64_t E, const float *G, double lam
     return e == cudaSuccess ? FEM_OK : cuda_fail(e);
 }
 
+int fem_bp30_apply_tc(const fem_basis *b, int64_t E, const float *G, double lambda, const float *q, float *Aq,
+                      void *stream) {
+    if (!b || E < 0) return FEM_EINVAL;
+    if (E == 0) return FEM_OK;
+    if (!G || !q || !Aq || !aligned16(G) || !aligned16(q) || !aligned16(Aq)) return FEM_EINVAL;
+    if ((const void *)Aq == (const void *)q || E > (int64_t)0x7fffffff) return FEM_EINVAL;
+    cudaError_t e = fem::launch_bp30_tc(b, E, G, lambda, q, Aq, (cudaStream_t)stream);
+    return e == cudaSuccess ? FEM_OK : cuda_fail(e);
+}
+
 int fem_bp30_apply(const fem_basis *b, int64_t E, const double *G, double lambda, const double *q,
                    double *Aq, void *stream) {
     const int c = check_apply(b, E, G, b ? 7 * cube(b->host.m) : 0, q, Aq);
@@ -344,6 +370,8 @@ int fem_bp30_apply_ex(const fem_basis *b, int64_t E, int prec, const void *G, co
             return fem_bp30_apply_f32(b, E, (const float *)G, lambda, (const float *)q, (float *)Aq, stream);
         case FEM_PREC_F16G:
             return fem_bp30_apply_f16g(b, E, G, ginv, lambda, (const float *)q, (float *)Aq, stream);
+        case FEM_PREC_F16TC:
+            return fem_bp30_apply_tc(b, E, (const float *)G, lambda, (const float *)q, (float *)Aq, stream);
         default:
             return FEM_EINVAL;
     }

@@ -47,6 +47,7 @@ bool compute_basis(int N, HostBasis *hb);
 struct fem_basis {
     fem::HostBasis host;
     double *d_ops;  // device copy of I, D, Dt (fem::OpsLayout)
+    void *d_tc;     // device table of the tensor-core operators' B fragments (tc_layout.h)
     int device;
 };
 
@@ -107,6 +108,15 @@ cudaError_t prepare_bp30_f16(int N, const double *fold_table);
 cudaError_t launch_bp30_pcg_f32(const fem_basis *b, int64_t E, const float *G, double lambda, const float *z,
                                 float *p, const double *beta, float *Ap, double *partials, cudaStream_t s);
 int64_t bp30_f16_blocks(int N, int64_t E);
+// tensor-core BP3.0 (FEM_PCG_MIXED_TC): FP32 data, f16 split contractions
+int64_t tc_table_words(int N);
+void build_tc_table(const HostBasis &h, uint32_t *words);
+cudaError_t prepare_bp30_tc(int N);
+cudaError_t launch_bp30_tc(const fem_basis *b, int64_t E, const float *G, double lambda, const float *q, float *Aq,
+                           cudaStream_t s);
+cudaError_t launch_bp30_pcg_tc(const fem_basis *b, int64_t E, const float *G, double lambda, const float *z,
+                               float *p, const double *beta, float *Ap, double *partials, cudaStream_t s);
+int64_t bp30_tc_blocks(int64_t E);
 int64_t bp30_blocks(int N, int64_t E, bool f32);
 
 // FP32 BP3.5 matvec (the inner operator of the mixed-precision solver).
