@@ -210,6 +210,10 @@ int fem_bp30_apply_f16g(const fem_basis *b, int64_t E, const void *G16, const do
  *                    one element per block, operators in shared memory. */
 #define FEM_LAYOUT_LINES 0
 #define FEM_LAYOUT_POINTS 1
+/* FEM_LAYOUT_WARP    two-dimensional lines as FEM_LAYOUT_LINES, one warp
+ *                    (two or four above N = 9) per element and no block
+ *                    barrier between the phases (FP32 BP3.0 only). */
+#define FEM_LAYOUT_WARP 2
 
 /* fem_bp30_apply with a chosen thread layout (same arguments, layouts and
  * errors; FEM_EINVAL for an unknown layout).  Both layouts compute the same
@@ -224,6 +228,14 @@ int fem_bp30_apply_layout(const fem_basis *b, int64_t E, const double *G, double
  * Errors: FEM_EINVAL, FEM_ECUDA. */
 int fem_bp30_apply_f32(const fem_basis *b, int64_t E, const float *G, double lambda,
                        const float *q, float *Aq, void *stream);
+
+/* fem_bp30_apply_f32 with a chosen kernel: FEM_LAYOUT_LINES (several
+ * elements per block, block barriers between the phases) or FEM_LAYOUT_WARP
+ * (one warp per element).  Same arguments, layouts and errors (FEM_EINVAL
+ * for another layout; E <= 2^31 - 1).  Both compute the same FP32 operator
+ * and agree to FP32 rounding. */
+int fem_bp30_apply_f32_layout(const fem_basis *b, int64_t E, const float *G, double lambda,
+                              const float *q, float *Aq, int layout, void *stream);
 
 /* BP3.0 matvec (Algorithm 5) with its twelve 1D contractions on the tensor
  * cores: mma.sync m16n8k16 with f16 operands and FP32 accumulation, FP32

@@ -127,6 +127,7 @@ int fem_basis_setup(int N, fem_basis **out) {
     if (e == cudaSuccess) e = fem::prepare_bp35_f16(N, fem::fold_table());
     if (e == cudaSuccess) e = fem::prepare_bp30_f16(N, fem::fold_table());
     if (e == cudaSuccess) e = fem::prepare_bp30_tc(N);
+    if (e == cudaSuccess) e = fem::prepare_bp30_warp(N, fem::fold_table());
     if (e != cudaSuccess) {
         cudaFree(b->d_ops);
         if (b->d_tc) cudaFree(b->d_tc);
@@ -315,6 +316,18 @@ int fem_bp30_apply_f32(const fem_basis *b, int64_t E, const float *G, double lam
     if (!G || !q || !Aq || !aligned16(G) || !aligned16(q) || !aligned16(Aq)) return FEM_EINVAL;
     if ((const void *)Aq == (const void *)q || (E + 1) > (int64_t)0x7fffffff) return FEM_EINVAL;
     cudaError_t e = fem::launch_bp30_f32(b, E, G, lambda, q, Aq, (cudaStream_t)stream);
+    return e == cudaSuccess ? FEM_OK : cuda_fail(e);
+}
+
+int fem_bp30_apply_f32_layout(const fem_basis *b, int64_t E, const float *G, double lambda, const float *q,
+                              float *Aq, int layout, void *stream) {
+    if (layout != FEM_LAYOUT_LINES && layout != FEM_LAYOUT_WARP) return FEM_EINVAL;
+    if (!b || E < 0) return FEM_EINVAL;
+    if (E == 0) return FEM_OK;
+    if (!G || !q || !Aq || !aligned16(G) || !aligned16(q) || !aligned16(Aq)) return FEM_EINVAL;
+    if ((const void *)Aq == (const void *)q || E > (int64_t)0x7fffffff) return FEM_EINVAL;
+    cudaError_t e = layout == FEM_LAYOUT_WARP ? fem::launch_bp30_warp(b, E, G, lambda, q, Aq, (cudaStream_t)stream)
+                                              : fem::launch_bp30_f32(b, E, G, lambda, q, Aq, (cudaStream_t)stream);
     return e == cudaSuccess ? FEM_OK : cuda_fail(e);
 }
 

@@ -117,6 +117,12 @@ cudaError_t launch_bp30_tc(const fem_basis *b, int64_t E, const float *G, double
 cudaError_t launch_bp30_pcg_tc(const fem_basis *b, int64_t E, const float *G, double lambda, const float *z,
                                float *p, const double *beta, float *Ap, double *partials, cudaStream_t s);
 int64_t bp30_tc_blocks(int64_t E);
+// FP32 BP3.0 with one warp per element (bp30_warp.cu)
+cudaError_t prepare_bp30_warp(int N, const double *fold_table);
+cudaError_t launch_bp30_warp(const fem_basis *b, int64_t E, const float *G, double lambda, const float *q, float *Aq,
+                             cudaStream_t s);
+cudaError_t launch_bp30_pcg_warp(const fem_basis *b, int64_t E, const float *G, double lambda, const float *z,
+                                 float *p, const double *beta, float *Ap, double *partials, cudaStream_t s);
 int64_t bp30_blocks(int N, int64_t E, bool f32);
 
 // FP32 BP3.5 matvec (the inner operator of the mixed-precision solver).
