@@ -680,6 +680,10 @@ def headline_summary(sections):
         for k, v in t.items():
             if k.endswith("_speedup"):
                 out["pcg_tol_1e-13"][k] = v
+        t30 = (pcg.get("bp30") or {}).get("tight", {})
+        if t30:
+            out["pcg_bp30_tol_5e-13"] = {k: (v.get("solves_per_s") if isinstance(v, dict) else v)
+                                         for k, v in t30.items() if k != "tol"}
     b = sections.get("batch")
     if b:
         out["batch_gdofs"] = {"separate": b["separate_launches"]["gdofs"],
@@ -796,10 +800,11 @@ def run_sweep(fem, torch, device, verts, args, sm_mhz):
         smem = smem_counts(N)
         row = {"N": N, "dofs": E * n ** 3}
         for name, kind in (("bp1", 1), ("bp35", 2), ("bp30", 3), ("bp1_bp30", 3), ("bp30_points", 3),
-                           ("bp35_f32", 2), ("bp30_f32", 3), ("bp35_f16", 2), ("bp30_f16", 3)):
+                           ("bp35_f32", 2), ("bp30_f32", 3), ("bp35_f16", 2), ("bp30_f16", 3),
+                           ("bp30_f32_warp", 3), ("bp30_tc", 3)):
             f16 = name.endswith("_f16")
-            f32 = name.endswith("_f32") or f16
-            base = name[:-4] if f32 else name
+            f32 = name.endswith("_f32") or f16 or name in ("bp30_f32_warp", "bp30_tc")
+            base = "bp30" if name in ("bp30_f32_warp", "bp30_tc") else (name[:-4] if f32 else name)
             ratio_base = "bp30" if base in ("bp30_points", "bp1_bp30") else base
             geo = torch.empty(fem.geo_shape(b, kind, E), dtype=torch.float64, device=device)
             fem.fem_mesh_geofacs(b, kind, verts, geo=geo, stream=stream)
@@ -815,7 +820,14 @@ def run_sweep(fem, torch, device, verts, args, sm_mhz):
             elif f32:
                 geo, qx = geo.float(), q.float()
                 o = torch.empty_like(qx)
-                fn = fem.fem_bp35_apply_f32 if base == "bp35" else fem.fem_bp30_apply_f32
+                if name == "bp30_tc":
+                    fn = fem.fem_bp30_apply_tc
+                elif name == "bp30_f32_warp":
+                    def fn(b_, g_, l_, q_, out, stream):
+                        return fem.fem_bp30_apply_f32_layout(b_, g_, l_, q_, fem.FEM_LAYOUT_WARP, out=out,
+                                                             stream=stream)
+                else:
+                    fn = fem.fem_bp35_apply_f32 if base == "bp35" else fem.fem_bp30_apply_f32
                 ms = timed(lambda: fn(b, geo, lam, qx, out=o, stream=stream), reps)
                 del qx, o
             elif name == "bp1_bp30":
@@ -872,7 +884,9 @@ def run_sweep(fem, torch, device, verts, args, sm_mhz):
     torch.cuda.empty_cache()
     return {"workload": f"BP1.0/BP3.5/BP3.0 FP64 (BP3.0 also in the point-per-thread layout, and BP1.0 + BP3.0 "
                         f"in one pass, whose GDOF/s count both operators' DOFs; BP3.5/BP3.0 FP32 "
-                        f"with FP32 and FP16 factors, the mixed solvers' inner operators) sweep, E={E} jittered "
+                        f"with FP32 and FP16 factors, the mixed solvers' inner operators; FP32 BP3.0 with one "
+                        f"warp per element and with its contractions on the tensor cores, split f16 mma.sync) "
+                        f"sweep, E={E} jittered "
                         f"hexes, lambda=1, median of {reps} launches per point, L2 evicted before each",
             "copy_roofline": "device-to-device copy of T/2 bytes moving T = the operator's algorithmic "
                              "bytes, recalibrated at every N (Section 5 of the paper)",
@@ -937,74 +951,75 @@ def manufactured_u(fem, basis, verts_h):
 
 
 def run_pcg(fem, torch, device, verts_h, args):
-    """Jacobi-PCG of the BP3.5 Helmholtz system (lambda = 1) with the
-    manufactured right-hand side b = A u_I: all-FP64 against FP32 inner
-    solves inside FP64 defect correction, both to ||r|| <= 1e-10 ||b||, then
-    each once more to 1e-13 for the distance between the solutions."""
-    N, lam, tol = args.degree, 1.0, 1e-10
+    """Jacobi-PCG of the BP3.5 Helmholtz system (lambda = 1; the precision
+    configuration) and of the BP3.0 one, with the manufactured right-hand
+    side b = A u_I: all-FP64 against FP64 defect correction with FP32 inner
+    solves (FP32 factors; FP16 factors; for BP3.0 also the tensor-core
+    contractions).  Each mode is solved to a tight residual (1e-13 for
+    BP3.5, 5e-13 for BP3.0, whose FP64 residual stagnates near 2e-13), where
+    every mode reaches the FP64 solution to 1e-10 and the distance to it is
+    reported, and to 1e-10, the configuration's residual, where the solves
+    differ by up to the FP64 solve's own distance to u_I (about 2e-8: the
+    error is the residual times up to the condition number)."""
+    N, lam = args.degree, 1.0
     basis = fem.fem_basis_setup(N)
     vd = torch.from_numpy(verts_h).to(device)
-    G = fem.fem_mesh_geofacs(basis, fem.FEM_GEO_BP35, vd)
     u = torch.from_numpy(manufactured_u(fem, basis, verts_h)).to(device)
-    b = fem.fem_bp35_apply(basis, G, lam, u)
-    out = {"workload": f"BP3.5 Helmholtz PCG (Jacobi), N={N}, E={verts_h.shape[0]}, lambda=1, "
-                       f"b = A u_I with u = sin(pi x) sin(pi y) sin(pi z), tol {tol:g}",
-           "error_reference": "u_I, the exact discrete solution (the oracle PCG agrees with the GPU "
-                              "solvers to 1e-8 on the smaller meshes of tests/test_pcg_gpu.py)"}
-    xs = {}
-    modes = [m for m in (("fp64", fem.FEM_PCG_FP64, 0.0), ("mixed", fem.FEM_PCG_MIXED, 1e-3),
-                         ("mixed16", fem.FEM_PCG_MIXED16, 1e-3)) if m[0] in args.pcg_modes.split(",")]
-    for name, mode, itol in modes:
-        s = fem.fem_pcg_create(basis, G, lam, mode)
-        x, info, code = s.solve(b, tol=tol, inner_tol=itol)  # warm-up
-        times = []
-        for _ in range(max(1, args.pcg_solves)):
-            x.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            x, info, code = s.solve(b, x=x, tol=tol, inner_tol=itol)
-            torch.cuda.synchronize()
-            times.append(time.perf_counter() - t0)
-        med = statistics.median(times)
-        err = (torch.linalg.norm(x - u) / torch.linalg.norm(u)).item()
-        out[name] = {"solves_per_s": 1.0 / med, "ms_per_solve": 1e3 * med, "iters": info["iters"],
-                     "outer": info["outer"], "relres": info["relres"], "status": code,
-                     "rel_err_vs_u_I": err}
-        xs[name] = x.clone()
-        s.free()
-    for name in ("mixed", "mixed16"):
-        if name in xs and "fp64" in xs:
-            out[name]["rel_diff_vs_fp64_solve"] = (torch.linalg.norm(xs[name] - xs["fp64"]) /
-                                                   torch.linalg.norm(xs["fp64"])).item()
-            out[name + "_speedup"] = out[name]["solves_per_s"] / out["fp64"]["solves_per_s"]
-    # the same solves to 1e-13: the solution error is the residual times up
-    # to the condition number, so a 1e-10 residual leaves the solves about
-    # 2e-8 apart; at 1e-13 each reaches u_I, and so the FP64 solve, to 1e-10
-    tight, xt = {"tol": 1e-13}, {}
-    for name, mode, itol in modes:
-        s = fem.fem_pcg_create(basis, G, lam, mode)
-        x, info, code = s.solve(b, tol=1e-13, inner_tol=itol, raise_on_error=False)  # warm-up
-        x.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        x, info, code = s.solve(b, x=x, tol=1e-13, inner_tol=itol, raise_on_error=False)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        tight[name] = {"solves_per_s": 1.0 / dt, "iters": info["iters"], "outer": info["outer"],
-                       "relres": info["relres"], "status": code,
-                       "rel_err_vs_u_I": (torch.linalg.norm(x - u) / torch.linalg.norm(u)).item()}
-        xt[name] = x.clone()
-        s.free()
-    for name in ("mixed", "mixed16"):
-        if name in xt and "fp64" in xt:
-            tight[name]["rel_diff_vs_fp64_solve"] = (torch.linalg.norm(xt[name] - xt["fp64"]) /
-                                                     torch.linalg.norm(xt["fp64"])).item()
-            tight[name + "_speedup"] = tight[name]["solves_per_s"] / tight["fp64"]["solves_per_s"]
-    out["tight"] = tight
-    out["modes"] = {"fp64": "all-FP64 Jacobi-PCG",
-                    "mixed": "FP64 defect correction, FP32 inner PCG with FP32 factors",
-                    "mixed16": "FP64 defect correction, FP32 inner PCG with binary16 factors (power-of-two "
-                               "scaled) widened to FP32 in the kernel"}
+    out = {"workload": f"Helmholtz PCG (Jacobi), N={N}, E={verts_h.shape[0]}, lambda=1, b = A u_I with "
+                       f"u = sin(pi x) sin(pi y) sin(pi z)",
+           "error_reference": "u_I, the exact discrete solution; rel_diff_vs_fp64_solve against the FP64 "
+                              "GPU solve of the same tolerance (the oracle PCG agrees with the GPU solvers to "
+                              "1e-8 on the smaller meshes of tests/test_pcg_gpu.py)",
+           "modes": {"fp64": "all-FP64 Jacobi-PCG",
+                     "mixed": "FP64 defect correction, FP32 inner PCG with FP32 factors",
+                     "mixed16": "FP64 defect correction, FP32 inner PCG with binary16 factors (power-of-two "
+                                "scaled) widened to FP32 in the kernel",
+                     "mixed_tc": "FP64 defect correction, FP32 inner PCG whose BP3.0 matvec runs its "
+                                 "contractions on the tensor cores (split f16 mma.sync, FP32 accumulate)"}}
+    wanted = args.pcg_modes.split(",")
+    for opname, op, kind in (("bp35", fem.FEM_OP_BP35, fem.FEM_GEO_BP35), ("bp30", fem.FEM_OP_BP30, fem.FEM_GEO_BP30)):
+        G = fem.fem_mesh_geofacs(basis, kind, vd)
+        apply = fem.fem_bp35_apply if op == fem.FEM_OP_BP35 else fem.fem_bp30_apply
+        b = apply(basis, G, lam, u)
+        modes = [(nm, md, it) for nm, md, it in (("fp64", fem.FEM_PCG_FP64, 0.0), ("mixed", fem.FEM_PCG_MIXED, 1e-3),
+                                                 ("mixed16", fem.FEM_PCG_MIXED16, 1e-3),
+                                                 ("mixed_tc", fem.FEM_PCG_MIXED_TC, 1e-3))
+                 if nm in wanted and not (nm == "mixed_tc" and op != fem.FEM_OP_BP30)]
+        res = {}
+        # the tight solve: 1e-13 for BP3.5; the FP64 BP3.0 residual stagnates
+        # near 2e-13 on this mesh, so 5e-13 for BP3.0
+        tight = 1e-13 if op == fem.FEM_OP_BP35 else 5e-13
+        for tol, reps in ((tight, 1), (1e-10, max(1, args.pcg_solves))):
+            blk, xs = {"tol": tol}, {}
+            for name, mode, itol in modes:
+                s = fem.fem_pcg_create(basis, G, lam, mode, op=op)
+                x, info, code = s.solve(b, tol=tol, inner_tol=itol, raise_on_error=False)  # warm-up
+                times = []
+                for _ in range(reps):
+                    x.zero_()
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    x, info, code = s.solve(b, x=x, tol=tol, inner_tol=itol, raise_on_error=False)
+                    torch.cuda.synchronize()
+                    times.append(time.perf_counter() - t0)
+                med = statistics.median(times)
+                blk[name] = {"solves_per_s": 1.0 / med, "ms_per_solve": 1e3 * med, "iters": info["iters"],
+                             "outer": info["outer"], "relres": info["relres"], "status": code,
+                             "rel_err_vs_u_I": (torch.linalg.norm(x - u) / torch.linalg.norm(u)).item()}
+                xs[name] = x.clone()
+                s.free()
+            for name in xs:
+                if name != "fp64" and "fp64" in xs:
+                    blk[name]["rel_diff_vs_fp64_solve"] = (torch.linalg.norm(xs[name] - xs["fp64"]) /
+                                                           torch.linalg.norm(xs["fp64"])).item()
+                    blk[name + "_speedup"] = blk[name]["solves_per_s"] / blk["fp64"]["solves_per_s"]
+            res["tight" if tol == tight else "tol_1e-10"] = blk
+            del xs
+        out[opname] = res
+        del G, b
+        torch.cuda.empty_cache()
+    # the precision configuration (BP3.5) at the top level, tight solve first
+    out["tight"] = out["bp35"]["tight"]
     basis.free()
     return out
 
@@ -1135,8 +1150,9 @@ def main(argv=None):
     ap.add_argument("--no-sweep", action="store_true", help="skip the per-N operator sweep")
     ap.add_argument("--no-pcg", action="store_true", help="skip the Helmholtz solve measurement")
     ap.add_argument("--pcg-solves", type=int, default=3)
-    ap.add_argument("--pcg-modes", default="fp64,mixed,mixed16",
-                    help="solver modes of the Helmholtz measurement (comma list of fp64, mixed, mixed16)")
+    ap.add_argument("--pcg-modes", default="fp64,mixed,mixed16,mixed_tc",
+                    help="solver modes of the Helmholtz measurement (comma list of fp64, mixed, mixed16, "
+                         "mixed_tc; mixed_tc applies to BP3.0)")
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-order batch measurement")
     ap.add_argument("--sections-out", default=None,
                     help="also write the side sections and the full headline to this JSON file")

@@ -346,6 +346,10 @@ int fem_dot_noalloc(int64_t n, const double *x, const double *y, double *result,
  *                  on the device from the largest factor) and widened to
  *                  FP32 in the kernel: half the factor bytes, same FP32
  *                  arithmetic.  The FP64 outer loop still reaches tol.
+ *   FEM_PCG_MIXED_TC  as FEM_PCG_MIXED, with the inner matvec's
+ *                  contractions on the tensor cores (fem_bp30_apply_tc:
+ *                  split f16 operands, FP32 accumulation); FEM_OP_BP30 only
+ *                  (FEM_EINVAL for BP3.5).
  * A solver context owns its device workspace (about 5 vectors in FP64
  * mode; 7 FP32 (MIXED16: FP16) factor planes and 6 FP32 + 1 FP64 vectors in
  * the mixed modes).
@@ -359,6 +363,7 @@ int fem_dot_noalloc(int64_t n, const double *x, const double *y, double *result,
 #define FEM_PCG_FP64 0
 #define FEM_PCG_MIXED 1
 #define FEM_PCG_MIXED16 2
+#define FEM_PCG_MIXED_TC 3
 
 typedef struct fem_pcg fem_pcg; /* opaque */
 
@@ -503,7 +508,7 @@ typedef struct {
     const double *rhs;   /* host, E*Np; read when the request is admitted           */
     double *x;           /* host output, E*Np; written when the request finishes    */
     double lambda;       /* >= 0                                                    */
-    int mode;            /* FEM_PCG_FP64, FEM_PCG_MIXED or FEM_PCG_MIXED16          */
+    int mode;            /* FEM_PCG_FP64, _MIXED, _MIXED16 or _MIXED_TC (BP3.0)     */
     double tol;          /* relative residual tolerance                             */
 } fem_serve_request;
 

@@ -23,14 +23,14 @@ __all__ = [
     "geo_shape", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_wait_selftest", "fem_bp30_apply_layout", "fem_fma_probe",
     "FEM_LAYOUT_LINES", "FEM_LAYOUT_POINTS", "FEM_LAYOUT_WARP", "fem_bp30_apply_f32_layout", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_bp30_apply_tc", "FEM_PREC_F16TC", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot", "fem_dot_scratch_size", "Pcg",
     "fem_bp35_apply_ex", "fem_bp30_apply_ex", "fem_bp1_bp30_apply", "FEM_PREC_F64", "FEM_PREC_F32", "FEM_PREC_F16G",
-    "fem_pcg_create", "fem_pcg_solve", "fem_pcg_destroy", "FEM_PCG_FP64", "FEM_PCG_MIXED", "FEM_PCG_MIXED16", "fem_bp35_apply_f16g", "fem_bp30_apply_f16g",
+    "fem_pcg_create", "fem_pcg_solve", "fem_pcg_destroy", "FEM_PCG_FP64", "FEM_PCG_MIXED", "FEM_PCG_MIXED16", "FEM_PCG_MIXED_TC", "fem_bp35_apply_f16g", "fem_bp30_apply_f16g",
     "Batch", "fem_batch_create", "FEM_OP_BP35", "FEM_OP_BP30", "Server",
     "FEM_REQ_QUEUED", "FEM_REQ_RUNNING", "FEM_REQ_DONE", "FEM_REQ_FAILED", "FEM_SERVE_FIFO", "FEM_SERVE_SHORTEST",
 ]
 
 FEM_OK, FEM_EINVAL, FEM_ECUDA, FEM_ENOMEM, FEM_ENODEV = 0, -1, -2, -3, -4
 FEM_EBREAKDOWN, FEM_ENOCONV, FEM_ETOOBIG = -5, -6, -7
-FEM_PCG_FP64, FEM_PCG_MIXED, FEM_PCG_MIXED16 = 0, 1, 2
+FEM_PCG_FP64, FEM_PCG_MIXED, FEM_PCG_MIXED16, FEM_PCG_MIXED_TC = 0, 1, 2, 3
 FEM_GEO_BP1, FEM_GEO_BP35, FEM_GEO_BP30 = 1, 2, 3
 FEM_OP_BP35, FEM_OP_BP30 = 2, 3
 FEM_LAYOUT_LINES, FEM_LAYOUT_POINTS, FEM_LAYOUT_WARP = 0, 1, 2

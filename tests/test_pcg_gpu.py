@@ -190,8 +190,13 @@ def test_apply_ex_selects_the_precision_entry_points(op, N):
     G16, ginv = _f16_factors(G)
     G16d, gi = torch.from_numpy(G16).to("cuda"), torch.tensor([ginv], dtype=torch.float64, device="cuda")
     assert torch.equal(ex(b, fem.FEM_PREC_F16G, G16d, 1.0, q32, ginv=gi), f16(b, G16d, gi, 1.0, q32))
+    if op == "bp30":
+        assert torch.equal(ex(b, fem.FEM_PREC_F16TC, G32, 1.0, q32), fem.fem_bp30_apply_tc(b, G32, 1.0, q32))
+    else:  # no tensor-core BP3.5 operator
+        with pytest.raises(fem.FemError):
+            ex(b, fem.FEM_PREC_F16TC, G32, 1.0, q32)
     with pytest.raises(ValueError):
-        ex(b, 3, Gd, 1.0, qd)
+        ex(b, 4, Gd, 1.0, qd)
     with pytest.raises(TypeError):
         ex(b, fem.FEM_PREC_F32, Gd, 1.0, qd)  # float64 tensors for the FP32 path
 
@@ -352,7 +357,7 @@ def test_bp30_jacobi_diagonal(N):
     assert _rel(got, ref) < 1e-12
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2], ids=["fp64", "mixed", "mixed16"])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3], ids=["fp64", "mixed", "mixed16", "mixed_tc"])
 @pytest.mark.parametrize("N", [2, 5])
 def test_bp30_pcg_manufactured(N, mode):
     fem = _fem()
@@ -416,3 +421,42 @@ def test_solve_on_a_side_stream_replays_graphs_with_the_same_bits():
             st.synchronize()
             assert torch.equal(ref1, x1) and torch.equal(ref1, x1b) and torch.equal(ref2, x2)
             assert i1["iters"] == j1["iters"] and i2["iters"] == j2["iters"]
+
+
+def test_mixed_tc_is_bp30_only():
+    fem = _fem()
+    N = 3
+    v = fem_synth.box_mesh(2)
+    G, _ = oracle.geofacs(N, oracle.KIND_BP35, v)
+    basis = fem.fem_basis_setup(N)
+    with pytest.raises(fem.FemError):
+        fem.fem_pcg_create(basis, _dev(G), 1.0, fem.FEM_PCG_MIXED_TC, op=fem.FEM_OP_BP35)
+
+
+def test_full_size_bp30_solves_all_modes():
+    """The BP3.0 Helmholtz solve (lambda = 1) on the 32^3 jittered mesh at
+    N = 7 with b = A u_I, in every mode to a 5e-13 relative residual (the
+    FP64 BP3.0 residual stagnates near 2e-13 on this mesh): the FP32,
+    FP16-factor and tensor-core defect-correction solves then reach the
+    FP64 solution to 1e-10."""
+    fem, torch = _fem(), _torch()
+    N = 7
+    v = fem_synth.box_mesh(32)
+    basis = fem.fem_basis_setup(N)
+    vd = _dev(v)
+    G = fem.fem_mesh_geofacs(basis, fem.FEM_GEO_BP30, vd)
+    X = oracle.gll_node_coordinates(N, v)
+    u = _dev(np.sin(np.pi * X[..., 0]) * np.sin(np.pi * X[..., 1]) * np.sin(np.pi * X[..., 2]))
+    b = fem.fem_bp30_apply(basis, G, 1.0, u)
+    xs = {}
+    for mode in (fem.FEM_PCG_FP64, fem.FEM_PCG_MIXED, fem.FEM_PCG_MIXED16, fem.FEM_PCG_MIXED_TC):
+        s = fem.fem_pcg_create(basis, G, 1.0, mode, op=fem.FEM_OP_BP30)
+        x, info, code = s.solve(b, tol=5e-13, inner_tol=1e-3)
+        assert code == 0, mode
+        r = b - fem.fem_bp30_apply(basis, G, 1.0, x)
+        assert (torch.linalg.norm(r) / torch.linalg.norm(b)).item() <= 1e-12, mode
+        xs[mode] = x
+        s.free()
+    ref = xs[fem.FEM_PCG_FP64]
+    for mode, x in xs.items():
+        assert (torch.linalg.norm(x - ref) / torch.linalg.norm(ref)).item() <= 1e-10, mode
