@@ -176,8 +176,11 @@ int fem_wait_timeouts(unsigned long long *count, int reset);
 /* Self-test of the bounded device waits: runs one block whose mbarrier
  * wait can never complete (a barrier expecting an arrival that never comes)
  * and reports in *gave_up how many warps gave up after the wait's limit
- * (about a second): 2 when the limit works.  The context stays usable; this
- * self-test's count is not added to fem_wait_timeouts.  Synchronous.
+ * (about a second): 2 when the limit works.  The block also reports the
+ * failure through a device status word, as the stream kernels report it to
+ * the solver; the call returns FEM_ETIMEDOUT when that report arrived (the
+ * expected outcome) and FEM_OK when it did not.  The context stays usable;
+ * this self-test's count is not added to fem_wait_timeouts.  Synchronous.
  * Errors: FEM_EINVAL, FEM_ECUDA. */
 int fem_wait_selftest(unsigned long long *gave_up);
 
@@ -356,6 +359,10 @@ int fem_dot_noalloc(int64_t n, const double *x, const double *y, double *result,
  * --------------------------------------------------------------------- */
 #define FEM_EBREAKDOWN (-5) /* p.Ap <= 0 or a non-finite value in the recurrence */
 #define FEM_ENOCONV (-6)    /* iteration limit reached; x holds the last iterate */
+#define FEM_ETIMEDOUT (-8)  /* a kernel's bounded device wait gave up during the solve
+                             * (its staged data may not have landed): x is not to be
+                             * trusted.  The solver stops at the end of the step in
+                             * which the kernel reported it. */
 
 #define FEM_OP_BP35 2 /* operator selectors of the solver and of batches */
 #define FEM_OP_BP30 3
@@ -402,9 +409,20 @@ int fem_pcg_create(const fem_basis *b, int op, int64_t E, const double *G, doubl
  * but the true one does not (rounding drift near FP64's attainable
  * accuracy), the iteration restarts from the true residual, at most 8 times
  * and only while each restart halves it; then FEM_ENOCONV.  Returns FEM_OK,
- * FEM_ENOCONV, FEM_EBREAKDOWN, FEM_EINVAL or FEM_ECUDA. */
+ * FEM_ENOCONV, FEM_EBREAKDOWN, FEM_ETIMEDOUT (a kernel's bounded device
+ * wait gave up), FEM_EINVAL or FEM_ECUDA. */
 int fem_pcg_solve(fem_pcg *s, const double *rhs, double *x, const fem_pcg_opts *opts,
                   fem_pcg_info *info, void *stream);
+
+/* Host-side fault injection for tests of the failure path: the solver's
+ * next solve reports its first step (FEM_PCG_FP64: its first chunk of
+ * iterations; the mixed modes: the first chunk of the first inner solve)
+ * exactly as a kernel whose bounded device wait gave up would, so that the
+ * solve returns FEM_ETIMEDOUT.  Nothing faults, hangs or waits on the GPU.
+ * fault: FEM_FAULT_WAIT_TIMEOUT.  Applies to one solve; synchronous, no GPU
+ * work.  Errors: FEM_EINVAL. */
+#define FEM_FAULT_WAIT_TIMEOUT 1
+int fem_pcg_inject_fault(fem_pcg *s, int fault);
 
 /* Frees a solver (NULL accepted).  Synchronous. */
 void fem_pcg_destroy(fem_pcg *s);
@@ -490,14 +508,18 @@ typedef struct fem_server fem_server; /* opaque */
                               * times 2.5 for BP3.0 and 0.15 for the mixed modes (the
                               * per-iteration cost and the growth of Jacobi-PCG's
                               * iteration count with N and the mesh size); ties by
-                              * arrival.  A large request can wait behind a stream of
-                              * smaller ones.                                          */
+                              * arrival, with aging: a request that has waited
+                              * max_wait_s goes first, so a large request is not
+                              * starved by a stream of smaller ones.                   */
 
 typedef struct {
     int64_t hbm_budget; /* device bytes admitted requests may hold (default 120 GiB) */
     int max_active;     /* requests in flight at once, 1..256 (default 8)          */
     int check_every;    /* PCG iterations between host checks (default 8)          */
     int policy;         /* FEM_SERVE_FIFO or FEM_SERVE_SHORTEST                     */
+    double max_wait_s;  /* FEM_SERVE_SHORTEST aging: once the oldest queued request
+                         * has waited this long it is admitted next, ahead of
+                         * smaller ones (default 2 s; <= 0 takes the default)   */
 } fem_serve_opts;
 
 typedef struct {
@@ -547,6 +569,24 @@ int fem_serve_progress(fem_server *s, int *active, int *queued);
 
 /* State and outcome of a request.  Errors: FEM_EINVAL (unknown id). */
 int fem_serve_poll(fem_server *s, int64_t id, fem_serve_result *res);
+
+/* Progresses the server (fem_serve_progress) until request id is DONE or
+ * FAILED or timeout_s seconds of host time have passed, then writes its
+ * result to *res.  Returns FEM_OK when it finished, FEM_ETIMEDOUT when the
+ * deadline passed first (the request is untouched and goes on in later
+ * calls).  Waits on the host only (it polls the solves' events).
+ * Errors: FEM_EINVAL (unknown id, NULL res, negative timeout). */
+int fem_serve_wait(fem_server *s, int64_t id, double timeout_s, fem_serve_result *res);
+
+/* Cancels request id.  A queued request is removed at once (FAILED,
+ * status FEM_ECANCELED).  A running one is given no further step: it
+ * becomes FAILED with FEM_ECANCELED at the first fem_serve_progress after
+ * the step in flight on its stream has finished (no kernel is interrupted),
+ * and its device memory is released.  A request whose solution is already
+ * on its way to the host, or that has finished, is left as it is.  Other
+ * requests are not affected.  Errors: FEM_EINVAL (unknown id). */
+#define FEM_ECANCELED (-9)
+int fem_serve_cancel(fem_server *s, int64_t id);
 
 /* Seconds since the server was created (the clock of fem_serve_result). */
 double fem_serve_clock(const fem_server *s);

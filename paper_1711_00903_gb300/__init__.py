@@ -23,13 +23,14 @@ __all__ = [
     "geo_shape", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_wait_selftest", "fem_bp30_apply_layout", "fem_fma_probe",
     "FEM_LAYOUT_LINES", "FEM_LAYOUT_POINTS", "FEM_LAYOUT_WARP", "fem_bp30_apply_f32_layout", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_bp30_apply_tc", "FEM_PREC_F16TC", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot", "fem_dot_scratch_size", "Pcg",
     "fem_bp35_apply_ex", "fem_bp30_apply_ex", "fem_bp1_bp30_apply", "FEM_PREC_F64", "FEM_PREC_F32", "FEM_PREC_F16G",
-    "fem_pcg_create", "fem_pcg_solve", "fem_pcg_destroy", "FEM_PCG_FP64", "FEM_PCG_MIXED", "FEM_PCG_MIXED16", "FEM_PCG_MIXED_TC", "fem_bp35_apply_f16g", "fem_bp30_apply_f16g",
+    "fem_pcg_create", "fem_pcg_solve", "fem_pcg_destroy", "FEM_ETIMEDOUT", "FEM_ECANCELED", "FEM_FAULT_WAIT_TIMEOUT", "FEM_EBREAKDOWN", "FEM_PCG_FP64", "FEM_PCG_MIXED", "FEM_PCG_MIXED16", "FEM_PCG_MIXED_TC", "fem_bp35_apply_f16g", "fem_bp30_apply_f16g",
     "Batch", "fem_batch_create", "FEM_OP_BP35", "FEM_OP_BP30", "Server",
     "FEM_REQ_QUEUED", "FEM_REQ_RUNNING", "FEM_REQ_DONE", "FEM_REQ_FAILED", "FEM_SERVE_FIFO", "FEM_SERVE_SHORTEST",
 ]
 
 FEM_OK, FEM_EINVAL, FEM_ECUDA, FEM_ENOMEM, FEM_ENODEV = 0, -1, -2, -3, -4
-FEM_EBREAKDOWN, FEM_ENOCONV, FEM_ETOOBIG = -5, -6, -7
+FEM_EBREAKDOWN, FEM_ENOCONV, FEM_ETOOBIG, FEM_ETIMEDOUT, FEM_ECANCELED = -5, -6, -7, -8, -9
+FEM_FAULT_WAIT_TIMEOUT = 1
 FEM_PCG_FP64, FEM_PCG_MIXED, FEM_PCG_MIXED16, FEM_PCG_MIXED_TC = 0, 1, 2, 3
 FEM_GEO_BP1, FEM_GEO_BP35, FEM_GEO_BP30 = 1, 2, 3
 FEM_OP_BP35, FEM_OP_BP30 = 2, 3
@@ -69,7 +70,7 @@ class BatchConfig(C.Structure):
 class ServeOpts(C.Structure):
     """fem_serve_opts (include/fem.h)."""
     _fields_ = [("hbm_budget", C.c_int64), ("max_active", C.c_int), ("check_every", C.c_int),
-                ("policy", C.c_int)]
+                ("policy", C.c_int), ("max_wait_s", C.c_double)]
 
 
 class ServeRequest(C.Structure):
@@ -158,6 +159,10 @@ def lib():
             L.fem_serve_submit.argtypes = [vp, C.POINTER(ServeRequest), C.POINTER(i64)]
             L.fem_serve_progress.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
             L.fem_serve_poll.argtypes = [vp, i64, C.POINTER(ServeResult)]
+            L.fem_serve_wait.argtypes = [vp, i64, dbl, C.POINTER(ServeResult)]
+            L.fem_serve_wait.restype = i32
+            L.fem_serve_cancel.argtypes = [vp, i64]
+            L.fem_serve_cancel.restype = i32
             L.fem_serve_clock.argtypes = [vp]
             L.fem_serve_clock.restype = dbl
             L.fem_serve_in_use.argtypes = [vp]
@@ -167,6 +172,8 @@ def lib():
             for f in ("fem_serve_create", "fem_serve_submit", "fem_serve_progress", "fem_serve_poll"):
                 getattr(L, f).restype = i32
             L.fem_pcg_destroy.argtypes = [vp]
+            L.fem_pcg_inject_fault.argtypes = [vp, i32]
+            L.fem_pcg_inject_fault.restype = i32
             L.fem_pcg_destroy.restype = None
             for f in ("fem_basis_setup", "fem_basis_tables", "fem_basis_host_tables",
                       "fem_mesh_geofacs", "fem_bp1_apply", "fem_bp35_apply", "fem_bp30_apply",
@@ -455,12 +462,15 @@ def fem_bp35_apply_f32(b: Basis, G, lam: float, q, out=None, stream=None):
     return out
 
 
-def fem_wait_selftest() -> int:
-    """Runs a kernel whose bounded wait cannot complete; returns how many
-    warps gave up (2 when the wait limit works)."""
+def fem_wait_selftest():
+    """Runs a kernel whose bounded wait cannot complete; returns (how many
+    warps gave up, the call's status): (2, FEM_ETIMEDOUT) when the wait
+    limit works and the kernel reported it through its status word."""
     c = C.c_ulonglong(0)
-    _check(lib().fem_wait_selftest(C.byref(c)), "fem_wait_selftest")
-    return int(c.value)
+    code = lib().fem_wait_selftest(C.byref(c))
+    if code not in (FEM_OK, FEM_ETIMEDOUT):
+        _check(code, "fem_wait_selftest")
+    return int(c.value), code
 
 
 def fem_fma_probe(iters: int, out=None, stream=None):
@@ -604,6 +614,11 @@ class Pcg:
         return fem_pcg_solve(self, rhs, x, tol, maxit, inner_tol, inner_maxit, check_every, stream,
                              raise_on_error)
 
+    def inject_fault(self, fault=FEM_FAULT_WAIT_TIMEOUT):
+        """Arms the host-side fault injection of the next solve
+        (fem_pcg_inject_fault)."""
+        _check(lib().fem_pcg_inject_fault(self.handle, int(fault)), "fem_pcg_inject_fault")
+
     def free(self):
         if self.handle and self.handle.value:
             lib().fem_pcg_destroy(self.handle)
@@ -719,9 +734,10 @@ class Server:
     solves).  Host arrays of a request are kept referenced here until the
     request has finished."""
 
-    def __init__(self, hbm_budget=120 << 30, max_active=8, check_every=8, policy=0):
-        """policy: FEM_SERVE_FIFO (0) or FEM_SERVE_SHORTEST (1)."""
-        o = ServeOpts(int(hbm_budget), int(max_active), int(check_every), int(policy))
+    def __init__(self, hbm_budget=120 << 30, max_active=8, check_every=8, policy=0, max_wait_s=0.0):
+        """policy: FEM_SERVE_FIFO (0) or FEM_SERVE_SHORTEST (1); max_wait_s:
+        the aging bound of FEM_SERVE_SHORTEST (0: the library's default)."""
+        o = ServeOpts(int(hbm_budget), int(max_active), int(check_every), int(policy), float(max_wait_s))
         h = C.c_void_p()
         _check(lib().fem_serve_create(C.byref(o), C.byref(h)), "fem_serve_create")
         self.handle = h
@@ -753,6 +769,18 @@ class Server:
         r = ServeResult()
         _check(lib().fem_serve_poll(self.handle, int(rid), C.byref(r)), "fem_serve_poll")
         return {k: getattr(r, k) for k, _ in ServeResult._fields_}
+
+    def wait(self, rid, timeout_s):
+        """Progresses until request rid finishes or timeout_s passes; returns
+        (result dict, status): FEM_OK, or FEM_ETIMEDOUT at the deadline."""
+        r = ServeResult()
+        code = lib().fem_serve_wait(self.handle, int(rid), float(timeout_s), C.byref(r))
+        if code not in (FEM_OK, FEM_ETIMEDOUT):
+            _check(code, "fem_serve_wait")
+        return {k: getattr(r, k) for k, _ in ServeResult._fields_}, code
+
+    def cancel(self, rid):
+        _check(lib().fem_serve_cancel(self.handle, int(rid)), "fem_serve_cancel")
 
     def clock(self) -> float:
         return lib().fem_serve_clock(self.handle)

@@ -63,6 +63,8 @@ const char *fem_strerror(int code) {
         case FEM_EBREAKDOWN: return "FEM_EBREAKDOWN: conjugate-gradient breakdown";
         case FEM_ENOCONV: return "FEM_ENOCONV: iteration limit reached";
         case FEM_ETOOBIG: return "FEM_ETOOBIG: size beyond the fixed capacity of the call";
+        case FEM_ECANCELED: return "FEM_ECANCELED: the request was cancelled";
+        case FEM_ETIMEDOUT: return "FEM_ETIMEDOUT: a bounded device wait gave up; the result is not to be trusted";
         default: return "unknown fem error code";
     }
 }
@@ -256,8 +258,10 @@ int fem_wait_timeouts(unsigned long long *count, int reset) {
 
 int fem_wait_selftest(unsigned long long *gave_up) {
     if (!gave_up) return FEM_EINVAL;
-    cudaError_t e = fem::run_wait_selftest(gave_up);
-    return e == cudaSuccess ? FEM_OK : cuda_fail(e);
+    bool reported = false;
+    cudaError_t e = fem::run_wait_selftest(gave_up, &reported);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return reported ? FEM_ETIMEDOUT : FEM_OK;
 }
 
 int64_t fem_fma_probe_threads(void) { return fem::fma_probe_threads(); }

@@ -95,9 +95,10 @@ struct Bp35PcgLaunchT {
     template <int N>
     struct L {
         static cudaError_t run(int64_t E, const T *G, double lambda, const T *z, T *p, const double *beta,
-                               T *Ap, double *partials, cudaStream_t s) {
+                               T *Ap, double *partials, cudaStream_t s, double *status) {
             if constexpr (sizeof(T) == 4 && bp35_streamed(N)) {
-                return launch_stream35<N, true>(E, G, lambda, nullptr, Ap, z, p, beta, partials, s);
+                return launch_stream35<N, true>(E, G, lambda, nullptr, Ap, z, p, beta, partials, s, nullptr,
+                                                status);
             } else {
                 using C = Bp35Cfg<T, N>;
                 const int64_t blocks = (E + C::EPB - 1) / C::EPB;
@@ -164,12 +165,14 @@ cudaError_t launch_bp35_f32(const fem_basis *b, int64_t E, const float *G, doubl
 
 cudaError_t launch_bp35_pcg(const fem_basis *b, int64_t E, const double *G, double lambda, const double *z,
                             double *p, const double *beta, double *Ap, double *partials, cudaStream_t s) {
-    return dispatch_degree<Bp35PcgLaunchT<double>::L>(b->host.N, E, G, lambda, z, p, beta, Ap, partials, s);
+    return dispatch_degree<Bp35PcgLaunchT<double>::L>(b->host.N, E, G, lambda, z, p, beta, Ap, partials, s,
+                                                       (double *)nullptr);
 }
 
 cudaError_t launch_bp35_pcg_f32(const fem_basis *b, int64_t E, const float *G, double lambda, const float *z,
-                                float *p, const double *beta, float *Ap, double *partials, cudaStream_t s) {
-    return dispatch_degree<Bp35PcgLaunchT<float>::L>(b->host.N, E, G, lambda, z, p, beta, Ap, partials, s);
+                                float *p, const double *beta, float *Ap, double *partials, cudaStream_t s,
+                                double *status) {
+    return dispatch_degree<Bp35PcgLaunchT<float>::L>(b->host.N, E, G, lambda, z, p, beta, Ap, partials, s, status);
 }
 
 int64_t bp35_max_blocks(int N, int64_t E) {

@@ -57,9 +57,9 @@ struct F16Launch {
     struct L {
         static cudaError_t run(int64_t E, const __half *G, const double *ginv, double lambda, const float *q,
                                float *Aq, const float *z, float *p, const double *beta, double *partials,
-                               cudaStream_t s) {
+                               cudaStream_t s, double *status) {
             if constexpr (bp35_streamed(N)) {
-                return launch_stream35<N, PCG, __half>(E, G, lambda, q, Aq, z, p, beta, partials, s, ginv);
+                return launch_stream35<N, PCG, __half>(E, G, lambda, q, Aq, z, p, beta, partials, s, ginv, status);
             } else {
                 using C = Bp35Cfg<float, N>;
                 const int64_t blocks = (E + C::EPB - 1) / C::EPB;
@@ -110,14 +110,15 @@ FEM_DEFINE_WAIT_COUNTER(wait_timeouts_bp35_f16)
 cudaError_t launch_bp35_f16g(const fem_basis *b, int64_t E, const __half *G, const double *ginv, double lambda,
                              const float *q, float *Aq, cudaStream_t s) {
     return dispatch_degree<F16Launch<false>::L>(b->host.N, E, G, ginv, lambda, q, Aq, (const float *)nullptr,
-                                                (float *)nullptr, (const double *)nullptr, (double *)nullptr, s);
+                                                (float *)nullptr, (const double *)nullptr, (double *)nullptr, s,
+                                                (double *)nullptr);
 }
 
 cudaError_t launch_bp35_pcg_f16g(const fem_basis *b, int64_t E, const __half *G, const double *ginv, double lambda,
                                  const float *z, float *p, const double *beta, float *Ap, double *partials,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, double *status) {
     return dispatch_degree<F16Launch<true>::L>(b->host.N, E, G, ginv, lambda, (const float *)nullptr, Ap, z, p, beta,
-                                               partials, s);
+                                               partials, s, status);
 }
 
 int64_t bp35_f16_blocks(int N, int64_t E) {

@@ -54,7 +54,8 @@ template <int N, bool PCG, typename TG>
 __global__ void __launch_bounds__(Bp35Stream<N, PCG, TG>::threads)
 bp35_stream_kernel(int64_t E, const TG *__restrict__ G, double lambda, const float *__restrict__ q,
                    float *__restrict__ Aq, const float *__restrict__ z, float *__restrict__ p,
-                   const double *__restrict__ beta, double *__restrict__ partials, const double *__restrict__ ginv) {
+                   const double *__restrict__ beta, double *__restrict__ partials, const double *__restrict__ ginv,
+                   double *__restrict__ status) {
     using S = Bp35Stream<N, PCG, TG>;
     using B = typename S::L::B;
     constexpr int n = S::n, nn = S::nn, NP = S::NP, EPS = S::EPS;
@@ -118,15 +119,18 @@ bp35_stream_kernel(int64_t E, const TG *__restrict__ G, double lambda, const flo
     __syncthreads();
 
     double dot = 0.0;  // the thread's p . Ap over its groups (FP32 per group)
-    bool ok = true;
+    bool failed = false, next_issued = false;
     int it = 0;
     for (int64_t g = blockIdx.x; g < groups; g += gridDim.x, it++) {
         const int k = it & 1;
         const unsigned parity = (unsigned)((it >> 1) & 1);
-        if (threadIdx.x == 0 && g + gridDim.x < groups) issue(g + gridDim.x, k ^ 1);
-        const bool done = mbar_wait(&bar[k], parity);
-        if (!done && (threadIdx.x & 31) == 0) atomicAdd(&g_wait_timeouts, 1ull);
-        ok = ok && done;
+        next_issued = g + gridDim.x < groups;
+        if (threadIdx.x == 0 && next_issued) issue(g + gridDim.x, k ^ 1);
+        // the whole block leaves together when any of its threads gave up
+        if (!__syncthreads_and(mbar_wait(&bar[k], parity))) {
+            failed = true;
+            break;
+        }
 
         const int64_t e0 = g * EPS;
         const int nel = (int)((E - e0) < EPS ? (E - e0) : EPS);
@@ -148,15 +152,26 @@ bp35_stream_kernel(int64_t E, const TG *__restrict__ G, double lambda, const flo
         dot += (double)bp35_core<float, N, EPS, PCG, true, TG>(boxes, e0, nel, sG, lambda, Aq, gscale);
         __syncthreads();  // the stage and the boxes are free again
     }
+    if (failed) {
+        // A stage did not land within the wait's limit: no more copies are
+        // issued and nothing more is computed.  The block reports it (the
+        // library-wide count, and the caller's status word when given),
+        // then waits once more, bounded, for the copies that may still be
+        // in flight (this iteration's stage and, if it was issued, the
+        // next one) before its shared memory is released.
+        if (threadIdx.x == 0) {
+            atomicAdd(&g_wait_timeouts, 1ull);
+            if (status) *status = 1.0;
+        }
+        const int k = it & 1;
+        mbar_wait(&bar[k], (unsigned)((it >> 1) & 1));
+        if (next_issued) mbar_wait(&bar[k ^ 1], (unsigned)(((it + 1) >> 1) & 1));
+        if (PCG && threadIdx.x == 0) partials[blockIdx.x] = 0.0;
+        return;
+    }
     if (PCG) {
         const double tot = block_sum(dot, reinterpret_cast<double *>(boxes));
         if (threadIdx.x == 0) partials[blockIdx.x] = tot;
-    }
-    // a copy that did not complete in time may still be in flight: wait for
-    // both stages once more (bounded) before the shared memory is released
-    if (!ok) {
-        mbar_wait(&bar[0], (unsigned)(((it + 1) >> 1) & 1));
-        mbar_wait(&bar[1], (unsigned)((it >> 1) & 1));
     }
 }
 
@@ -180,11 +195,11 @@ inline int64_t stream_grid35(int64_t groups, int blocks_per_sm) {
 template <int N, bool PCG, typename TG = float>
 cudaError_t launch_stream35(int64_t E, const TG *G, double lambda, const float *q, float *Aq, const float *z,
                             float *p, const double *beta, double *partials, cudaStream_t s,
-                            const double *ginv = nullptr) {
+                            const double *ginv = nullptr, double *status = nullptr) {
     using S = Bp35Stream<N, PCG, TG>;
     const int64_t grid = stream_grid35((E + S::EPS - 1) / S::EPS, S::blocks_per_sm);
     bp35_stream_kernel<N, PCG, TG><<<(unsigned)grid, S::threads, S::smem, s>>>(E, G, lambda, q, Aq, z, p, beta,
-                                                                               partials, ginv);
+                                                                               partials, ginv, status);
     return cudaGetLastError();
 }
 

@@ -93,9 +93,11 @@ cudaError_t launch_bp30_pcg(const fem_basis *b, int64_t E, const double *G, doub
 // power of two, the inverse scale at ginv (device)
 cudaError_t launch_bp35_f16g(const fem_basis *b, int64_t E, const __half *G, const double *ginv, double lambda,
                              const float *q, float *Aq, cudaStream_t s);
+// status: device word set to 1.0 when a bounded wait of the stream kernel
+// gave up (may be NULL)
 cudaError_t launch_bp35_pcg_f16g(const fem_basis *b, int64_t E, const __half *G, const double *ginv, double lambda,
                                  const float *z, float *p, const double *beta, float *Ap, double *partials,
-                                 cudaStream_t s);
+                                 cudaStream_t s, double *status);
 int64_t bp35_f16_blocks(int N, int64_t E);
 cudaError_t prepare_bp35_f16(int N, const double *fold_table);
 cudaError_t wait_timeouts_bp35_f16(unsigned long long *count, bool reset);
@@ -130,7 +132,7 @@ cudaError_t wait_timeouts_bp35(unsigned long long *count, bool reset);
 cudaError_t launch_stream_sum(int planes, int64_t n, const void *src, void *dst, int word, cudaStream_t s);
 int stream_max_planes();
 int64_t fma_probe_threads();
-cudaError_t run_wait_selftest(unsigned long long *gave_up);
+cudaError_t run_wait_selftest(unsigned long long *gave_up, bool *reported);
 cudaError_t launch_fma_probe(int64_t iters, double *out, cudaStream_t s);
 cudaError_t launch_bp35_f32(const fem_basis *b, int64_t E, const float *G, double lambda, const float *q,
                             float *Aq, cudaStream_t s);
@@ -151,6 +153,12 @@ cudaError_t pcg_begin(fem_pcg *s, const double *b, double *x, const fem_pcg_opts
 int pcg_advance(fem_pcg *s, bool blocking);
 int pcg_solve(fem_pcg *s, const double *b, double *x, const fem_pcg_opts *o, fem_pcg_info *info, cudaStream_t st);
 int pcg_status(const fem_pcg *s, fem_pcg_info *info);
-constexpr int kPcgScalars = 13;  // doubles of pinned host memory a solver context needs
+// Host-side fault injection: the solver's next solve reports its first
+// inner step (FP64 mode: its first chunk) as if a device wait had given up.
+void pcg_arm_wait_fault(fem_pcg *s);
+// 1 when no step of the solve is in flight on its stream, 0 while one is,
+// -1 on a CUDA error (non-blocking).
+int pcg_quiescent(fem_pcg *s);
+constexpr int kPcgScalars = 14;  // doubles of pinned host memory a solver context needs
 
 }  // namespace fem

@@ -43,6 +43,7 @@ enum {
     S_RR_OUTER,  // FP64 residual norm^2 of the defect-correction loop
     S_GMAX,      // FEM_PCG_MIXED16: largest |factor| (bits of a non-negative double)
     S_GINV,      // FEM_PCG_MIXED16: inverse of the FP16 factor scale
+    S_WAITFAIL,  // set to 1 by a kernel whose bounded device wait gave up
     S_COUNT
 };
 
@@ -488,6 +489,7 @@ struct fem_pcg {
     double *g_x;
     double g_tol, g_itol;          // and the tolerances
     bool use_graphs;               // not on the legacy default stream, which cannot be captured
+    bool wait_fault_armed;         // host-side fault injection (fem_pcg_inject_fault)
 };
 
 namespace fem {
@@ -495,7 +497,8 @@ namespace fem {
 cudaError_t launch_bp35_pcg(const fem_basis *b, int64_t E, const double *G, double lambda, const double *z,
                             double *p, const double *beta, double *Ap, double *partials, cudaStream_t s);
 cudaError_t launch_bp35_pcg_f32(const fem_basis *b, int64_t E, const float *G, double lambda, const float *z,
-                                float *p, const double *beta, float *Ap, double *partials, cudaStream_t s);
+                                float *p, const double *beta, float *Ap, double *partials, cudaStream_t s,
+                                double *status);
 int64_t bp35_max_blocks(int N, int64_t E);
 int64_t bp35_blocks(int N, int64_t E, bool f32);
 cudaError_t launch_bp35(const fem_basis *b, int64_t E, const double *G, double lambda, const double *q, double *Aq,
@@ -526,10 +529,11 @@ cudaError_t op_pcg(fem_pcg *s, const float *G, const float *z, float *p, float *
         return s->op == FEM_OP_BP30 ? launch_bp30_pcg_f16g(s->basis, s->E, s->G16, s->scal + S_GINV, s->lambda, z, p,
                                                            s->scal + S_BETA, Ap, s->part, st)
                                     : launch_bp35_pcg_f16g(s->basis, s->E, s->G16, s->scal + S_GINV, s->lambda, z, p,
-                                                           s->scal + S_BETA, Ap, s->part, st);
+                                                           s->scal + S_BETA, Ap, s->part, st, s->scal + S_WAITFAIL);
     return s->op == FEM_OP_BP30
                ? launch_bp30_pcg_f32(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, s->part, st)
-               : launch_bp35_pcg_f32(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, s->part, st);
+               : launch_bp35_pcg_f32(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, s->part, st,
+                                     s->scal + S_WAITFAIL);
 }
 
 template <typename P>
@@ -577,6 +581,17 @@ cudaError_t outer_body(fem_pcg *s) {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(s->hscal, s->scal, sizeof(double) * S_COUNT, cudaMemcpyDeviceToHost, s->st);
     return e;
+}
+
+__global__ void set_scalar_kernel(double *p, double v) { *p = v; }
+
+// Host-side fault injection: writes the wait-failure word exactly as a
+// kernel whose bounded wait gave up would, once, before the first chunk.
+cudaError_t inject_armed_fault(fem_pcg *s) {
+    if (!s->wait_fault_armed) return cudaSuccess;
+    s->wait_fault_armed = false;
+    set_scalar_kernel<<<1, 1, 0, s->st>>>(s->scal + S_WAITFAIL, 1.0);
+    return cudaGetLastError();
 }
 
 // Captures whatever `body` enqueues on s->st into an executable graph.
@@ -762,7 +777,8 @@ cudaError_t pcg_begin(fem_pcg *s, const double *b, double *x, const fem_pcg_opts
     s->restart_rr = 0.0;
     s->status = FEM_OK;
     std::memset(&s->info, 0, sizeof s->info);
-    cudaError_t e = launch_dot(s->len, b, b, s->scal + S_BB, s->part, st);
+    cudaError_t e = cudaMemsetAsync(s->scal + S_WAITFAIL, 0, sizeof(double), st);
+    if (e == cudaSuccess) e = launch_dot(s->len, b, b, s->scal + S_BB, s->part, st);
     if (e == cudaSuccess) e = end_step(s);
     s->state = PS_BB;
     return e;
@@ -786,9 +802,23 @@ int pcg_advance(fem_pcg *s, bool blocking) {
     }
     const double *h = s->hscal;
     cudaError_t e = cudaSuccess;
+    if (h[S_WAITFAIL] != 0.0) {
+        // a kernel of the last step gave up a bounded device wait: its
+        // output, and so x, are not to be trusted
+        s->status = FEM_ETIMEDOUT;
+        s->info.iters = s->inner_iters + (s->mode == FEM_PCG_FP64 ? (int)h[S_ITER] : 0);
+        s->info.outer = s->outer;
+        s->state = PS_DONE;
+        return 1;
+    }
     switch (s->state) {
         case PS_BB:
             s->bb = h[S_BB];
+            if (!std::isfinite(s->bb)) {  // a NaN or an infinity in the right-hand side
+                s->status = FEM_EBREAKDOWN;
+                s->state = PS_DONE;
+                return 1;
+            }
             if (s->bb == 0.0) {  // the solution of A x = 0 is 0
                 e = cudaMemsetAsync(s->x, 0, sizeof(double) * s->len, s->st);
                 s->state = PS_DONE;
@@ -804,6 +834,7 @@ int pcg_advance(fem_pcg *s, bool blocking) {
                     e = cudaGetLastError();
                 }
                 const int c = next_chunk(s, 0, s->maxit);
+                if (e == cudaSuccess) e = inject_armed_fault(s);
                 if (e == cudaSuccess) e = enqueue_chunk<double, double>(s, s->G, s->x, s->p, s->r, s->q, s->z, s->dinv, c);
                 s->chunk_done = c;
                 s->state = PS_RUN64;
@@ -879,7 +910,9 @@ int pcg_advance(fem_pcg *s, bool blocking) {
             }
             s->chunk_done = 0;
             const int c = next_chunk(s, 0, s->imaxit);
-            e = enqueue_chunk<float, float>(s, s->G32, s->d32, s->p32, s->r32, s->q32, s->z32, s->dinv32, c);
+            e = inject_armed_fault(s);
+            if (e == cudaSuccess)
+                e = enqueue_chunk<float, float>(s, s->G32, s->d32, s->p32, s->r32, s->q32, s->z32, s->dinv32, c);
             s->chunk_done = c;
             s->state = PS_INNER;
             break;
@@ -994,6 +1027,16 @@ int pcg_status(const fem_pcg *s, fem_pcg_info *info) {
     return s->status;
 }
 
+void pcg_arm_wait_fault(fem_pcg *s) { s->wait_fault_armed = true; }
+
+int pcg_quiescent(fem_pcg *s) {
+    if (!s->pending) return 1;
+    const cudaError_t q = cudaEventQuery(s->ev);
+    if (q == cudaErrorNotReady) return 0;
+    s->pending = false;
+    return q == cudaSuccess ? 1 : -1;
+}
+
 static_assert(kPcgScalars == S_COUNT, "pinned scalar block size");
 
 }  // namespace fem
@@ -1019,6 +1062,12 @@ void fem_pcg_destroy(fem_pcg *s) {
     if (!s) return;
     fem::pcg_release(s);
     delete s;
+}
+
+int fem_pcg_inject_fault(fem_pcg *s, int fault) {
+    if (!s || fault != FEM_FAULT_WAIT_TIMEOUT) return FEM_EINVAL;
+    fem::pcg_arm_wait_fault(s);
+    return FEM_OK;
 }
 
 int fem_pcg_solve(fem_pcg *s, const double *rhs, double *x, const fem_pcg_opts *opts, fem_pcg_info *info,

@@ -35,6 +35,7 @@ struct Request {
     fem_pcg *pcg;
     double *verts_d, *G, *rhs_d, *x_d;
     bool finishing;  // solve finished, x on its way to the host
+    bool cancel;     // cancelled while running: retire once no step is in flight
     cudaEvent_t done_ev;
 };
 
@@ -66,7 +67,10 @@ double est_work(const fem_serve_request &r) {
     const double n = r.N + 1.0;
     double w = std::pow((double)r.E, 4.0 / 3.0) * n * n * n * r.N * std::log(1.0 / r.tol);
     if (r.op == FEM_OP_BP30) w *= 2.5;
-    if (r.mode != FEM_PCG_FP64) w *= 0.15;
+    if (r.mode == FEM_PCG_MIXED_TC)
+        w *= 0.3;  // the tensor-core inner operator measured about twice the FP32 one's time
+    else if (r.mode != FEM_PCG_FP64)
+        w *= 0.15;
     return w;
 }
 
@@ -154,6 +158,7 @@ int fem_serve_create(const fem_serve_opts *opts, fem_server **out) {
     o.max_active = (opts && opts->max_active > 0) ? opts->max_active : 8;
     o.check_every = (opts && opts->check_every > 0) ? opts->check_every : 8;
     o.policy = opts ? opts->policy : FEM_SERVE_FIFO;
+    o.max_wait_s = (opts && opts->max_wait_s > 0.0) ? opts->max_wait_s : 2.0;
     if (o.max_active > 256 || (o.policy != FEM_SERVE_FIFO && o.policy != FEM_SERVE_SHORTEST)) return FEM_EINVAL;
     fem_server *s = new (std::nothrow) fem_server();
     if (!s) return FEM_ENOMEM;
@@ -211,6 +216,21 @@ int fem_serve_progress(fem_server *s, int *active, int *queued) {
     for (size_t k = 0; k < s->running.size();) {
         Request &R = s->reqs[s->running[k]];
         bool retire = false;
+        if (R.cancel && !R.finishing) {
+            // no further step is enqueued; the request retires once the step
+            // in flight (if any) has finished on its stream
+            const int q = fem::pcg_quiescent(R.pcg);
+            if (q != 0) {
+                R.res.state = FEM_REQ_FAILED;
+                R.res.status = q > 0 ? FEM_ECANCELED : fem::record_cuda_error(cudaGetLastError());
+                R.res.t_done = now_s(s->t0);
+                release(s, R);
+                s->running.erase(s->running.begin() + k);
+            } else {
+                k++;
+            }
+            continue;
+        }
         if (!R.finishing) {
             const int r = fem::pcg_advance(R.pcg, false);
             if (r < 0) {
@@ -257,9 +277,13 @@ int fem_serve_progress(fem_server *s, int *active, int *queued) {
         }
     }
     // 2. admit from the head of the queue (first come, first served), or
-    // the least estimated work first (ties by arrival)
+    // the least estimated work first (ties by arrival) among the requests
+    // that have waited less than max_wait_s: once the oldest request has
+    // waited that long it goes first (aging), so a large request is not
+    // starved by a stream of smaller ones
     while (!s->queue.empty()) {
-        if (s->opts.policy == FEM_SERVE_SHORTEST) {
+        if (s->opts.policy == FEM_SERVE_SHORTEST &&
+            now_s(s->t0) - s->reqs[s->queue.front()].res.t_submit < s->opts.max_wait_s) {
             auto best = s->queue.begin();
             for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
                 if (s->reqs[*it].work < s->reqs[*best].work) best = it;
@@ -312,6 +336,45 @@ int fem_serve_poll(fem_server *s, int64_t id, fem_serve_result *res) {
     if (it == s->reqs.end()) return FEM_EINVAL;
     *res = it->second.res;
     return FEM_OK;
+}
+
+int fem_serve_wait(fem_server *s, int64_t id, double timeout_s, fem_serve_result *res) {
+    if (!s || !res || !(timeout_s >= 0.0)) return FEM_EINVAL;
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return FEM_EINVAL;
+    const double deadline = now_s(s->t0) + timeout_s;
+    for (;;) {
+        const int st = it->second.res.state;
+        if (st == FEM_REQ_DONE || st == FEM_REQ_FAILED) break;
+        if (now_s(s->t0) >= deadline) {
+            *res = it->second.res;
+            return FEM_ETIMEDOUT;
+        }
+        const int r = fem_serve_progress(s, nullptr, nullptr);
+        if (r != FEM_OK) return r;
+    }
+    *res = it->second.res;
+    return FEM_OK;
+}
+
+int fem_serve_cancel(fem_server *s, int64_t id) {
+    if (!s) return FEM_EINVAL;
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return FEM_EINVAL;
+    Request &R = it->second;
+    if (R.res.state == FEM_REQ_QUEUED) {
+        for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+            if (*q == id) {
+                s->queue.erase(q);
+                break;
+            }
+        R.res.state = FEM_REQ_FAILED;
+        R.res.status = FEM_ECANCELED;
+        R.res.t_done = now_s(s->t0);
+        return FEM_OK;
+    }
+    if (R.res.state == FEM_REQ_RUNNING && !R.finishing) R.cancel = true;
+    return FEM_OK;  // finishing, done or failed: nothing to cancel
 }
 
 int64_t fem_serve_in_use(const fem_server *s) { return s ? s->in_use : 0; }

@@ -89,30 +89,41 @@ __global__ void __launch_bounds__(256) fma_probe_kernel(int64_t iters, double b,
 
 // Self-test of the bounded mbarrier wait: one block waits on a barrier
 // that expects two arrivals and gets one, so the phase never completes; every
-// wait must give up after its iteration limit and count itself, and the
-// kernel must return normally.
+// wait must give up after its iteration limit and count itself, the block
+// must report the failure through a status word the way the stream kernels
+// report it to the solver, and the kernel must return normally.
 namespace {
-__global__ void __launch_bounds__(64) wait_selftest_kernel() {
+__global__ void __launch_bounds__(64) wait_selftest_kernel(double *status) {
     __shared__ __align__(8) uint64_t bar;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 2);
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(&bar)) : "memory");
     }
     __syncthreads();
-    if (!mbar_wait(&bar, 0) && (threadIdx.x & 31) == 0) atomicAdd(&g_wait_timeouts, 1ull);
+    const bool done = mbar_wait(&bar, 0);
+    if (!done && (threadIdx.x & 31) == 0) atomicAdd(&g_wait_timeouts, 1ull);
+    if (!__syncthreads_and(done) && threadIdx.x == 0) *status = 1.0;
 }
+__device__ double g_selftest_status;
 }  // namespace
 
 FEM_DEFINE_WAIT_COUNTER(wait_timeouts_selftest)
 
-cudaError_t run_wait_selftest(unsigned long long *gave_up) {
+cudaError_t run_wait_selftest(unsigned long long *gave_up, bool *reported) {
     unsigned long long zero = 0;
     cudaError_t e = wait_timeouts_selftest(&zero, true);
+    const double z = 0.0;
+    double *st = nullptr;
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_selftest_status, &z, sizeof z);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress((void **)&st, g_selftest_status);
     if (e != cudaSuccess) return e;
-    wait_selftest_kernel<<<1, 64>>>();
+    wait_selftest_kernel<<<1, 64>>>(st);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = wait_timeouts_selftest(gave_up, true);
+    double v = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(&v, g_selftest_status, sizeof v);
+    *reported = (v != 0.0);
     return e;
 }
 

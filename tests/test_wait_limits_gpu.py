@@ -14,7 +14,9 @@ pytestmark = pytest.mark.gpu
 def test_bounded_wait_gives_up_and_the_context_stays_usable():
     import torch
     import paper_1711_00903_gb300 as fem
-    assert fem.fem_wait_selftest() == 2  # both warps of the block gave up
+    gave_up, code = fem.fem_wait_selftest()
+    assert gave_up == 2  # both warps of the block gave up
+    assert code == fem.FEM_ETIMEDOUT  # and the block reported it through its status word
     # the same process then runs the stream kernel normally
     fem.fem_wait_timeouts(reset=True)
     N = 7
