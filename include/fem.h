@@ -313,11 +313,11 @@ int fem_dot(int64_t n, const double *x, const double *y, double *result, double 
             void *stream);
 
 /* The same dot product without any device allocation, for callers that
- * cannot call cudaMalloc where they need the reduction: code running while a
- * stream is captured into a CUDA graph, a serving loop that must not
- * allocate per request (an allocation can synchronise the device or fail
- * under a fixed memory budget), or an application whose device memory is
- * owned by its own allocator.  The paper has no counterpart; this is a
+ * cannot call cudaMalloc where they need the reduction: a serving loop that
+ * must not allocate per request (an allocation can synchronise the device
+ * or fail under a fixed memory budget), or an application whose device
+ * memory is owned by its own allocator, so that a library may not take
+ * memory behind its back.  The paper has no counterpart; this is a
  * library convenience.  The caller passes x, y (device, n doubles) and
  * result (device, one double) only.  The partial sums live in a 32 KiB
  * device array inside the library (one partial per 8192 entries), which
@@ -325,7 +325,9 @@ int fem_dot(int64_t n, const double *x, const double *y, double *result, double 
  * capped at fem_dot_noalloc_max_n() = 33,554,432; larger n returns
  * FEM_ETOOBIG without launching anything.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call
+ * current and keeps it for the rest of the process; make that first call
+ * before any stream capture.  cudaDeviceReset of that device after the
+ * first call is not supported (the kept address would be stale).  Every call
  * shares the array and overwrites the slots it uses (nothing needs
  * clearing), so calls that overlap on the GPU (different streams, or
  * several host threads) race and must be serialised by the caller.

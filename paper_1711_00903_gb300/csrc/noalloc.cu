@@ -2,12 +2,10 @@
 // file-scope device array instead of caller- or library-allocated memory.
 //
 // Who needs it: callers that cannot call cudaMalloc at the point where they
-// need a reduction -- code that runs while a stream is being captured into a
-// CUDA graph (an allocation there is not part of the graph and may be
-// refused), a serving loop that must not allocate per request because an
-// allocation can synchronise the device or fail under a fixed memory budget,
-// and embedding applications whose device memory is owned by their own
-// allocator.  They pass inputs and the output only.
+// need a reduction -- a serving loop that must not allocate per request
+// because an allocation can synchronise the device or fail under a fixed
+// memory budget, and embedding applications whose device memory is owned by
+// their own allocator.  They pass inputs and the output only.
 //
 // The scratch array is small (kNoallocParts doubles, 32 KiB) and every GPU
 // that loads the library holds it until the process exits.  Each block of
@@ -54,7 +52,9 @@ noalloc_final_kernel(int nparts, const double *__restrict__ part, double *__rest
 }
 
 // Device address of the scratch array, looked up once per device with that
-// device current (in host code the symbol is only a host-side stand-in).
+// device current (in host code the symbol is only a host-side stand-in) and
+// kept for the process: a cudaDeviceReset of the device after the first call
+// would leave it stale, which the header states as unsupported.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double *g_addr[kMaxDevices] = {};

@@ -1,9 +1,8 @@
 """The allocation-free dot product (fem_dot_noalloc) through the C ABI.
 
 It serves callers that cannot allocate device memory where they need a
-reduction (inside a stream capture, in a serving loop with a fixed memory
-budget, under an application-owned allocator): its partial sums live in a
-device array inside the library.  This file is collected last so that a run
+reduction (a serving loop with a fixed memory budget, an application-owned
+allocator): its partial sums live in a device array inside the library.  This file is collected last so that a run
 stopping at the first failure has already run every other test; it also
 passes alone in a fresh process (the first call performs the one-time
 device set-up)."""
