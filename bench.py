@@ -107,6 +107,9 @@ def alg_counts(N: int):
     fma_pts = 2 * (m * n3 + m * m * n * n + m3 * n) + 6 * m ** 4  # direct contractions of the point layout
     inst = {
         "bp30_points": fma_pts + m3 * (9 + 3 + 2),  # (lambda wJ) q as two products
+        # one thread per node: 3 derivatives and 3 transposed derivatives of
+        # length n per node, the 3x3 product and (lambda wJ) q
+        "bp35_points": 6 * n ** 4 + n3 * (9 + 2),
         "bp1": (nn + m * n + mm) * (i_mn + i_nm) + m3,
         "bp35": 6 * nn * i_dd + n3 * (9 + lam_i + 2),
         "bp30": (nn + m * n + mm) * (i_mn + i_nm) + 6 * mm * i_gg + m3 * (9 + lam_i + 2),
@@ -118,6 +121,7 @@ def alg_counts(N: int):
     }
     std = {
         "bp30_points": 2 * interp + 12 * m ** 4 + 18 * m3,
+        "bp35_points": 12 * n ** 4 + 18 * n3,
         "bp1": 2 * interp + m3,
         "bp35": 12 * n ** 4 + 18 * n3,
         "bp30": 2 * interp + 12 * m ** 4 + 18 * m3,
@@ -127,6 +131,7 @@ def alg_counts(N: int):
     }
     byts = {
         "bp30_points": 8 * (2 * n3 + 7 * m3),
+        "bp35_points": 8 * (9 * n3),
         "geofacs_bp30_bp1": 8 * (24 + 8 * m3),
         "geofacs_bp35": 8 * (24 + 7 * n3),
         "bp1": 8 * (2 * n3 + m3),
@@ -148,7 +153,9 @@ def smem_counts(N: int, word: int = 8):
            projection phases plus the Gauss-point derivative, chain-rule and
            transpose phases);
     BP3.0, point layout: two words per multiply-add (operand and operator
-           entry) plus every phase output."""
+           entry) plus every phase output;
+    BP3.5, point layout: likewise, 6 n^4 multiply-adds and 5 n^3 stores
+           and loads of whole boxes."""
     n, m = N + 1, N + 2
     # point layout: every multiply-add reads an operand and an operator entry
     # from shared memory; every phase output is stored once
@@ -156,6 +163,9 @@ def smem_counts(N: int, word: int = 8):
     outs_pts = n ** 3 + 2 * (m * n * n + m * m * n) + 5 * m ** 3 + n ** 3
     return {
         "bp30_points": word * (2 * fma_pts + outs_pts + m ** 3),
+        # one thread per node: operand and operator entry per multiply-add,
+        # the staged field, the three products stored and q read for the mass term
+        "bp35_points": word * (2 * 6 * n ** 4 + 5 * n ** 3),
         "bp1": word * (2 * n ** 3 + 3 * m * n * n + 4 * m * m * n),
         "bp35": word * 17 * n ** 3,
         "bp30": word * (2 * n ** 3 + 3 * m * n * n + 4 * m * m * n + 16 * m ** 3),
@@ -799,13 +809,13 @@ def run_sweep(fem, torch, device, verts, args, sm_mhz):
         std, inst, byts = alg_counts(N)
         smem = smem_counts(N)
         row = {"N": N, "dofs": E * n ** 3}
-        for name, kind in (("bp1", 1), ("bp35", 2), ("bp30", 3), ("bp1_bp30", 3), ("bp30_points", 3),
+        for name, kind in (("bp1", 1), ("bp35", 2), ("bp30", 3), ("bp1_bp30", 3), ("bp30_points", 3), ("bp35_points", 2),
                            ("bp35_f32", 2), ("bp30_f32", 3), ("bp35_f16", 2), ("bp30_f16", 3),
                            ("bp30_f32_warp", 3), ("bp30_tc", 3)):
             f16 = name.endswith("_f16")
             f32 = name.endswith("_f32") or f16 or name in ("bp30_f32_warp", "bp30_tc")
             base = "bp30" if name in ("bp30_f32_warp", "bp30_tc") else (name[:-4] if f32 else name)
-            ratio_base = "bp30" if base in ("bp30_points", "bp1_bp30") else base
+            ratio_base = "bp30" if base in ("bp30_points", "bp1_bp30") else ("bp35" if base == "bp35_points" else base)
             geo = torch.empty(fem.geo_shape(b, kind, E), dtype=torch.float64, device=device)
             fem.fem_mesh_geofacs(b, kind, verts, geo=geo, stream=stream)
             if f16:
@@ -837,6 +847,9 @@ def run_sweep(fem, torch, device, verts, args, sm_mhz):
                 del out2
             elif name == "bp30_points":
                 ms = timed(lambda: fem.fem_bp30_apply_layout(b, geo, lam, q, fem.FEM_LAYOUT_POINTS, out=out,
+                                                             stream=stream), reps)
+            elif name == "bp35_points":
+                ms = timed(lambda: fem.fem_bp35_apply_layout(b, geo, lam, q, fem.FEM_LAYOUT_POINTS, out=out,
                                                              stream=stream), reps)
             elif name == "bp1":
                 ms = timed(lambda: fem.fem_bp1_apply(b, geo, q, out=out, stream=stream), reps)

@@ -224,6 +224,14 @@ int fem_bp30_apply_f16g(const fem_basis *b, int64_t E, const void *G16, const do
 int fem_bp30_apply_layout(const fem_basis *b, int64_t E, const double *G, double lambda,
                           const double *q, double *Aq, int layout, void *stream);
 
+/* fem_bp35_apply with a chosen thread layout: FEM_LAYOUT_LINES (the
+ * default kernels) or FEM_LAYOUT_POINTS (Algorithm 7: one thread per GLL
+ * node, one element per block, D in shared memory).  Same arguments,
+ * layouts and errors (FEM_EINVAL for another layout); both compute the
+ * same operator and agree to rounding. */
+int fem_bp35_apply_layout(const fem_basis *b, int64_t E, const double *G, double lambda,
+                          const double *q, double *Aq, int layout, void *stream);
+
 /* BP3.0 matvec in FP32 (Algorithm 5 with float data and FP32 arithmetic;
  * the inner operator of the mixed-precision BP3.0 solver).  Same layouts as
  * fem_bp30_apply: G device E*7*m^3 floats, q and Aq device E*n^3 floats,
@@ -434,8 +442,9 @@ void fem_pcg_destroy(fem_pcg *s);
  * with its own operator (BP3.5 or BP3.0, FP64), factors, lambda, input and
  * output, applied in ONE persistent launch (Section 4: every element is
  * independent, so meshes are just more elements).  Each element's result is
- * bit-identical to the per-mesh fem_bp35_apply / fem_bp30_apply_layout call
- * with the batch's layout.
+ * bit-identical to the per-mesh fem_bp35_apply_layout / fem_bp30_apply_layout
+ * call with the layout the batch's configuration gives its operator and
+ * degree.
  * --------------------------------------------------------------------- */
 
 typedef struct {
@@ -452,10 +461,15 @@ typedef struct {
     int threads; /* threads per persistent block: 256 or 512              */
     int group;   /* tasks taken per fetch of the shared counter, 1..64    */
     int order;   /* 0: tasks by decreasing cost per element; 1: as given  */
-    int layout;  /* BP3.0 tasks up to N = 8: FEM_LAYOUT_LINES (default) or
-                  * FEM_LAYOUT_POINTS (one thread per Gauss point)         */
+    int layout;  /* thread layout of the tasks, a bit mask (0: lines, the
+                  * default): FEM_BATCH_POINTS30 puts BP3.0 tasks up to N = 8,
+                  * FEM_BATCH_POINTS35 BP3.5 tasks up to N = 9, in the point
+                  * layout (one thread per quadrature point or node)        */
     float ms;    /* measured time of one launch (fem_batch_tune), or 0    */
 } fem_batch_config;
+
+#define FEM_BATCH_POINTS30 1 /* = FEM_LAYOUT_POINTS: BP3.0 tasks in the point layout */
+#define FEM_BATCH_POINTS35 2 /* BP3.5 tasks in the point layout                    */
 
 typedef struct fem_batch fem_batch; /* opaque */
 
@@ -471,8 +485,10 @@ int fem_batch_create(const fem_batch_item *items, int count, fem_batch **out);
 int fem_batch_apply(fem_batch *b, void *stream);
 
 /* Autotuner: times every configuration (threads 256/512 x group 1/2/4/8 x
- * both task orders x both BP3.0 layouts when the batch has BP3.0 meshes of
- * degree <= 8; reps launches each after a warm-up) on the batch itself,
+ * both task orders x the layout masks that change something: BP3.0 points
+ * when the batch has BP3.0 meshes of degree <= 8, BP3.5 points when it has
+ * BP3.5 meshes of degree <= 9, and both; reps launches each after a
+ * warm-up) on the batch itself,
  * keeps the fastest as the batch's configuration, and writes up to
  * max_results timings to results (may be NULL) and their count to
  * *nresults (may be NULL).  Synchronous.  Errors: FEM_EINVAL, FEM_ECUDA. */

@@ -313,6 +313,16 @@ int fem_bp30_apply_layout(const fem_basis *b, int64_t E, const double *G, double
     return e == cudaSuccess ? FEM_OK : cuda_fail(e);
 }
 
+int fem_bp35_apply_layout(const fem_basis *b, int64_t E, const double *G, double lambda, const double *q,
+                          double *Aq, int layout, void *stream) {
+    if (layout != FEM_LAYOUT_LINES && layout != FEM_LAYOUT_POINTS) return FEM_EINVAL;
+    if (layout == FEM_LAYOUT_LINES) return fem_bp35_apply(b, E, G, lambda, q, Aq, stream);
+    const int c = check_apply(b, E, G, b ? 7 * cube(b->host.n) : 0, q, Aq);
+    if (c != FEM_OK || E == 0) return c;
+    cudaError_t e = fem::launch_bp35_point(b, E, G, lambda, q, Aq, (cudaStream_t)stream);
+    return e == cudaSuccess ? FEM_OK : cuda_fail(e);
+}
+
 int fem_bp30_apply_f32(const fem_basis *b, int64_t E, const float *G, double lambda, const float *q, float *Aq,
                        void *stream) {
     if (!b || E < 0) return FEM_EINVAL;

@@ -12,8 +12,9 @@
 // is made of cheap tasks.
 //
 // The launch shape (threads per block, tasks per counter fetch, task order,
-// and the thread layout of BP3.0 tasks up to N = 8: lines or one thread per
-// Gauss point, bp30_point.cuh) is chosen by a small autotuner that times
+// and the thread layout per operator: lines, or one thread per point for
+// BP3.0 tasks up to N = 8 (bp30_point.cuh) and BP3.5 tasks up to N = 9
+// (bp35_point.cuh, Algorithm 7)) is chosen by a small autotuner that times
 // every candidate on the batch itself; the chosen configuration can be
 // replayed from a CUDA graph that contains the counter reset and the kernel.
 #include <algorithm>
@@ -24,12 +25,14 @@
 #include "bp30_body.cuh"
 #include "bp30_point.cuh"
 #include "bp35_body.cuh"
+#include "bp35_point.cuh"
 
 namespace fem {
 namespace {
 
 constexpr int kBatchMaxN = 10;
-constexpr int kBatchMaxPointN = 8;  // point layout: m^3 <= 1000 points, 4 m^3 doubles of shared memory
+constexpr int kBatchMaxPointN = 8;    // BP3.0 point layout: m^3 <= 1000 points, 4 m^3 doubles of shared memory
+constexpr int kBatchMaxPointN35 = 9;  // BP3.5 point layout: n^3 <= 1000 nodes
 constexpr int kBatchSmemBudget = 96 * 1024;
 
 struct BatchMesh {
@@ -69,8 +72,10 @@ constexpr int batch_smem_n() {
     constexpr int s35 = Bp35Layout<double, N, Epb35<THREADS, N>::v>::smem;
     constexpr int s30 = Bp30Layout<N, Epb30<THREADS, N>::v>::smem;
     constexpr int sp = N <= kBatchMaxPointN ? Bp30Point<N>::smem : 0;
+    constexpr int sp35 = N <= kBatchMaxPointN35 ? Bp35Point<N>::smem : 0;
     constexpr int s = s35 > s30 ? s35 : s30;
-    return s > sp ? s : sp;
+    constexpr int t = s > sp ? s : sp;
+    return t > sp35 ? t : sp35;
 }
 
 template <int THREADS>
@@ -111,12 +116,19 @@ template <int THREADS, int K>
 __device__ __noinline__ void task30(unsigned char *smem, const BatchTask tk, const BatchMesh M) {
     bp30_block<K, Epb30<THREADS, K>::v>(reinterpret_cast<double *>(smem), tk.e0, tk.nel, M.G, M.lambda, M.q, M.out);
 }
-// the same task in the point layout: its elements one after the other
+// the same tasks in the point layouts: their elements one after the other
 template <int THREADS, int K>
 __device__ __noinline__ void task30_point(unsigned char *smem, const BatchTask tk, const BatchMesh M) {
     for (int el = 0; el < tk.nel; el++) {
         if (el > 0) __syncthreads();
         bp30_point_block<K, THREADS>(reinterpret_cast<double *>(smem), M.ops, tk.e0 + el, M.G, M.lambda, M.q, M.out);
+    }
+}
+template <int THREADS, int K>
+__device__ __noinline__ void task35_point(unsigned char *smem, const BatchTask tk, const BatchMesh M) {
+    for (int el = 0; el < tk.nel; el++) {
+        if (el > 0) __syncthreads();
+        bp35_point_block<K, THREADS>(reinterpret_cast<double *>(smem), M.ops, tk.e0 + el, M.G, M.lambda, M.q, M.out);
     }
 }
 
@@ -140,10 +152,13 @@ batch_kernel(const BatchMesh *__restrict__ meshes, const BatchTask *__restrict__
             switch (M.op * 16 + M.N) {
 #define FEM_TASK(K)                                           \
     case FEM_OP_BP35 * 16 + K:                                \
-        task35<THREADS, K>(smem, tk, M);                      \
+        if (K <= kBatchMaxPointN35 && (layout & FEM_BATCH_POINTS35)) \
+            task35_point<THREADS, (K <= kBatchMaxPointN35 ? K : 1)>(smem, tk, M); \
+        else                                                  \
+            task35<THREADS, K>(smem, tk, M);                  \
         break;                                                \
     case FEM_OP_BP30 * 16 + K:                                \
-        if (K <= kBatchMaxPointN && layout == FEM_LAYOUT_POINTS) \
+        if (K <= kBatchMaxPointN && (layout & FEM_BATCH_POINTS30)) \
             task30_point<THREADS, (K <= kBatchMaxPointN ? K : 1)>(smem, tk, M); \
         else                                                  \
             task30<THREADS, K>(smem, tk, M);                  \
@@ -252,7 +267,8 @@ void release(fem_batch *b) {
 
 bool valid_config(const fem_batch_config *c) {
     return c && (c->threads == 256 || c->threads == 512) && c->group >= 1 && c->group <= 64 &&
-           (c->order == 0 || c->order == 1) && (c->layout == FEM_LAYOUT_LINES || c->layout == FEM_LAYOUT_POINTS);
+           (c->order == 0 || c->order == 1) && c->layout >= 0 &&
+           c->layout <= (FEM_BATCH_POINTS30 | FEM_BATCH_POINTS35);
 }
 
 }  // namespace
@@ -346,11 +362,15 @@ int fem_batch_tune(fem_batch *b, void *stream, int reps, fem_batch_config *resul
     if (!b || reps < 1) return FEM_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     const int threads[2] = {256, 512}, groups[4] = {1, 2, 4, 8};
-    // the point layout is a candidate only when the batch has BP3.0 meshes it applies to
-    bool point_ok = false;
-    for (const fem::BatchMesh &m : b->host_meshes)
-        point_ok = point_ok || (m.op == FEM_OP_BP30 && m.N <= fem::kBatchMaxPointN && m.E > 0);
-    const int nlayouts = point_ok ? 2 : 1;
+    // a point layout is a candidate only when the batch has meshes it applies to
+    bool p30 = false, p35 = false;
+    for (const fem::BatchMesh &m : b->host_meshes) {
+        p30 = p30 || (m.op == FEM_OP_BP30 && m.N <= fem::kBatchMaxPointN && m.E > 0);
+        p35 = p35 || (m.op == FEM_OP_BP35 && m.N <= fem::kBatchMaxPointN35 && m.E > 0);
+    }
+    int layouts[4], nlayouts = 0;
+    for (int l = 0; l <= (FEM_BATCH_POINTS30 | FEM_BATCH_POINTS35); l++)
+        if ((!(l & FEM_BATCH_POINTS30) || p30) && (!(l & FEM_BATCH_POINTS35) || p35)) layouts[nlayouts++] = l;
     cudaEvent_t e0, e1;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -366,7 +386,7 @@ int fem_batch_tune(fem_batch *b, void *stream, int reps, fem_batch_config *resul
                 c.threads = threads[ti];
                 c.group = groups[gi];
                 c.order = order;
-                c.layout = li;
+                c.layout = layouts[li];
                 e = fem::launch(b, c, s);  // warm-up
                 if (e == cudaSuccess) e = cudaEventRecord(e0, s);
                 for (int r = 0; r < reps && e == cudaSuccess; r++) e = fem::launch(b, c, s);

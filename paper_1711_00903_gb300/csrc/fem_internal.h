@@ -84,7 +84,9 @@ int record_cuda_error(cudaError_t e);
 // BP3.0 launchers for the solver (FP32 plain and both PCG-fused variants).
 cudaError_t launch_bp30_point(const fem_basis *b, int64_t E, const double *G, double lambda, const double *q,
                               double *Aq, cudaStream_t s);
-cudaError_t prepare_bp30_point(int N);
+cudaError_t prepare_bp30_point(int N);  // and the BP3.5 point kernels
+cudaError_t launch_bp35_point(const fem_basis *b, int64_t E, const double *G, double lambda, const double *q,
+                              double *Aq, cudaStream_t s);
 cudaError_t launch_bp30_f32(const fem_basis *b, int64_t E, const float *G, double lambda, const float *q,
                             float *Aq, cudaStream_t s);
 cudaError_t launch_bp30_pcg(const fem_basis *b, int64_t E, const double *G, double lambda, const double *z,

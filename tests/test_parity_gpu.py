@@ -152,6 +152,22 @@ def test_bp30_point_layout_parity(bases, N, lam):
     assert _rel(got, ref) < TOL
 
 
+@pytest.mark.parametrize("lam", [0.0, 1.0, 0.37])
+@pytest.mark.parametrize("N", range(1, 16))
+def test_bp35_point_layout_parity(bases, N, lam):
+    """The point-per-thread layout of BP3.5 (Algorithm 7) against the oracle,
+    with a ragged element count (one element per block; above n^3 = 1024
+    nodes a thread takes several)."""
+    fem = _fem()
+    v, q = _ops(N, E_RAGGED, lam)
+    G, _ = oracle.geofacs(N, oracle.KIND_BP35, v)
+    ref = oracle.bp35(N, G, lam, q)
+    got = fem.fem_bp35_apply_layout(bases[N], _dev(G), lam, _dev(q), fem.FEM_LAYOUT_POINTS).cpu().numpy()
+    assert _rel(got, ref) < TOL
+    lines = fem.fem_bp35_apply_layout(bases[N], _dev(G), lam, _dev(q), fem.FEM_LAYOUT_LINES).cpu().numpy()
+    assert np.array_equal(lines, fem.fem_bp35_apply(bases[N], _dev(G), lam, _dev(q)).cpu().numpy())
+
+
 @pytest.mark.parametrize("N", [1, 2, 7, 15])
 def test_chain_from_vertices(bases, N):
     """Vertices -> device geometric factors -> device operators, against the
