@@ -795,6 +795,11 @@ class Server:
     def cancel(self, rid):
         _check(lib().fem_serve_cancel(self.handle, int(rid)), "fem_serve_cancel")
 
+    def forget(self, rid):
+        """Drops this wrapper's references to a finished request's host
+        arrays (the caller keeps its own x if it needs it)."""
+        self._keep.pop(int(rid), None)
+
     def clock(self) -> float:
         return lib().fem_serve_clock(self.handle)
 

@@ -137,8 +137,11 @@ def _fake_run():
              "persistent_default": {"ms": 25.0, "gdofs": 4.0}, "persistent_tuned": {"ms": 20.0, "gdofs": 5.0,
                                                                                      "config": {"threads": 256}},
              "graph": {"ms": 20.0, "gdofs": 5.0}, "tuner_candidates": 32}
-    serve = {"workload": "s" * 200, "steady_state": {"offered_per_s": 200.0, "solves_per_s": 15.0, "p50_s": 1.0,
-                                                      "p99_s": 3.0, "queue_depth": list(range(300))}}
+    serve = {"workload": "s" * 200,
+             "steady_state": {"arrival_rate_per_s": 12.0, "served_per_s": 12.0, "p50_s": 1.0, "p99_s": 3.0,
+                              "queue_depth": {"every_0.5s": list(range(60))}},
+             "config_arrivals_200_per_s": {"fifo": {"offered_per_s": 200.0, "served_per_s": 15.0, "p50_s": 9.0,
+                                                    "p99_s": 19.0}}}
     return line, {"sweep": sweep, "small_case": {"us_per_launch_graph": 3.0}, "pcg": pcg, "batch": batch,
                   "serve": serve}
 
@@ -162,7 +165,8 @@ def test_headline_is_last_and_compact(capsys, tmp_path):
     for k in ("bound", "achieved", "peak", "unit", "frac", "traffic", "fp64_issue_frac"):
         assert k in head["roofline"], k
     assert head["summary"]["pcg_tol_1e-13"]["mixed_tc"]["rel_diff_vs_fp64_solve"] == 5e-12
-    assert head["summary"]["serve"]["offered_per_s"] == 200.0
+    assert head["summary"]["serve"]["config"]["offered_per_s"] == 200.0
+    assert head["summary"]["serve"]["steady"]["arrival_rate_per_s"] == 12.0
     for ln in out[:-1]:
         assert json.loads(ln)["section"] in sections
     full = json.loads(side.read_text())
