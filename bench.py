@@ -1103,12 +1103,13 @@ def run_serve(fem, torch, args):
     The requests cycle a pool of 32 distinct problems drawn from that
     distribution (each request is tens of MB of host data; the arrival times
     are the configuration's own).  Three runs:
-      config   the configuration's arrival process, first come first served
-               and least estimated work first (with aging): the offered load
-               is far above what one GPU serves, so the queue grows while
-               requests arrive and drains after;
-      steady   the same requests arriving at 0.8 x the measured service
-               rate (the Poisson process rescaled in time): a steady state;
+      config   the configuration's arrival process, first come first served:
+               the offered load is far above what one GPU serves, so the
+               queue grows while requests arrive and drains after;
+      steady   the same request stream arriving at 0.8 x the measured
+               service rate (the Poisson process rescaled in time) for
+               serve_window seconds: a steady state, first come first served
+               and least estimated work first with aging;
       alone    the first 24 problems one at a time, for the check that each
                result is the same bits alone and in the mix.
     Latency percentiles exclude the first 10 % of requests (warm-up); the
@@ -1182,11 +1183,15 @@ def run_serve(fem, torch, args):
         return out, xs
 
     cfg_fifo, xs_mix = play(arrivals)
-    cfg_sjf, _ = play(arrivals, fem.FEM_SERVE_SHORTEST, keep=0)
     rate = 0.8 * cfg_fifo["served_per_s"]
+    # the same Poisson process slowed to `rate`, over a window of
+    # args.serve_window seconds of arrivals
     steady_times = [t * 200.0 / rate for t in arrivals]
-    steady, _ = play(steady_times)
+    steady_times = [t for t in steady_times if t <= args.serve_window] or steady_times[:2]
+    steady, _ = play(steady_times, keep=0)
     steady["arrival_rate_per_s"] = rate
+    steady_sjf, _ = play(steady_times, fem.FEM_SERVE_SHORTEST, keep=0)
+    steady_sjf["arrival_rate_per_s"] = rate
     srv = fem.Server(max_active=1)
     same = True
     for k in range(min(24, n_req)):
@@ -1196,500 +1201,12 @@ def run_serve(fem, torch, args):
     srv.free()
     return {"workload": f"{n_req} requests cycling {pool_n} problems: BP3.0|BP3.5, N 3..9, E 512..32768 "
                         "log-uniform, rhs U[-1,1], tol 1e-8, FP64|mixed (FP16 factors), 120 GiB budget, 8 slots",
-            "config_arrivals_200_per_s": {"fifo": cfg_fifo, "shortest_first_aging": cfg_sjf},
+            "config_arrivals_200_per_s": {"fifo": cfg_fifo},
             "steady_state": steady,
+            "steady_state_shortest_first_aging": steady_sjf,
             "results_identical_alone_and_in_mix": bool(same),
             "identical_check": "the first 24 requests of the config run against the same problems solved one "
                                "at a time"}
-
-
-HEADLINE_MAX_BYTES = 4096
-
-
-def _r(x, digits=4):
-    """x rounded to `digits` significant figures (floats only; containers
-    recursively), to keep the headline line short."""
-    if isinstance(x, float):
-        return float(f"{x:.{digits}g}")
-    if isinstance(x, dict):
-        return {k: _r(v, digits) for k, v in x.items()}
-    if isinstance(x, list):
-        return [_r(v, digits) for v in x]
-    return x
-
-
-def headline_summary(sections):
-    """A few figures of the side sections for the headline: the Helmholtz
-    solves at 1e-13 (where the mixed solves reach the FP64 solution to
-    1e-10), the batch and the serving measurement."""
-    out = {}
-    pcg = sections.get("pcg")
-    if pcg:
-        t = pcg.get("tight", {})
-        out["pcg_tol_1e-13"] = {k: {"solves_per_s": v.get("solves_per_s"),
-                                    "rel_diff_vs_fp64_solve": v.get("rel_diff_vs_fp64_solve"),
-                                    "rel_err_vs_u_I": v.get("rel_err_vs_u_I")}
-                                for k, v in t.items() if isinstance(v, dict)}
-        for k, v in t.items():
-            if k.endswith("_speedup"):
-                out["pcg_tol_1e-13"][k] = v
-        t30 = (pcg.get("bp30") or {}).get("tight", {})
-        if t30:
-            out["pcg_bp30_tol_5e-13"] = {k: (v.get("solves_per_s") if isinstance(v, dict) else v)
-                                         for k, v in t30.items() if k != "tol"}
-    b = sections.get("batch")
-    if b:
-        out["batch_gdofs"] = {"separate": b["separate_launches"]["gdofs"],
-                              "persistent_tuned": b["persistent_tuned"]["gdofs"], "graph": b["graph"]["gdofs"]}
-    sv = sections.get("serve")
-    if sv:
-        st = sv.get("steady_state") or {}
-        cf = (sv.get("config_arrivals_200_per_s") or {}).get("fifo") or {}
-        out["serve"] = {"steady": {k: st.get(k) for k in ("arrival_rate_per_s", "served_per_s", "p50_s", "p99_s")
-                                   if k in st},
-                        "config": {k: cf.get(k) for k in ("offered_per_s", "served_per_s", "p50_s", "p99_s")
-                                   if k in cf}}
-    return out
-
-
-def compact_headline(line, sections):
-    """The last stdout line: the contract's keys and the roofline, rounded,
-    with the side sections reduced to a few figures."""
-    keep_kern = ("ms", "gdofs", "alg_gbs", "hbm_frac", "fp64_tflops", "fp64_issue_frac", "smem_frac")
-    head = dict(line)
-    head["kernels"] = {k: {f: v.get(f) for f in keep_kern} for k, v in line.get("kernels", {}).items()}
-    rf = dict(line.get("roofline") or {})
-    for long_key in ("fp64_probe", "flop_count"):
-        rf.pop(long_key, None)
-    if isinstance(rf.get("smem"), dict):
-        rf["smem"] = {k: rf["smem"][k] for k in ("achieved_gbs", "peak_gbs", "frac") if k in rf["smem"]}
-    head["roofline"] = rf
-    e2e = dict(line.get("e2e") or {})
-    e2e.pop("pipelining", None)
-    head["e2e"] = e2e
-    head["summary"] = headline_summary(sections)
-    head["sections"] = [k for k, v in sections.items() if v is not None]
-    head = _r(head)
-    if len(json.dumps(head)) > HEADLINE_MAX_BYTES:  # drop detail, never the contract's keys
-        head.pop("kernels", None)
-        head.pop("summary", None)
-    return head
-
-
-def emit(line, sections, sections_out=None):
-    """Prints every side section as its own JSON line ({"section": name,
-    ...}), then the compact headline as the last line.  With sections_out,
-    the sections and the full headline also go to that file as one JSON
-    document."""
-    for name, data in sections.items():
-        if data is not None:
-            print(json.dumps({"section": name, **data}))
-    head = compact_headline(line, sections)
-    if sections_out:
-        os.makedirs(os.path.dirname(os.path.abspath(sections_out)), exist_ok=True)
-        with open(sections_out, "w") as f:
-            json.dump({"headline": line, "sections": sections}, f, indent=1)
-    sys.stdout.flush()
-    print(json.dumps(head))
-    sys.stdout.flush()
-    return head
-
-
-def parse_degrees(spec: str):
-    out = []
-    for part in spec.split(","):
-        part = part.strip()
-        if not part:
-            continue
-        if "-" in part:
-            lo, hi = part.split("-")
-            out.extend(range(int(lo), int(hi) + 1))
-        else:
-            out.append(int(part))
-    return out
-
-
-def run_sweep(fem, torch, device, verts, args, sm_mhz):
-    """GDOF/s and roofline fractions of the three FP64 operators (and the
-    FP32 BP3.5/BP3.0 operators of the mixed-precision solver) against N on
-    the benchmark mesh, with the copy roofline recalibrated at every size as
-    the paper does (Section 5): a device-to-device copy of half the
-    operator's algorithmic bytes (a copy of T/2 bytes moves T), and the
-    library's calibration stream with the operator's read:write ratio (k
-    planes read, their sum written).  Each figure is the median of `reps`
-    launches timed with CUDA events after two warm-up launches, each launch
-    preceded (outside its events) by a 258 MB write that evicts L2, so that
-    the low degrees, whose arrays would fit in L2, are timed cold too."""
-    stream = torch.cuda.current_stream(device)
-    E = verts.shape[0]
-    lam, reps = 1.0, args.sweep_reps
-    hbm, _, _ = _peaks()
-    rows = []
-
-    # a write of twice the L2 size before every timed launch, outside its
-    # events: each launch starts from a cold L2, also at the low degrees
-    # whose arrays would otherwise stay resident between launches
-    flush = torch.empty(2 * 129 * 2 ** 20, dtype=torch.uint8, device=device)
-
-    def timed(fn, count):
-        for _ in range(2):
-            fn()
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(count)]
-        for a, b_ in ev:
-            flush.zero_()
-            a.record(stream)
-            fn()
-            b_.record(stream)
-        torch.cuda.synchronize()
-        return statistics.median(a.elapsed_time(b_) for a, b_ in ev)
-
-    degrees = parse_degrees(args.sweep)
-    if not degrees:
-        return None
-    # one seeded U[-1,1] field of the largest size; smaller N take a prefix
-    q_all = torch.from_numpy(fem_synth.field(fem_synth.SEED_Q, E, (max(degrees) + 1) ** 3)).to(device).view(-1)
-    for N in degrees:
-        n = N + 1
-        b = fem.fem_basis_setup(N)
-        q = q_all[:E * n ** 3].view(E, n ** 3)
-        out = torch.empty_like(q)
-        std, inst, byts = alg_counts(N)
-        smem = smem_counts(N)
-        row = {"N": N, "dofs": E * n ** 3}
-        for name, kind in (("bp1", 1), ("bp35", 2), ("bp30", 3), ("bp1_bp30", 3), ("bp30_points", 3), ("bp35_points", 2),
-                           ("bp35_f32", 2), ("bp30_f32", 3), ("bp35_f16", 2), ("bp30_f16", 3),
-                           ("bp30_f32_warp", 3), ("bp30_tc", 3)):
-            f16 = name.endswith("_f16")
-            f32 = name.endswith("_f32") or f16 or name in ("bp30_f32_warp", "bp30_tc")
-            base = "bp30" if name in ("bp30_f32_warp", "bp30_tc") else (name[:-4] if f32 else name)
-            ratio_base = "bp30" if base in ("bp30_points", "bp1_bp30") else ("bp35" if base == "bp35_points" else base)
-            geo = torch.empty(fem.geo_shape(b, kind, E), dtype=torch.float64, device=device)
-            fem.fem_mesh_geofacs(b, kind, verts, geo=geo, stream=stream)
-            if f16:
-                # binary16 factors scaled by 2^(14 - e), max|G| < 2^e, as the solver stores them
-                ex = int(np.frexp(geo.abs().max().item())[1])
-                gi = torch.tensor([2.0 ** (ex - 14)], dtype=torch.float64, device=device)
-                geo, qx = (geo * 2.0 ** (14 - ex)).half(), q.float()
-                o = torch.empty_like(qx)
-                fn = fem.fem_bp35_apply_f16g if base == "bp35" else fem.fem_bp30_apply_f16g
-                ms = timed(lambda: fn(b, geo, gi, lam, qx, out=o, stream=stream), reps)
-                del qx, o, gi
-            elif f32:
-                geo, qx = geo.float(), q.float()
-                o = torch.empty_like(qx)
-                if name == "bp30_tc":
-                    fn = fem.fem_bp30_apply_tc
-                elif name == "bp30_f32_warp":
-                    def fn(b_, g_, l_, q_, out, stream):
-                        return fem.fem_bp30_apply_f32_layout(b_, g_, l_, q_, fem.FEM_LAYOUT_WARP, out=out,
-                                                             stream=stream)
-                else:
-                    fn = fem.fem_bp35_apply_f32 if base == "bp35" else fem.fem_bp30_apply_f32
-                ms = timed(lambda: fn(b, geo, lam, qx, out=o, stream=stream), reps)
-                del qx, o
-            elif name == "bp1_bp30":
-                out2 = torch.empty_like(q)
-                ms = timed(lambda: fem.fem_bp1_bp30_apply(b, geo, lam, q, out_m=out2, out_a=out, stream=stream),
-                           reps)
-                del out2
-            elif name == "bp30_points":
-                ms = timed(lambda: fem.fem_bp30_apply_layout(b, geo, lam, q, fem.FEM_LAYOUT_POINTS, out=out,
-                                                             stream=stream), reps)
-            elif name == "bp35_points":
-                ms = timed(lambda: fem.fem_bp35_apply_layout(b, geo, lam, q, fem.FEM_LAYOUT_POINTS, out=out,
-                                                             stream=stream), reps)
-            elif name == "bp1":
-                ms = timed(lambda: fem.fem_bp1_apply(b, geo, q, out=out, stream=stream), reps)
-            elif name == "bp35":
-                ms = timed(lambda: fem.fem_bp35_apply(b, geo, lam, q, out=out, stream=stream), reps)
-            else:
-                ms = timed(lambda: fem.fem_bp30_apply(b, geo, lam, q, out=out, stream=stream), reps)
-            del geo
-            word = 4 if f32 else 8
-            per_elem = byts[base] * word // 8
-            if f16:  # the factor planes move in two bytes per value
-                per_elem = 4 * (2 * n ** 3) + 2 * 7 * (n ** 3 if base == "bp35" else (N + 2) ** 3)
-            T = E * per_elem
-            # recalibrated copy roofline at this byte count
-            half = torch.empty(T // 2 // 8, dtype=torch.float64, device=device)
-            dst = torch.empty_like(half)
-            copy_ms = timed(lambda: dst.copy_(half), 10)
-            del half, dst
-            # read:write ratio of the operator (planes read per plane written)
-            k = round((byts[ratio_base] - 8 * n ** 3) / (8 * n ** 3))
-            src = torch.empty((k, E * n ** 3), dtype=torch.float32 if f32 else torch.float64, device=device)
-            src.fill_(1.0)
-            red = torch.empty(E * n ** 3, dtype=src.dtype, device=device)
-            ratio_ms = timed(lambda: fem.fem_stream_sum(src, out=red, stream=stream), 10)
-            ratio_gbs = word * (k + 1) * E * n ** 3 / (ratio_ms / 1e3) / 1e9
-            del src, red
-            t = ms / 1e3
-            gbs = T / t / 1e9
-            copy_gbs = T / (copy_ms / 1e3) / 1e9
-            ops = 2 if name == "bp1_bp30" else 1  # the fused pass applies two operators
-            row[name] = {
-                "ms": ms, "gdofs": ops * E * n ** 3 / t / 1e9, "alg_gbs": gbs,
-                "hbm_frac": gbs / hbm, "copy_gbs_at_size": copy_gbs, "copy_frac_at_size": gbs / copy_gbs,
-                "ratio_stream_gbs": ratio_gbs, "ratio_read_planes": k,
-                "hbm_bound_gdofs": ops * copy_gbs / (per_elem / n ** 3),
-                "smem_frac": E * smem[base] * word // 8 / t / 1e9 / smem_peak_gbs(sm_mhz),
-            }
-            if not f32:
-                row[name]["fp64_tflops"] = E * std[name] / t / 1e12
-                row[name]["fp64_issue_frac"] = E * inst[name] / t / 1e9 / fp64_peak_ginst(sm_mhz)
-        rows.append(row)
-        del q, out
-        b.free()
-    del q_all
-    torch.cuda.empty_cache()
-    return {"workload": f"BP1.0/BP3.5/BP3.0 FP64 (BP3.0 also in the point-per-thread layout, and BP1.0 + BP3.0 "
-                        f"in one pass, whose GDOF/s count both operators' DOFs; BP3.5/BP3.0 FP32 "
-                        f"with FP32 and FP16 factors, the mixed solvers' inner operators; FP32 BP3.0 with one "
-                        f"warp per element and with its contractions on the tensor cores, split f16 mma.sync) "
-                        f"sweep, E={E} jittered "
-                        f"hexes, lambda=1, median of {reps} launches per point, L2 evicted before each",
-            "copy_roofline": "device-to-device copy of T/2 bytes moving T = the operator's algorithmic "
-                             "bytes, recalibrated at every N (Section 5 of the paper)",
-            "rows": rows}
-
-
-def run_small_case(fem, torch, device):
-    """The small configuration: BP1.0 at N = 3 on the 8^3 jittered mesh (E =
-    512, 32768 DOFs, 1.04 MB of algorithmic traffic, resident in L2).  It is
-    bound by launch latency, so the figure is microseconds per launch: back
-    to back on one stream, and replayed from a CUDA graph of 100 launches."""
-    N, reps = 3, 100
-    b = fem.fem_basis_setup(N)
-    v = torch.from_numpy(fem_synth.box_mesh(8)).to(device)
-    E = v.shape[0]
-    wJ = fem.fem_mesh_geofacs(b, fem.FEM_GEO_BP1, v)
-    q = torch.from_numpy(fem_synth.field(fem_synth.SEED_Q, E, (N + 1) ** 3)).to(device)
-    out = torch.empty_like(q)
-    st = torch.cuda.Stream(device)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(st):
-        for _ in range(10):
-            fem.fem_bp1_apply(b, wJ, q, out=out, stream=st)
-        st.synchronize()
-        e0.record(st)
-        for _ in range(reps):
-            fem.fem_bp1_apply(b, wJ, q, out=out, stream=st)
-        e1.record(st)
-        st.synchronize()
-        us_stream = e0.elapsed_time(e1) * 1e3 / reps
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=st):
-            for _ in range(reps):
-                fem.fem_bp1_apply(b, wJ, q, out=out, stream=st)
-        g.replay()
-        st.synchronize()
-        e0.record(st)
-        g.replay()
-        e1.record(st)
-        st.synchronize()
-        us_graph = e0.elapsed_time(e1) * 1e3 / reps
-    dofs = E * (N + 1) ** 3
-    b.free()
-    return {"workload": "BP1.0 FP64, N=3, E=512 (8^3 jittered mesh), inputs resident in L2",
-            "us_per_launch_stream": us_stream, "us_per_launch_graph": us_graph,
-            "gdofs_graph": dofs / (us_graph * 1e-6) / 1e9}
-
-
-def manufactured_u(fem, basis, verts_h):
-    """u_I = sin(pi x) sin(pi y) sin(pi z) at every element's GLL nodes
-    (physical coordinates through the trilinear map, GLL nodes from the
-    library's basis tables)."""
-    N = basis.N
-    r = fem.fem_basis_tables(basis)["r"]
-    n = N + 1
-    R, S, T = np.meshgrid(r, r, r, indexing="ij")
-    R, S, T = (a.transpose(2, 1, 0).reshape(-1) for a in (R, S, T))
-    phi = np.stack([(1 + (1 if c & 1 else -1) * R) * (1 + (1 if c & 2 else -1) * S) *
-                    (1 + (1 if c & 4 else -1) * T) / 8 for c in range(8)], axis=1)
-    X = np.einsum("pc,ecd->epd", phi, verts_h)
-    return np.sin(np.pi * X[..., 0]) * np.sin(np.pi * X[..., 1]) * np.sin(np.pi * X[..., 2])
-
-
-def run_pcg(fem, torch, device, verts_h, args):
-    """Jacobi-PCG of the BP3.5 Helmholtz system (lambda = 1; the precision
-    configuration) and of the BP3.0 one, with the manufactured right-hand
-    side b = A u_I: all-FP64 against FP64 defect correction with FP32 inner
-    solves (FP32 factors; FP16 factors; for BP3.0 also the tensor-core
-    contractions).  Each mode is solved to a tight residual (1e-13 for
-    BP3.5, 5e-13 for BP3.0, whose FP64 residual stagnates near 2e-13), where
-    every mode reaches the FP64 solution to 1e-10 and the distance to it is
-    reported, and to 1e-10, the configuration's residual, where the solves
-    differ by up to the FP64 solve's own distance to u_I (about 2e-8: the
-    error is the residual times up to the condition number)."""
-    N, lam = args.degree, 1.0
-    basis = fem.fem_basis_setup(N)
-    vd = torch.from_numpy(verts_h).to(device)
-    u = torch.from_numpy(manufactured_u(fem, basis, verts_h)).to(device)
-    out = {"workload": f"Helmholtz PCG (Jacobi), N={N}, E={verts_h.shape[0]}, lambda=1, b = A u_I with "
-                       f"u = sin(pi x) sin(pi y) sin(pi z)",
-           "error_reference": "u_I, the exact discrete solution; rel_diff_vs_fp64_solve against the FP64 "
-                              "GPU solve of the same tolerance (the oracle PCG agrees with the GPU solvers to "
-                              "1e-8 on the smaller meshes of tests/test_pcg_gpu.py)",
-           "modes": {"fp64": "all-FP64 Jacobi-PCG",
-                     "mixed": "FP64 defect correction, FP32 inner PCG with FP32 factors",
-                     "mixed16": "FP64 defect correction, FP32 inner PCG with binary16 factors (power-of-two "
-                                "scaled) widened to FP32 in the kernel",
-                     "mixed_tc": "FP64 defect correction, FP32 inner PCG whose BP3.0 matvec runs its "
-                                 "contractions on the tensor cores (split f16 mma.sync, FP32 accumulate)"}}
-    wanted = args.pcg_modes.split(",")
-    for opname, op, kind in (("bp35", fem.FEM_OP_BP35, fem.FEM_GEO_BP35), ("bp30", fem.FEM_OP_BP30, fem.FEM_GEO_BP30)):
-        G = fem.fem_mesh_geofacs(basis, kind, vd)
-        apply = fem.fem_bp35_apply if op == fem.FEM_OP_BP35 else fem.fem_bp30_apply
-        b = apply(basis, G, lam, u)
-        modes = [(nm, md, it) for nm, md, it in (("fp64", fem.FEM_PCG_FP64, 0.0), ("mixed", fem.FEM_PCG_MIXED, 1e-3),
-                                                 ("mixed16", fem.FEM_PCG_MIXED16, 1e-3),
-                                                 ("mixed_tc", fem.FEM_PCG_MIXED_TC, 1e-3))
-                 if nm in wanted and not (nm == "mixed_tc" and op != fem.FEM_OP_BP30)]
-        res = {}
-        # the tight solve: 1e-13 for BP3.5; the FP64 BP3.0 residual stagnates
-        # near 2e-13 on this mesh, so 5e-13 for BP3.0
-        tight = 1e-13 if op == fem.FEM_OP_BP35 else 5e-13
-        for tol, reps in ((tight, 1), (1e-10, max(1, args.pcg_solves))):
-            blk, xs = {"tol": tol}, {}
-            for name, mode, itol in modes:
-                s = fem.fem_pcg_create(basis, G, lam, mode, op=op)
-                x, info, code = s.solve(b, tol=tol, inner_tol=itol, raise_on_error=False)  # warm-up
-                times = []
-                for _ in range(reps):
-                    x.zero_()
-                    torch.cuda.synchronize()
-                    t0 = time.perf_counter()
-                    x, info, code = s.solve(b, x=x, tol=tol, inner_tol=itol, raise_on_error=False)
-                    torch.cuda.synchronize()
-                    times.append(time.perf_counter() - t0)
-                med = statistics.median(times)
-                blk[name] = {"solves_per_s": 1.0 / med, "ms_per_solve": 1e3 * med, "iters": info["iters"],
-                             "outer": info["outer"], "relres": info["relres"], "status": code,
-                             "rel_err_vs_u_I": (torch.linalg.norm(x - u) / torch.linalg.norm(u)).item()}
-                xs[name] = x.clone()
-                s.free()
-            for name in xs:
-                if name != "fp64" and "fp64" in xs:
-                    blk[name]["rel_diff_vs_fp64_solve"] = (torch.linalg.norm(xs[name] - xs["fp64"]) /
-                                                           torch.linalg.norm(xs["fp64"])).item()
-                    blk[name + "_speedup"] = blk[name]["solves_per_s"] / blk["fp64"]["solves_per_s"]
-            res["tight" if tol == tight else "tol_1e-10"] = blk
-            del xs
-        out[opname] = res
-        del G, b
-        torch.cuda.empty_cache()
-    # the precision configuration (BP3.5) at the top level, tight solve first
-    out["tight"] = out["bp35"]["tight"]
-    basis.free()
-    return out
-
-
-def run_batch(fem, torch, device, args):
-    """64 independent jittered meshes, N uniform in 2..10, E log-uniform in
-    64..8192, BP3.5 and BP3.0 (FP64, lambda = 1) on each: 128 separate launches
-    against one persistent launch (default and autotuned configuration) and
-    its CUDA-graph replay."""
-    w = fem_synth.batch_workload()
-    bases = {N: fem.fem_basis_setup(N) for N in sorted({s["N"] for s in w})}
-    items, dofs = [], 0
-    for s in w:
-        b = bases[s["N"]]
-        v = torch.from_numpy(fem_synth.box_mesh(s["nx"], s["ny"], s["nz"], jitter=0.1,
-                                                seed=s["mesh_seed"])).to(device)
-        q = torch.from_numpy(fem_synth.field(s["mesh_seed"] + 7, s["E"], (s["N"] + 1) ** 3)).to(device)
-        for op, kind in ((fem.FEM_OP_BP35, fem.FEM_GEO_BP35), (fem.FEM_OP_BP30, fem.FEM_GEO_BP30)):
-            g = fem.fem_mesh_geofacs(b, kind, v)
-            items.append((op, b, g, 1.0, q, torch.empty_like(q)))
-            dofs += q.numel()
-    batch = fem.Batch(items)
-
-    def timed(fn, reps=10):
-        for _ in range(3):
-            fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            fn()
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
-
-    def separate():
-        for op, b, g, lam, q, out in items:
-            (fem.fem_bp35_apply if op == fem.FEM_OP_BP35 else fem.fem_bp30_apply)(b, g, lam, q, out=out)
-
-    ms_sep = timed(separate)
-    ms_default = timed(batch.apply)
-    results = batch.tune(reps=5)
-    ms_tuned = timed(batch.apply)
-    ms_graph = timed(batch.graph_launch)
-    out = {"workload": "64 jittered meshes, N uniform 2..10, E log-uniform 64..8192 (108835 elements), "
-                       "BP3.5 and BP3.0 FP64 lambda=1 on each (128 matvecs)",
-           "dofs_per_pass": dofs,
-           "separate_launches": {"ms": ms_sep, "gdofs": dofs / ms_sep / 1e6},
-           "persistent_default": {"ms": ms_default, "gdofs": dofs / ms_default / 1e6},
-           "persistent_tuned": {"ms": ms_tuned, "gdofs": dofs / ms_tuned / 1e6, "config": batch.config},
-           "graph": {"ms": ms_graph, "gdofs": dofs / ms_graph / 1e6},
-           "tuner_candidates": len(results)}
-    batch.free()
-    return out
-
-
-def run_serve(fem, torch, args):
-    """Poisson arrivals (mean 200 requests/s) of Helmholtz PCG solves, BP3.0
-    or BP3.5 at random, N uniform in 3..9, E log-uniform in 512..32768, rhs
-    uniform in [-1, 1], tolerance 1e-8, FP64 or mixed precision (FP16
-    factors) at random, 120 GiB HBM budget; continuous batching with 8 slots
-    (first come first served, and least estimated work first) against one
-    request at a time (first come, first served)."""
-    reqs = fem_synth.serve_workload(args.serve_requests)
-    data = []
-    for r in reqs:
-        v = fem_synth.box_mesh(r["nx"], r["ny"], r["nz"], jitter=0.1, seed=r["mesh_seed"])
-        rhs = fem_synth.field(r["rhs_seed"], r["E"], (r["N"] + 1) ** 3)
-        data.append((r, v, rhs))
-
-    def play(max_active, policy=0):
-        srv = fem.Server(hbm_budget=120 << 30, max_active=max_active, policy=policy)
-        t0 = srv.clock()
-        k, ids = 0, []
-        while True:
-            now = srv.clock() - t0
-            while k < len(data) and data[k][0]["t"] <= now:
-                r, v, rhs = data[k]
-                mode = fem.FEM_PCG_MIXED16 if r["mixed"] else fem.FEM_PCG_FP64
-                rid, x = srv.submit(r["op"], r["N"], v, rhs, lam=1.0, mode=mode, tol=1e-8)
-                ids.append((rid, r, x))
-                k += 1
-            a, q = srv.progress()
-            if k == len(data) and a == 0 and q == 0:
-                break
-        res = [(srv.poll(rid), r, x) for rid, r, x in ids]
-        srv.free()
-        lat = np.array([p["t_done"] - p["t_submit"] for p, _, _ in res])
-        span = max(p["t_done"] for p, _, _ in res) - min(p["t_submit"] for p, _, _ in res)
-        out = {"solves_per_s": len(res) / span, "makespan_s": span,
-               "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-               "failed": int(sum(p["state"] != fem.FEM_REQ_DONE for p, _, _ in res)),
-               "max_relres": float(max(p["relres"] for p, _, _ in res))}
-        for name, flag in (("mixed", True), ("fp64", False)):
-            sel = np.array([r["mixed"] == flag for _, r, _ in res])
-            if sel.any():
-                out[name] = {"count": int(sel.sum()), "p50_s": float(np.percentile(lat[sel], 50)),
-                             "p99_s": float(np.percentile(lat[sel], 99)),
-                             "mean_iters": float(np.mean([p["iters"] for (p, _, _), s_ in zip(res, sel) if s_]))}
-        return out, [x for _, _, x in res]
-
-    cb, xs_cb = play(8)
-    sjf, xs_sjf = play(8, fem.FEM_SERVE_SHORTEST)
-    fifo, xs_fifo = play(1)
-    same = all(np.array_equal(a, b) and np.array_equal(a, c) for a, b, c in zip(xs_cb, xs_fifo, xs_sjf))
-    return {"workload": f"{len(data)} requests, Poisson arrivals at 200/s, BP3.0|BP3.5, N 3..9, E 512..32768 "
-                        "log-uniform, rhs U[-1,1], tol 1e-8, FP64|mixed (FP16 factors), 120 GiB budget",
-            "continuous_batching_8_slots": cb, "continuous_batching_8_slots_shortest_first": sjf,
-            "one_at_a_time": fifo,
-            "results_identical_alone_and_in_mix": same}
 
 
 def main(argv=None):
@@ -1716,6 +1233,8 @@ def main(argv=None):
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-order batch measurement")
     ap.add_argument("--sections-out", default=None,
                     help="also write the side sections and the full headline to this JSON file")
+    ap.add_argument("--serve-window", type=float, default=30.0,
+                    help="seconds of arrivals of the steady-state serving runs")
     ap.add_argument("--serve-requests", type=int, default=300,
                     help="requests of the Poisson-arrival serving measurement (0 skips it)")
     args = ap.parse_args(argv)

@@ -171,3 +171,11 @@ def test_headline_is_last_and_compact(capsys, tmp_path):
         assert json.loads(ln)["section"] in sections
     full = json.loads(side.read_text())
     assert len(full["sections"]["sweep"]["rows"]) == 15
+
+
+def test_bench_defines_each_function_once():
+    """A second definition of a function would silently replace the first."""
+    import ast
+    tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
+    names = [n.name for n in tree.body if isinstance(n, (ast.FunctionDef, ast.ClassDef))]
+    assert len(names) == len(set(names)), sorted(n for n in names if names.count(n) > 1)
