@@ -20,7 +20,9 @@
 //   * several elements per block (n^2 threads each), coalesced loads of q
 //     and of each geometric-factor plane, coalesced stores.
 // FP32 at degree up to 9 (the mixed solver's hot kernel) runs as a
-// persistent, double-buffered TMA stream instead (see bp35_stream_kernel).
+// persistent, double-buffered TMA stream instead (see bp35_stream_kernel),
+// and above 9 as the stream kernel with one factor stage
+// (bp35_stream1_kernel).
 #include "bp35_stream.cuh"
 
 namespace fem {
@@ -80,6 +82,8 @@ struct Bp35F32Launch {
                            cudaStream_t s) {
         if constexpr (bp35_streamed(N)) {
             return launch_stream35<N, false>(E, G, lambda, q, Aq, nullptr, nullptr, nullptr, nullptr, s);
+        } else if constexpr (bp35_streamed1<N, false, float>()) {
+            return launch_stream35_1<N, false>(E, G, lambda, q, Aq, nullptr, nullptr, nullptr, nullptr, s);
         } else {
             using C = Bp35Cfg<float, N>;
             const int64_t blocks = (E + C::EPB - 1) / C::EPB;
@@ -99,6 +103,9 @@ struct Bp35PcgLaunchT {
             if constexpr (sizeof(T) == 4 && bp35_streamed(N)) {
                 return launch_stream35<N, true>(E, G, lambda, nullptr, Ap, z, p, beta, partials, s, nullptr,
                                                 status);
+            } else if constexpr (sizeof(T) == 4 && bp35_streamed1<N, true, float>()) {
+                return launch_stream35_1<N, true>(E, G, lambda, nullptr, Ap, z, p, beta, partials, s, nullptr,
+                                                  status);
             } else {
                 using C = Bp35Cfg<T, N>;
                 const int64_t blocks = (E + C::EPB - 1) / C::EPB;
@@ -120,6 +127,8 @@ struct Bp35Blocks {
         if constexpr (bp35_streamed(N)) {
             using S = Bp35Stream<N, true>;
             b = stream_grid35((E + S::EPS - 1) / S::EPS, S::blocks_per_sm);
+        } else if constexpr (bp35_streamed1<N, true, float>()) {
+            b = stream_grid35(E, Bp35Stream1<N, true, float>::blocks_per_sm);
         }
         *out = which == 0 ? a : which == 1 ? b : (a > b ? a : b);
         return cudaSuccess;
@@ -142,6 +151,7 @@ struct Bp35Prepare {
         } else {
             if (e == cudaSuccess) e = one<float, false>();
             if (e == cudaSuccess) e = one<float, true>();
+            if (e == cudaSuccess) e = prepare_stream35_1<N, float>();
         }
         return e;
     }

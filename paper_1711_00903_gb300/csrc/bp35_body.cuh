@@ -37,6 +37,17 @@ struct Bp35Cfg
                           sizeof(T) == 8 ? (N >= 8 ? 512 : 256) : (N == 10 ? 128 : 256))> {
 };
 
+// Hooks around the factor phase of bp35_core, for kernels that stage the
+// factors asynchronously: before() runs on every thread after the
+// derivative phase's barrier and returns whether the factors are there (the
+// same value on every thread; false ends the core at once), after() runs on
+// every thread once the factor phase's barrier has passed (the factors are
+// no longer read).  The default does nothing.
+struct NoFactorHooks {
+    __device__ __forceinline__ bool before() const { return true; }
+    __device__ __forceinline__ void after() const {}
+};
+
 // The operator on elements [e0, e0 + nel) (nel <= EPB) whose input field is
 // already in the first box of each element (boxes: EPB x 3 boxes, filled
 // before a barrier): derivatives, chain rule with the factors, transposes,
@@ -45,9 +56,9 @@ struct Bp35Cfg
 // TG (T, or FP16 scaled by a power of two that gscale undoes on the output).
 // Returns the thread's share of q . Aq (PCG; 0 otherwise).  Ends without a
 // barrier.
-template <typename T, int N, int EPB_, bool PCG, bool G_SMEM, typename TG = T>
+template <typename T, int N, int EPB_, bool PCG, bool G_SMEM, typename TG = T, typename H = NoFactorHooks>
 __device__ __forceinline__ T bp35_core(T *smem, int64_t e0, int nel, const TG *__restrict__ Gsrc, double lambda,
-                                       T *__restrict__ Aq, T gscale = T(1)) {
+                                       T *__restrict__ Aq, T gscale = T(1), const H &hooks = H()) {
     using C = Bp35Layout<T, N, EPB_>;
     using B = typename C::B;
     constexpr int n = C::n, nn = C::nn, NP = C::NP;
@@ -76,6 +87,7 @@ __device__ __forceinline__ T bp35_core(T *smem, int64_t e0, int nel, const TG *_
         eo_apply<n, n, -1, C::oD>(x, qt);
     }
     __syncthreads();
+    if (!hooks.before()) return T(0);
 
     // chain rule at the nodes of column (i=u, j=v), t-transpose in registers
     T acc[n];
@@ -102,6 +114,7 @@ __device__ __forceinline__ T bp35_core(T *smem, int64_t e0, int nel, const TG *_
         for (int k = 0; k < n; k++) acc[k] = (lambda != 0.0) ? fmx(lam, acc[k], y[k]) : y[k];
     }
     __syncthreads();
+    hooks.after();
 
     // r- and s-transposes, in place
     if (act) {

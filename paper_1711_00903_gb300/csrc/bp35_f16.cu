@@ -60,6 +60,9 @@ struct F16Launch {
                                cudaStream_t s, double *status) {
             if constexpr (bp35_streamed(N)) {
                 return launch_stream35<N, PCG, __half>(E, G, lambda, q, Aq, z, p, beta, partials, s, ginv, status);
+            } else if constexpr (bp35_streamed1<N, PCG, __half>()) {
+                return launch_stream35_1<N, PCG, __half>(E, G, lambda, q, Aq, z, p, beta, partials, s, ginv,
+                                                         status);
             } else {
                 using C = Bp35Cfg<float, N>;
                 const int64_t blocks = (E + C::EPB - 1) / C::EPB;
@@ -77,6 +80,8 @@ struct F16Blocks {
         if constexpr (bp35_streamed(N)) {
             using S = Bp35Stream<N, true, __half>;
             *out = stream_grid35((E + S::EPS - 1) / S::EPS, S::blocks_per_sm);
+        } else if constexpr (bp35_streamed1<N, true, __half>()) {
+            *out = stream_grid35(E, Bp35Stream1<N, true, __half>::blocks_per_sm);
         } else {
             using C = Bp35Cfg<float, N>;
             *out = (E + C::EPB - 1) / C::EPB;
@@ -96,6 +101,7 @@ struct F16Prepare {
             if (e == cudaSuccess)
                 e = cudaFuncSetAttribute(f16g_fn<N, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          Bp35Cfg<float, N>::smem);
+            if (e == cudaSuccess) e = prepare_stream35_1<N, __half>();
             return e;
         }
     }

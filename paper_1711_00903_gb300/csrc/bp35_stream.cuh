@@ -220,5 +220,211 @@ cudaError_t prepare_stream35() {
     return e;
 }
 
+// ---------------------------------------------------------------------------
+// Single-factor-stage stream kernel, for the degrees above 9 where two
+// stages of an element's factors (37-115 KB in FP32) do not fit in shared
+// memory.  One element per group; the input field is double-buffered (TMA
+// bulk copies, one group ahead) and the factors have one stage: the copy of
+// the next group's factors is issued as soon as this group's factor phase
+// has passed its barrier (bp35_core's hooks), so it lands while this group
+// finishes (transposes, output) and the next one stages its field and
+// takes its derivatives.  The PCG variant reads the old p directly from
+// global memory in the staging loop (a stage for it would not fit at
+// N = 15).  Every wait is bounded; a block whose wait gives up stops
+// issuing copies, waits once more (bounded) for those in flight, reports
+// through the status word and leaves.
+template <int N, bool PCG, typename TG = float>
+struct Bp35Stream1 {
+    static constexpr int n = N + 1, nn = n * n, NP = n * n * n;
+    using L = Bp35Layout<float, N, 1>;
+    static constexpr int threads = L::threads;
+    static constexpr int gElem = 7 * NP * (int)sizeof(TG);
+    static constexpr int vElem = NP * 4;
+    static constexpr bool ALIGNED = gElem % 16 == 0 && vElem % 16 == 0;
+    static constexpr int gRegion = ALIGNED ? gElem : ((gElem + 32 + 15) / 16) * 16;
+    static constexpr int vRegion = ALIGNED ? vElem : ((vElem + 32 + 15) / 16) * 16;
+    static constexpr int oG = 32;  // three mbarriers, then the factor stage
+    static constexpr int oV = oG + gRegion;
+    static constexpr int oBox = oV + 2 * vRegion;
+    static constexpr int smem = oBox + (L::smem > 256 ? L::smem : 256);
+    static constexpr bool fits = smem <= 227 * 1024;
+    static constexpr int per_sm_raw = (220 * 1024) / (smem + 1024);
+    static constexpr int blocks_per_sm = per_sm_raw > 8 ? 8 : (per_sm_raw < 1 ? 1 : per_sm_raw);
+};
+
+// The kernel choice above N = 9: the one-factor-stage stream kernel where
+// it fits in shared memory and measured faster than the block kernel on the
+// 32^3 mesh (GB300, fraction of the copy rate).  FP32 factors: 0.97, 0.78,
+// 0.97, 0.78 and 0.79 at N = 10, 11, 12, 14 and 15, against 0.57-0.70 for
+// the block kernel; at N = 13 one block per SM fits and it measured 0.62
+// against 0.65.  FP16 factors: 0.46-0.72 against 0.39-0.56 at N = 10-14,
+// 0.48 against 0.50 at N = 15.
+template <int N, bool PCG, typename TG>
+constexpr bool bp35_streamed1() {
+    constexpr bool faster = sizeof(TG) == 4 ? (N != 13) : (N != 15);
+    return !bp35_streamed(N) && faster && Bp35Stream1<N, PCG, TG>::fits;
+}
+
+template <int N, bool PCG, typename TG>
+__global__ void __launch_bounds__(Bp35Stream1<N, PCG, TG>::threads)
+bp35_stream1_kernel(int64_t E, const TG *__restrict__ G, double lambda, const float *__restrict__ q,
+                    float *__restrict__ Aq, const float *__restrict__ z, float *__restrict__ p,
+                    const double *__restrict__ beta, double *__restrict__ partials, const double *__restrict__ ginv,
+                    double *__restrict__ status) {
+    using S = Bp35Stream1<N, PCG, TG>;
+    using B = typename S::L::B;
+    constexpr int n = S::n, nn = S::nn, NP = S::NP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);  // [0] factors, [1], [2] field stages
+    float *boxes = reinterpret_cast<float *>(smem_raw + S::oBox);
+    const float bt = PCG ? (float)(*beta) : 0.0f;
+    const float gscale = factor_unscale<float>(ginv);
+    const float *fld = PCG ? z : q;
+    const TG *G_end = G + E * 7 * NP;
+    const float *fld_end = fld + E * NP;
+
+    auto gplan = [&](int64_t e) {
+        return S::ALIGNED ? RangeCopy{(unsigned)S::gElem, 0u}
+                          : range_copy_plan(G + e * 7 * NP, (unsigned long long)S::gElem, G_end);
+    };
+    auto vplan = [&](int64_t e) {
+        return S::ALIGNED ? RangeCopy{(unsigned)S::vElem, 0u}
+                          : range_copy_plan(fld + e * NP, (unsigned long long)S::vElem, fld_end);
+    };
+    auto issue_g = [&](int64_t e) {
+        const RangeCopy pl = gplan(e);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        mbar_arrive_expect_tx(&bar[0], pl.tma_bytes);
+        range_copy_issue(smem_raw + S::oG, G + e * 7 * NP, (unsigned long long)S::gElem, pl, &bar[0]);
+    };
+    auto issue_v = [&](int64_t e, int k) {
+        const RangeCopy pl = vplan(e);
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        mbar_arrive_expect_tx(&bar[1 + k], pl.tma_bytes);
+        range_copy_issue(smem_raw + S::oV + k * S::vRegion, fld + e * NP, (unsigned long long)S::vElem, pl,
+                         &bar[1 + k]);
+    };
+
+    // copies in flight, the same on every thread: the factors of the
+    // current element, and each field stage with the use it belongs to
+    bool pend_g = false, pend_v[2] = {false, false};
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init(&bar[2], 1);
+        if ((int64_t)blockIdx.x < E) {
+            issue_g(blockIdx.x);
+            issue_v(blockIdx.x, 0);
+        }
+    }
+    if ((int64_t)blockIdx.x < E) pend_g = pend_v[0] = true;
+    __syncthreads();
+
+    double dot = 0.0;
+    bool failed = false;
+    int it = 0;
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x, it++) {
+        const int k = it & 1;
+        const bool has_next = e + gridDim.x < E;
+        if (has_next) {
+            if (threadIdx.x == 0) issue_v(e + gridDim.x, k ^ 1);
+            pend_v[k ^ 1] = true;
+        }
+        if (!__syncthreads_and(mbar_wait(&bar[1 + k], (unsigned)((it >> 1) & 1)))) {
+            failed = true;
+            break;
+        }
+        pend_v[k] = false;
+
+        const RangeCopy vp = vplan(e), gp = gplan(e);
+        const float *sV = reinterpret_cast<const float *>(smem_raw + S::oV + k * S::vRegion + vp.offset);
+        const TG *sG = reinterpret_cast<const TG *>(smem_raw + S::oG + gp.offset);
+        for (int t = threadIdx.x; t < NP; t += blockDim.x) {
+            float v = sV[t];
+            if (PCG) {
+                if (bt != 0.0f) v = fmx(bt, p[e * NP + t], v);
+                p[e * NP + t] = v;
+            }
+            boxes[B::at(t % n, (t / n) % n, t / nn)] = v;
+        }
+        __syncthreads();
+
+        struct Hooks {
+            uint64_t *barg;
+            unsigned parity;
+            bool *failed, *pend_g;
+            const bool next;
+            decltype(issue_g) *iss;
+            int64_t next_e;
+            __device__ __forceinline__ bool before() const {
+                const bool ok = __syncthreads_and(mbar_wait(barg, parity));
+                if (!ok) *failed = true;
+                return ok;
+            }
+            __device__ __forceinline__ void after() const {
+                // the factor stage is free: the next element's factors go in now
+                *pend_g = next;
+                if (next && threadIdx.x == 0) (*iss)(next_e);
+            }
+        } hooks{&bar[0], (unsigned)(it & 1), &failed, &pend_g, has_next, &issue_g, e + gridDim.x};
+        dot += (double)bp35_core<float, N, 1, PCG, true, TG, Hooks>(boxes, e, 1, sG, lambda, Aq, gscale, hooks);
+        if (failed) break;
+        __syncthreads();  // the boxes and the field stage are free again
+    }
+    if (failed) {
+        // report, then wait once more (bounded) for every copy still in
+        // flight before the shared memory is released
+        if (threadIdx.x == 0) {
+            atomicAdd(&g_wait_timeouts, 1ull);
+            if (status) *status = 1.0;
+        }
+        if (pend_g) mbar_wait(&bar[0], (unsigned)(it & 1));
+        for (int kk = 0; kk < 2; kk++)
+            if (pend_v[kk]) {
+                // stage kk's outstanding copy belongs to iteration it (kk == it & 1) or it + 1
+                const int owner = (kk == (it & 1)) ? it : it + 1;
+                mbar_wait(&bar[1 + kk], (unsigned)((owner >> 1) & 1));
+            }
+        if (PCG && threadIdx.x == 0) partials[blockIdx.x] = 0.0;
+        return;
+    }
+    if (PCG) {
+        const double tot = block_sum(dot, reinterpret_cast<double *>(boxes));
+        if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+    }
+}
+
+template <int N, bool PCG, typename TG = float>
+cudaError_t launch_stream35_1(int64_t E, const TG *G, double lambda, const float *q, float *Aq, const float *z,
+                              float *p, const double *beta, double *partials, cudaStream_t s,
+                              const double *ginv = nullptr, double *status = nullptr) {
+    using S = Bp35Stream1<N, PCG, TG>;
+    const int64_t grid = stream_grid35(E, S::blocks_per_sm);
+    bp35_stream1_kernel<N, PCG, TG><<<(unsigned)grid, S::threads, S::smem, s>>>(E, G, lambda, q, Aq, z, p, beta,
+                                                                                partials, ginv, status);
+    return cudaGetLastError();
+}
+
+template <int N, typename TG>
+cudaError_t prepare_stream35_1() {
+    cudaError_t e = cudaSuccess;
+    if constexpr (Bp35Stream1<N, false, TG>::fits) {
+        e = cudaFuncSetAttribute(bp35_stream1_kernel<N, false, TG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 Bp35Stream1<N, false, TG>::smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(bp35_stream1_kernel<N, false, TG>,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    }
+    if constexpr (Bp35Stream1<N, true, TG>::fits) {
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(bp35_stream1_kernel<N, true, TG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     Bp35Stream1<N, true, TG>::smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(bp35_stream1_kernel<N, true, TG>,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    }
+    return e;
+}
+
 }  // namespace
 }  // namespace fem

@@ -82,14 +82,16 @@ def test_bp30_f32_matches_fp64_operator(N):
     assert _rel(got, ref) < 2e-6 * (N + 2)
 
 
-@pytest.mark.parametrize("op,N", [("bp35", 7), ("bp35", 5), ("bp35", 4), ("bp35", 8), ("bp30", 7), ("bp30", 4),
-                                  ("bp30", 9)])
+@pytest.mark.parametrize("op,N", [("bp35", 7), ("bp35", 5), ("bp35", 4), ("bp35", 8), ("bp35", 10), ("bp35", 12),
+                                  ("bp35", 15), ("bp30", 7), ("bp30", 4), ("bp30", 9)])
 def test_stream_kernels_many_groups_per_block(op, N):
     """The FP32 and FP16-factor operators on 1001 elements: for BP3.5 the TMA
-    stream kernel with several element groups per persistent block (stages
-    reused), and at even N element ranges off 16-byte boundaries (range
-    copies, with the plain-load tail at the end of the arrays); for BP3.0 the
-    block kernels.  Against the oracle on the same rounded inputs."""
+    stream kernels with several element groups per persistent block (stages
+    reused; above N = 9 the kernel with one factor stage, whose next copy
+    starts in the middle of the element), and at even N element ranges off
+    16-byte boundaries (range copies, with the plain-load tail at the end of
+    the arrays); for BP3.0 the block kernels.  Against the oracle on the same
+    rounded inputs."""
     fem, torch = _fem(), _torch()
     v = fem_synth.box_mesh(11, 10, 10)[:1001]
     E = v.shape[0]
@@ -112,13 +114,13 @@ def test_stream_kernels_many_groups_per_block(op, N):
 
 
 def test_stream_f32_operator_ragged_groups_and_no_wait_timeouts():
-    """The FP32 BP3.5 kernel that stages the factors with TMA bulk copies
-    (N <= 9; N = 11 takes the block kernel): a single element, element
-    counts that leave the last group partly filled, results equal to the
-    oracle's on the same FP32 inputs, and no bounded wait gave up."""
+    """The FP32 BP3.5 kernels that stage the factors with TMA bulk copies
+    (two stages up to N = 9, one factor stage above): a single element,
+    element counts that leave the last group partly filled, results equal
+    to the oracle's on the same FP32 inputs, and no bounded wait gave up."""
     fem, torch = _fem(), _torch()
     fem.fem_wait_timeouts(reset=True)
-    for N, E in ((7, 1), (7, 37), (3, 33), (4, 7), (8, 5), (11, 3)):
+    for N, E in ((7, 1), (7, 37), (3, 33), (4, 7), (8, 5), (10, 1), (11, 3), (14, 2), (15, 5)):
         v = fem_synth.box_mesh(4)[:E]
         G, _ = oracle.geofacs(N, oracle.KIND_BP35, v)
         q = fem_synth.field(3, E, (N + 1) ** 3)
@@ -460,3 +462,25 @@ def test_full_size_bp30_solves_all_modes():
     ref = xs[fem.FEM_PCG_FP64]
     for mode, x in xs.items():
         assert (torch.linalg.norm(x - ref) / torch.linalg.norm(ref)).item() <= 1e-10, mode
+
+
+@pytest.mark.parametrize("N", [10, 13])
+def test_high_degree_mixed_solves_match_fp64(N):
+    """BP3.5 mixed solves above N = 9, whose inner operator is the stream
+    kernel with one factor stage (FP32 and FP16 factors), reach the FP64
+    solve of the same system."""
+    fem, torch = _fem(), _torch()
+    v = fem_synth.box_mesh(2)
+    G, _ = oracle.geofacs(N, oracle.KIND_BP35, v)
+    b = _dev(fem_synth.field(21, v.shape[0], (N + 1) ** 3))
+    basis = fem.fem_basis_setup(N)
+    xs = {}
+    for mode in (fem.FEM_PCG_FP64, fem.FEM_PCG_MIXED, fem.FEM_PCG_MIXED16):
+        s = fem.fem_pcg_create(basis, _dev(G), 1.0, mode)
+        x, info, code = s.solve(b, tol=1e-11, inner_tol=1e-3)
+        assert code == fem.FEM_OK and info["relres"] <= 1e-11
+        xs[mode] = x
+    for mode in (fem.FEM_PCG_MIXED, fem.FEM_PCG_MIXED16):
+        d = (torch.linalg.norm(xs[mode] - xs[fem.FEM_PCG_FP64]) / torch.linalg.norm(xs[fem.FEM_PCG_FP64])).item()
+        assert d <= 1e-8, mode
+    assert fem.fem_wait_timeouts() == 0
