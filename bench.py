@@ -815,10 +815,10 @@ def run_sweep(fem, torch, device, verts, args, sm_mhz):
         row = {"N": N, "dofs": E * n ** 3}
         for name, kind in (("bp1", 1), ("bp35", 2), ("bp30", 3), ("bp1_bp30", 3), ("bp30_points", 3), ("bp35_points", 2),
                            ("bp35_f32", 2), ("bp30_f32", 3), ("bp35_f16", 2), ("bp30_f16", 3),
-                           ("bp30_f32_warp", 3), ("bp30_tc", 3)):
+                           ("bp30_f32_block", 3), ("bp30_f32_warp", 3), ("bp30_tc", 3)):
             f16 = name.endswith("_f16")
-            f32 = name.endswith("_f32") or f16 or name in ("bp30_f32_warp", "bp30_tc")
-            base = "bp30" if name in ("bp30_f32_warp", "bp30_tc") else (name[:-4] if f32 else name)
+            f32 = name.endswith("_f32") or f16 or name in ("bp30_f32_block", "bp30_f32_warp", "bp30_tc")
+            base = "bp30" if name in ("bp30_f32_block", "bp30_f32_warp", "bp30_tc") else (name[:-4] if f32 else name)
             ratio_base = "bp30" if base in ("bp30_points", "bp1_bp30") else ("bp35" if base == "bp35_points" else base)
             geo = torch.empty(fem.geo_shape(b, kind, E), dtype=torch.float64, device=device)
             fem.fem_mesh_geofacs(b, kind, verts, geo=geo, stream=stream)
@@ -836,10 +836,11 @@ def run_sweep(fem, torch, device, verts, args, sm_mhz):
                 o = torch.empty_like(qx)
                 if name == "bp30_tc":
                     fn = fem.fem_bp30_apply_tc
-                elif name == "bp30_f32_warp":
-                    def fn(b_, g_, l_, q_, out, stream):
-                        return fem.fem_bp30_apply_f32_layout(b_, g_, l_, q_, fem.FEM_LAYOUT_WARP, out=out,
-                                                             stream=stream)
+                elif name in ("bp30_f32_warp", "bp30_f32_block"):
+                    lay = fem.FEM_LAYOUT_WARP if name == "bp30_f32_warp" else fem.FEM_LAYOUT_LINES
+
+                    def fn(b_, g_, l_, q_, out, stream, lay=lay):
+                        return fem.fem_bp30_apply_f32_layout(b_, g_, l_, q_, lay, out=out, stream=stream)
                 else:
                     fn = fem.fem_bp35_apply_f32 if base == "bp35" else fem.fem_bp30_apply_f32
                 ms = timed(lambda: fn(b, geo, lam, qx, out=o, stream=stream), reps)

@@ -217,6 +217,13 @@ int fem_bp30_apply_f16g(const fem_basis *b, int64_t E, const void *G16, const do
  *                    (two or four above N = 9) per element and no block
  *                    barrier between the phases (FP32 BP3.0 only). */
 #define FEM_LAYOUT_WARP 2
+/* FEM_LAYOUT_STREAM  FP32 BP3.0 only: a persistent grid that stages each
+ *                    element's field and factors in shared memory with TMA
+ *                    bulk copies, the next element's factors in flight
+ *                    while the current one finishes (lines as
+ *                    FEM_LAYOUT_LINES; degrees whose element fits in
+ *                    shared memory). */
+#define FEM_LAYOUT_STREAM 3
 
 /* fem_bp30_apply with a chosen thread layout (same arguments, layouts and
  * errors; FEM_EINVAL for an unknown layout).  Both layouts compute the same
@@ -241,10 +248,13 @@ int fem_bp30_apply_f32(const fem_basis *b, int64_t E, const float *G, double lam
                        const float *q, float *Aq, void *stream);
 
 /* fem_bp30_apply_f32 with a chosen kernel: FEM_LAYOUT_LINES (several
- * elements per block, block barriers between the phases) or FEM_LAYOUT_WARP
- * (one warp per element).  Same arguments, layouts and errors (FEM_EINVAL
- * for another layout; E <= 2^31 - 1).  Both compute the same FP32 operator
- * and agree to FP32 rounding. */
+ * elements per block, block barriers between the phases, factors read from
+ * global memory), FEM_LAYOUT_STREAM (factors staged by TMA, FEM_EINVAL at a
+ * degree where an element does not fit in shared memory) or
+ * FEM_LAYOUT_WARP (one warp per element); fem_bp30_apply_f32 takes the
+ * fastest measured for the degree.  Same arguments, layouts and errors
+ * (FEM_EINVAL for another layout; E <= 2^31 - 1).  All compute the same
+ * FP32 operator and agree to FP32 rounding. */
 int fem_bp30_apply_f32_layout(const fem_basis *b, int64_t E, const float *G, double lambda,
                               const float *q, float *Aq, int layout, void *stream);
 

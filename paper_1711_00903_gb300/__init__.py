@@ -21,7 +21,7 @@ __all__ = [
     "fem_basis_tables", "fem_basis_host_tables", "fem_mesh_geofacs", "fem_bp1_apply",
     "fem_bp35_apply", "fem_bp30_apply", "FEM_GEO_BP1", "FEM_GEO_BP35", "FEM_GEO_BP30",
     "geo_shape", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_wait_selftest", "fem_bp30_apply_layout", "fem_fma_probe",
-    "FEM_LAYOUT_LINES", "FEM_LAYOUT_POINTS", "FEM_LAYOUT_WARP", "fem_bp30_apply_f32_layout", "fem_bp35_apply_layout", "FEM_BATCH_POINTS30",
+    "FEM_LAYOUT_LINES", "FEM_LAYOUT_POINTS", "FEM_LAYOUT_WARP", "FEM_LAYOUT_STREAM", "fem_bp30_apply_f32_layout", "fem_bp35_apply_layout", "FEM_BATCH_POINTS30",
     "FEM_BATCH_POINTS35", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_bp30_apply_tc", "FEM_PREC_F16TC", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot", "fem_dot_scratch_size", "Pcg",
     "fem_bp35_apply_ex", "fem_bp30_apply_ex", "fem_bp1_bp30_apply", "FEM_PREC_F64", "FEM_PREC_F32", "FEM_PREC_F16G",
     "fem_pcg_create", "fem_pcg_solve", "fem_pcg_destroy", "FEM_ETIMEDOUT", "FEM_ECANCELED", "FEM_FAULT_WAIT_TIMEOUT", "FEM_EBREAKDOWN", "FEM_PCG_FP64", "FEM_PCG_MIXED", "FEM_PCG_MIXED16", "FEM_PCG_MIXED_TC", "fem_bp35_apply_f16g", "fem_bp30_apply_f16g",
@@ -35,7 +35,7 @@ FEM_FAULT_WAIT_TIMEOUT = 1
 FEM_PCG_FP64, FEM_PCG_MIXED, FEM_PCG_MIXED16, FEM_PCG_MIXED_TC = 0, 1, 2, 3
 FEM_GEO_BP1, FEM_GEO_BP35, FEM_GEO_BP30 = 1, 2, 3
 FEM_OP_BP35, FEM_OP_BP30 = 2, 3
-FEM_LAYOUT_LINES, FEM_LAYOUT_POINTS, FEM_LAYOUT_WARP = 0, 1, 2
+FEM_LAYOUT_LINES, FEM_LAYOUT_POINTS, FEM_LAYOUT_WARP, FEM_LAYOUT_STREAM = 0, 1, 2, 3
 FEM_BATCH_POINTS30, FEM_BATCH_POINTS35 = 1, 2
 FEM_PREC_F64, FEM_PREC_F32, FEM_PREC_F16G, FEM_PREC_F16TC = 0, 1, 2, 3
 FEM_REQ_QUEUED, FEM_REQ_RUNNING, FEM_REQ_DONE, FEM_REQ_FAILED = 0, 1, 2, 3

@@ -335,13 +335,16 @@ int fem_bp30_apply_f32(const fem_basis *b, int64_t E, const float *G, double lam
 
 int fem_bp30_apply_f32_layout(const fem_basis *b, int64_t E, const float *G, double lambda, const float *q,
                               float *Aq, int layout, void *stream) {
-    if (layout != FEM_LAYOUT_LINES && layout != FEM_LAYOUT_WARP) return FEM_EINVAL;
+    if (layout != FEM_LAYOUT_LINES && layout != FEM_LAYOUT_WARP && layout != FEM_LAYOUT_STREAM) return FEM_EINVAL;
     if (!b || E < 0) return FEM_EINVAL;
     if (E == 0) return FEM_OK;
     if (!G || !q || !Aq || !aligned16(G) || !aligned16(q) || !aligned16(Aq)) return FEM_EINVAL;
     if ((const void *)Aq == (const void *)q || E > (int64_t)0x7fffffff) return FEM_EINVAL;
-    cudaError_t e = layout == FEM_LAYOUT_WARP ? fem::launch_bp30_warp(b, E, G, lambda, q, Aq, (cudaStream_t)stream)
-                                              : fem::launch_bp30_f32(b, E, G, lambda, q, Aq, (cudaStream_t)stream);
+    cudaError_t e = layout == FEM_LAYOUT_WARP
+                        ? fem::launch_bp30_warp(b, E, G, lambda, q, Aq, (cudaStream_t)stream)
+                        : fem::launch_bp30_f32(b, E, G, lambda, q, Aq, (cudaStream_t)stream,
+                                               layout == FEM_LAYOUT_STREAM ? 2 : 1);
+    if (e == cudaErrorInvalidValue && layout == FEM_LAYOUT_STREAM) return FEM_EINVAL;  // does not fit at this degree
     return e == cudaSuccess ? FEM_OK : cuda_fail(e);
 }
 

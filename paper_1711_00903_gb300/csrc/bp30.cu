@@ -123,12 +123,19 @@ struct Bp1Bp30Launch {
 
 FEM_DEFINE_FOLD_UPLOAD(upload_fold_bp30_tu)
 
+// kernel selection of the FP32 entry points: 0 the default for the degree,
+// 1 the block kernel, 2 the stream kernel
 template <typename T, bool PCG>
 struct Bp30LaunchT {
     template <int N>
     struct L {
         static cudaError_t run(int64_t E, const T *G, double lambda, const T *q, T *Aq, const T *z, T *p,
-                               const double *beta, double *partials, cudaStream_t s) {
+                               const double *beta, double *partials, cudaStream_t s, double *status = nullptr,
+                               int which = 0) {
+            if constexpr (sizeof(T) == 4) {
+                if (which == 2 || (which == 0 && bp30_stream_default(N)))
+                    return launch_bp30_stream(N, PCG, E, G, lambda, q, Aq, z, p, beta, partials, s, status);
+            }
             using C = Bp30Cfg<N, T>;
             const int64_t blocks = (E + C::EPB - 1) / C::EPB;
             bp30_fn<T, N, PCG>()<<<(unsigned)blocks, C::threads, C::smem, s>>>(E, G, lambda, q, Aq, z, p, beta,
@@ -143,6 +150,7 @@ struct Bp30Blocks {
     static cudaError_t run(int64_t E, bool f32, int64_t *out) {
         const int epb = f32 ? Bp30Cfg<N, float>::EPB : Bp30Cfg<N, double>::EPB;
         *out = (E + epb - 1) / epb;
+        if (f32 && bp30_stream_default(N)) *out = bp30_stream_grid(N, E);
         return cudaSuccess;
     }
 };
@@ -176,10 +184,10 @@ cudaError_t launch_bp30(const fem_basis *b, int64_t E, const double *G, double l
 }
 
 cudaError_t launch_bp30_f32(const fem_basis *b, int64_t E, const float *G, double lambda, const float *q,
-                            float *Aq, cudaStream_t s) {
+                            float *Aq, cudaStream_t s, int which) {
     return dispatch_degree<Bp30LaunchT<float, false>::L>(b->host.N, E, G, lambda, q, Aq, (const float *)nullptr,
                                                           (float *)nullptr, (const double *)nullptr,
-                                                          (double *)nullptr, s);
+                                                          (double *)nullptr, s, (double *)nullptr, which);
 }
 
 cudaError_t launch_bp30_pcg(const fem_basis *b, int64_t E, const double *G, double lambda, const double *z,
@@ -189,9 +197,10 @@ cudaError_t launch_bp30_pcg(const fem_basis *b, int64_t E, const double *G, doub
 }
 
 cudaError_t launch_bp30_pcg_f32(const fem_basis *b, int64_t E, const float *G, double lambda, const float *z,
-                                float *p, const double *beta, float *Ap, double *partials, cudaStream_t s) {
+                                float *p, const double *beta, float *Ap, double *partials, cudaStream_t s,
+                                double *status) {
     return dispatch_degree<Bp30LaunchT<float, true>::L>(b->host.N, E, G, lambda, (const float *)nullptr, Ap, z, p,
-                                                         beta, partials, s);
+                                                         beta, partials, s, status, 0);
 }
 
 cudaError_t launch_bp1_bp30(const fem_basis *b, int64_t E, const double *G, double lambda, const double *q,
@@ -207,8 +216,9 @@ int64_t bp30_blocks(int N, int64_t E, bool f32) {
 
 cudaError_t prepare_bp30(int N, const double *fold_table) {
     cudaError_t e = upload_fold_bp30_tu(fold_table);
-    if (e != cudaSuccess) return e;
-    return dispatch_degree<Bp30Prepare>(N);
+    if (e == cudaSuccess) e = dispatch_degree<Bp30Prepare>(N);
+    if (e == cudaSuccess) e = prepare_bp30_stream(N, fold_table);
+    return e;
 }
 
 }  // namespace fem

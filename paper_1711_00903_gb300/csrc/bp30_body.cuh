@@ -58,10 +58,11 @@ struct Bp30Cfg : Bp30Layout<N,
 // seventh factor, from the interpolated field the operator computes anyway
 // (four boxes per element, the fourth, D, for BP1.0's t-projection); its
 // projections run in phases 5, 6 and 8 beside the operator's.
-template <int N, int EPB_, typename T, bool PCG, bool G_SMEM, typename TG, bool MASS = false>
+template <int N, int EPB_, typename T, bool PCG, bool G_SMEM, typename TG, bool MASS = false,
+          typename H = NoFactorHooks>
 __device__ __forceinline__ T bp30_core(T *smem, int64_t e0, int nel, const TG *__restrict__ Gsrc, double lambda,
                                        T *__restrict__ Aq, const T *__restrict__ p, T gscale,
-                                       T *__restrict__ Mq = nullptr) {
+                                       T *__restrict__ Mq = nullptr, const H &hooks = H()) {
     using C = Bp30Layout<N, EPB_, T, MASS ? 4 : 3>;
     using B0 = typename C::B0;
     using B1 = typename C::B1;
@@ -130,6 +131,7 @@ __device__ __forceinline__ T bp30_core(T *smem, int64_t e0, int nel, const TG *_
         for (int l = 0; l < m; l++) US[B3::at(u, l, v)] = y[l];
     });
     __syncthreads();
+    if (!hooks.before()) return T(0);
 
     // 5. column (a, b): t-derivative, chain rule, t-transpose, mass term.
     // Each thread has at most one column task (threads >= m*m*EPB), so acc
@@ -175,6 +177,7 @@ __device__ __forceinline__ T bp30_core(T *smem, int64_t e0, int nel, const TG *_
         }
     }
     __syncthreads();
+    hooks.after();
 
     // 6. r- and s-transposes in place
     for_tasks<mm, EPB>(nel, [&](int el, int r) {

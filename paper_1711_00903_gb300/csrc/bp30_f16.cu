@@ -58,7 +58,9 @@ struct F16Launch30 {
     struct L {
         static cudaError_t run(int64_t E, const __half *G, const double *ginv, double lambda, const float *q,
                                float *Aq, const float *z, float *p, const double *beta, double *partials,
-                               cudaStream_t s) {
+                               cudaStream_t s, double *status) {
+            if (bp30_stream_default(N, true))
+                return launch_bp30_stream_f16g(N, PCG, E, G, ginv, lambda, q, Aq, z, p, beta, partials, s, status);
             using C = Bp30Cfg<N, float>;
             const int64_t blocks = (E + C::EPB - 1) / C::EPB;
             f16g30_fn<N, PCG>()<<<(unsigned)blocks, C::threads, C::smem, s>>>(E, G, ginv, lambda, q, Aq, z, p, beta,
@@ -83,7 +85,8 @@ struct F16Prepare30 {
 template <int N>
 struct F16Blocks30 {
     static cudaError_t run(int64_t E, int64_t *out) {
-        *out = (E + Bp30Cfg<N, float>::EPB - 1) / Bp30Cfg<N, float>::EPB;
+        *out = bp30_stream_default(N, true) ? bp30_stream_grid(N, E, true)
+                                            : (E + Bp30Cfg<N, float>::EPB - 1) / Bp30Cfg<N, float>::EPB;
         return cudaSuccess;
     }
 };
@@ -95,14 +98,15 @@ FEM_DEFINE_FOLD_UPLOAD(upload_fold_bp30_f16_tu)
 cudaError_t launch_bp30_f16g(const fem_basis *b, int64_t E, const __half *G, const double *ginv, double lambda,
                              const float *q, float *Aq, cudaStream_t s) {
     return dispatch_degree<F16Launch30<false>::L>(b->host.N, E, G, ginv, lambda, q, Aq, (const float *)nullptr,
-                                                  (float *)nullptr, (const double *)nullptr, (double *)nullptr, s);
+                                                  (float *)nullptr, (const double *)nullptr, (double *)nullptr, s,
+                                                  (double *)nullptr);
 }
 
 cudaError_t launch_bp30_pcg_f16g(const fem_basis *b, int64_t E, const __half *G, const double *ginv, double lambda,
                                  const float *z, float *p, const double *beta, float *Ap, double *partials,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, double *status) {
     return dispatch_degree<F16Launch30<true>::L>(b->host.N, E, G, ginv, lambda, (const float *)nullptr, Ap, z, p,
-                                                 beta, partials, s);
+                                                 beta, partials, s, status);
 }
 
 int64_t bp30_f16_blocks(int N, int64_t E) {

@@ -37,17 +37,6 @@ struct Bp35Cfg
                           sizeof(T) == 8 ? (N >= 8 ? 512 : 256) : (N == 10 ? 128 : 256))> {
 };
 
-// Hooks around the factor phase of bp35_core, for kernels that stage the
-// factors asynchronously: before() runs on every thread after the
-// derivative phase's barrier and returns whether the factors are there (the
-// same value on every thread; false ends the core at once), after() runs on
-// every thread once the factor phase's barrier has passed (the factors are
-// no longer read).  The default does nothing.
-struct NoFactorHooks {
-    __device__ __forceinline__ bool before() const { return true; }
-    __device__ __forceinline__ void after() const {}
-};
-
 // The operator on elements [e0, e0 + nel) (nel <= EPB) whose input field is
 // already in the first box of each element (boxes: EPB x 3 boxes, filled
 // before a barrier): derivatives, chain rule with the factors, transposes,

@@ -87,8 +87,22 @@ cudaError_t launch_bp30_point(const fem_basis *b, int64_t E, const double *G, do
 cudaError_t prepare_bp30_point(int N);  // and the BP3.5 point kernels
 cudaError_t launch_bp35_point(const fem_basis *b, int64_t E, const double *G, double lambda, const double *q,
                               double *Aq, cudaStream_t s);
+// FP32 BP3.0 TMA stream kernel (bp30_stream.cu): launch (cudaErrorInvalidValue
+// where an element does not fit in shared memory), whether it is the default
+// FP32 BP3.0 operator of the degree, its persistent grid (the PCG partials).
+cudaError_t launch_bp30_stream(int N, bool pcg, int64_t E, const float *G, double lambda, const float *q, float *Aq,
+                               const float *z, float *p, const double *beta, double *partials, cudaStream_t s,
+                               double *status);
+cudaError_t launch_bp30_stream_f16g(int N, bool pcg, int64_t E, const __half *G, const double *ginv, double lambda,
+                                    const float *q, float *Aq, const float *z, float *p, const double *beta,
+                                    double *partials, cudaStream_t s, double *status);
+bool bp30_stream_default(int N, bool f16 = false);
+int64_t bp30_stream_grid(int N, int64_t E, bool f16 = false);
+cudaError_t prepare_bp30_stream(int N, const double *fold_table);
+// which: 0 the default kernel for the degree, 1 the block kernel, 2 the TMA
+// stream kernel (cudaErrorInvalidValue where it does not fit)
 cudaError_t launch_bp30_f32(const fem_basis *b, int64_t E, const float *G, double lambda, const float *q,
-                            float *Aq, cudaStream_t s);
+                            float *Aq, cudaStream_t s, int which = 0);
 cudaError_t launch_bp30_pcg(const fem_basis *b, int64_t E, const double *G, double lambda, const double *z,
                             double *p, const double *beta, double *Ap, double *partials, cudaStream_t s);
 // half-precision factors (FEM_PCG_MIXED16): binary16 planes scaled by a
@@ -107,10 +121,11 @@ cudaError_t launch_bp30_f16g(const fem_basis *b, int64_t E, const __half *G, con
                              const float *q, float *Aq, cudaStream_t s);
 cudaError_t launch_bp30_pcg_f16g(const fem_basis *b, int64_t E, const __half *G, const double *ginv, double lambda,
                                  const float *z, float *p, const double *beta, float *Ap, double *partials,
-                                 cudaStream_t s);
+                                 cudaStream_t s, double *status);
 cudaError_t prepare_bp30_f16(int N, const double *fold_table);
 cudaError_t launch_bp30_pcg_f32(const fem_basis *b, int64_t E, const float *G, double lambda, const float *z,
-                                float *p, const double *beta, float *Ap, double *partials, cudaStream_t s);
+                                float *p, const double *beta, float *Ap, double *partials, cudaStream_t s,
+                                double *status);
 int64_t bp30_f16_blocks(int N, int64_t E);
 // tensor-core BP3.0 (FEM_PCG_MIXED_TC): FP32 data, f16 split contractions
 int64_t tc_table_words(int N);

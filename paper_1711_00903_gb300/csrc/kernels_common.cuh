@@ -194,6 +194,18 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return v;
 }
 
+// Hooks around the factor phase of the operator cores (bp35_core,
+// bp30_core), for kernels that stage the factors asynchronously: before()
+// runs on every thread after the barrier that precedes the factor phase and
+// returns whether the factors are there (the same value on every thread;
+// false ends the core at once), after() runs on every thread once the
+// factor phase's barrier has passed (the factors are no longer read).  The
+// default does nothing.
+struct NoFactorHooks {
+    __device__ __forceinline__ bool before() const { return true; }
+    __device__ __forceinline__ void after() const {}
+};
+
 // Dispatch of a functor templated on the degree N (1..15) at run time.
 template <template <int> class F, typename... Args>
 cudaError_t dispatch_degree(int N, Args &&...args) {

@@ -527,11 +527,12 @@ cudaError_t op_pcg(fem_pcg *s, const float *G, const float *z, float *p, float *
         return launch_bp30_pcg_tc(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, s->part, st);
     if (s->mode == FEM_PCG_MIXED16)
         return s->op == FEM_OP_BP30 ? launch_bp30_pcg_f16g(s->basis, s->E, s->G16, s->scal + S_GINV, s->lambda, z, p,
-                                                           s->scal + S_BETA, Ap, s->part, st)
+                                                           s->scal + S_BETA, Ap, s->part, st, s->scal + S_WAITFAIL)
                                     : launch_bp35_pcg_f16g(s->basis, s->E, s->G16, s->scal + S_GINV, s->lambda, z, p,
                                                            s->scal + S_BETA, Ap, s->part, st, s->scal + S_WAITFAIL);
     return s->op == FEM_OP_BP30
-               ? launch_bp30_pcg_f32(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, s->part, st)
+               ? launch_bp30_pcg_f32(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, s->part, st,
+                                     s->scal + S_WAITFAIL)
                : launch_bp35_pcg_f32(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, s->part, st,
                                      s->scal + S_WAITFAIL);
 }
