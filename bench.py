@@ -815,10 +815,11 @@ def run_sweep(fem, torch, device, verts, args, sm_mhz):
         row = {"N": N, "dofs": E * n ** 3}
         for name, kind in (("bp1", 1), ("bp35", 2), ("bp30", 3), ("bp1_bp30", 3), ("bp30_points", 3), ("bp35_points", 2),
                            ("bp35_f32", 2), ("bp30_f32", 3), ("bp35_f16", 2), ("bp30_f16", 3),
-                           ("bp30_f32_block", 3), ("bp30_f32_warp", 3), ("bp30_tc", 3)):
+                           ("bp30_f32_block", 3), ("bp30_f32_warp", 3), ("bp30_tc", 3), ("bp35_tc", 2)):
             f16 = name.endswith("_f16")
-            f32 = name.endswith("_f32") or f16 or name in ("bp30_f32_block", "bp30_f32_warp", "bp30_tc")
-            base = "bp30" if name in ("bp30_f32_block", "bp30_f32_warp", "bp30_tc") else (name[:-4] if f32 else name)
+            f32 = name.endswith("_f32") or f16 or name in ("bp30_f32_block", "bp30_f32_warp", "bp30_tc", "bp35_tc")
+            base = ("bp30" if name in ("bp30_f32_block", "bp30_f32_warp", "bp30_tc")
+                    else "bp35" if name == "bp35_tc" else (name[:-4] if f32 else name))
             ratio_base = "bp30" if base in ("bp30_points", "bp1_bp30") else ("bp35" if base == "bp35_points" else base)
             geo = torch.empty(fem.geo_shape(b, kind, E), dtype=torch.float64, device=device)
             fem.fem_mesh_geofacs(b, kind, verts, geo=geo, stream=stream)
@@ -836,6 +837,8 @@ def run_sweep(fem, torch, device, verts, args, sm_mhz):
                 o = torch.empty_like(qx)
                 if name == "bp30_tc":
                     fn = fem.fem_bp30_apply_tc
+                elif name == "bp35_tc":
+                    fn = fem.fem_bp35_apply_tc
                 elif name in ("bp30_f32_warp", "bp30_f32_block"):
                     lay = fem.FEM_LAYOUT_WARP if name == "bp30_f32_warp" else fem.FEM_LAYOUT_LINES
 
@@ -972,7 +975,7 @@ def run_pcg(fem, torch, device, verts_h, args):
     """Jacobi-PCG of the BP3.5 Helmholtz system (lambda = 1; the precision
     configuration) and of the BP3.0 one, with the manufactured right-hand
     side b = A u_I: all-FP64 against FP64 defect correction with FP32 inner
-    solves (FP32 factors; FP16 factors; for BP3.0 also the tensor-core
+    solves (FP32 factors; FP16 factors; the tensor-core
     contractions).  Each mode is solved to a tight residual (1e-13 for
     BP3.5, 5e-13 for BP3.0, whose FP64 residual stagnates near 2e-13), where
     every mode reaches the FP64 solution to 1e-10 and the distance to it is
@@ -992,7 +995,7 @@ def run_pcg(fem, torch, device, verts_h, args):
                      "mixed": "FP64 defect correction, FP32 inner PCG with FP32 factors",
                      "mixed16": "FP64 defect correction, FP32 inner PCG with binary16 factors (power-of-two "
                                 "scaled) widened to FP32 in the kernel",
-                     "mixed_tc": "FP64 defect correction, FP32 inner PCG whose BP3.0 matvec runs its "
+                     "mixed_tc": "FP64 defect correction, FP32 inner PCG whose matvec runs its 1D "
                                  "contractions on the tensor cores (split f16 mma.sync, FP32 accumulate)"}}
     wanted = args.pcg_modes.split(",")
     for opname, op, kind in (("bp35", fem.FEM_OP_BP35, fem.FEM_GEO_BP35), ("bp30", fem.FEM_OP_BP30, fem.FEM_GEO_BP30)):
@@ -1002,7 +1005,7 @@ def run_pcg(fem, torch, device, verts_h, args):
         modes = [(nm, md, it) for nm, md, it in (("fp64", fem.FEM_PCG_FP64, 0.0), ("mixed", fem.FEM_PCG_MIXED, 1e-3),
                                                  ("mixed16", fem.FEM_PCG_MIXED16, 1e-3),
                                                  ("mixed_tc", fem.FEM_PCG_MIXED_TC, 1e-3))
-                 if nm in wanted and not (nm == "mixed_tc" and op != fem.FEM_OP_BP30)]
+                 if nm in wanted]
         res = {}
         # the tight solve: 1e-13 for BP3.5; the FP64 BP3.0 residual stagnates
         # near 2e-13 on this mesh, so 5e-13 for BP3.0
@@ -1230,7 +1233,7 @@ def main(argv=None):
     ap.add_argument("--pcg-solves", type=int, default=3)
     ap.add_argument("--pcg-modes", default="fp64,mixed,mixed16,mixed_tc",
                     help="solver modes of the Helmholtz measurement (comma list of fp64, mixed, mixed16, "
-                         "mixed_tc; mixed_tc applies to BP3.0)")
+                         "mixed_tc)")
     ap.add_argument("--no-batch", action="store_true", help="skip the mixed-order batch measurement")
     ap.add_argument("--sections-out", default=None,
                     help="also write the side sections and the full headline to this JSON file")

@@ -272,6 +272,16 @@ int fem_bp30_apply_f32_layout(const fem_basis *b, int64_t E, const float *G, dou
 int fem_bp30_apply_tc(const fem_basis *b, int64_t E, const float *G, double lambda,
                       const float *q, float *Aq, void *stream);
 
+/* BP3.5 matvec (Algorithm 4) with its six 1D derivative contractions (D and
+ * D^T at the GLL nodes) on the tensor cores, by the same split-f16 scheme
+ * as fem_bp30_apply_tc; the chain rule with the factors and the lambda term
+ * in FP32.  The inner operator of FEM_PCG_MIXED_TC for BP3.5.  Layouts as
+ * fem_bp35_apply_f32 (G E*7*n^3 floats, q, Aq E*n^3 floats, 16-byte
+ * aligned, Aq != q); E <= 2^31 - 1.  Asynchronous on stream, allocates
+ * nothing.  Errors: FEM_EINVAL, FEM_ECUDA. */
+int fem_bp35_apply_tc(const fem_basis *b, int64_t E, const float *G, double lambda,
+                      const float *q, float *Aq, void *stream);
+
 /* BP1.0 and BP3.0 of one field in one pass (Algorithms 3 and 5): the
  * interpolation of q to the Gauss points is computed once for both, and
  * BP1.0's wJ is the seventh plane of G (the same w |J| at the same points,
@@ -290,7 +300,7 @@ int fem_bp1_bp30_apply(const fem_basis *b, int64_t E, const double *G, double la
 #define FEM_PREC_F16G 2 /* binary16 factors scaled by a power of two, FP32 vectors and
                          * arithmetic (fem_bp*_apply_f16g) */
 #define FEM_PREC_F16TC 3 /* FP32 factors and vectors, contractions on the tensor cores
-                          * (fem_bp30_apply_tc; BP3.0 only) */
+                          * (fem_bp35_apply_tc, fem_bp30_apply_tc) */
 
 /* BP3.5 and BP3.0 matvecs with the precision chosen at run time: each call
  * is the precision's own entry point above, with G, q and Aq of that
@@ -370,9 +380,9 @@ int fem_dot_noalloc(int64_t n, const double *x, const double *y, double *result,
  *                  FP32 in the kernel: half the factor bytes, same FP32
  *                  arithmetic.  The FP64 outer loop still reaches tol.
  *   FEM_PCG_MIXED_TC  as FEM_PCG_MIXED, with the inner matvec's
- *                  contractions on the tensor cores (fem_bp30_apply_tc:
- *                  split f16 operands, FP32 accumulation); FEM_OP_BP30 only
- *                  (FEM_EINVAL for BP3.5).
+ *                  contractions on the tensor cores (fem_bp35_apply_tc,
+ *                  fem_bp30_apply_tc: split f16 operands, FP32
+ *                  accumulation); E <= 2^31 - 1.
  * A solver context owns its device workspace (about 5 vectors in FP64
  * mode; 7 FP32 (MIXED16: FP16) factor planes and 6 FP32 + 1 FP64 vectors in
  * the mixed modes).
@@ -558,7 +568,7 @@ typedef struct {
     const double *rhs;   /* host, E*Np; read when the request is admitted           */
     double *x;           /* host output, E*Np; written when the request finishes    */
     double lambda;       /* >= 0                                                    */
-    int mode;            /* FEM_PCG_FP64, _MIXED, _MIXED16 or _MIXED_TC (BP3.0)     */
+    int mode;            /* FEM_PCG_FP64, _MIXED, _MIXED16 or _MIXED_TC             */
     double tol;          /* relative residual tolerance                             */
 } fem_serve_request;
 

@@ -22,7 +22,7 @@ __all__ = [
     "fem_bp35_apply", "fem_bp30_apply", "FEM_GEO_BP1", "FEM_GEO_BP35", "FEM_GEO_BP30",
     "geo_shape", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_wait_selftest", "fem_bp30_apply_layout", "fem_fma_probe",
     "FEM_LAYOUT_LINES", "FEM_LAYOUT_POINTS", "FEM_LAYOUT_WARP", "FEM_LAYOUT_STREAM", "fem_bp30_apply_f32_layout", "fem_bp35_apply_layout", "FEM_BATCH_POINTS30",
-    "FEM_BATCH_POINTS35", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_bp30_apply_tc", "FEM_PREC_F16TC", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot", "fem_dot_scratch_size", "Pcg",
+    "FEM_BATCH_POINTS35", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_bp30_apply_tc", "fem_bp35_apply_tc", "FEM_PREC_F16TC", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot", "fem_dot_scratch_size", "Pcg",
     "fem_bp35_apply_ex", "fem_bp30_apply_ex", "fem_bp1_bp30_apply", "FEM_PREC_F64", "FEM_PREC_F32", "FEM_PREC_F16G",
     "fem_pcg_create", "fem_pcg_solve", "fem_pcg_destroy", "FEM_ETIMEDOUT", "FEM_ECANCELED", "FEM_FAULT_WAIT_TIMEOUT", "FEM_EBREAKDOWN", "FEM_PCG_FP64", "FEM_PCG_MIXED", "FEM_PCG_MIXED16", "FEM_PCG_MIXED_TC", "fem_bp35_apply_f16g", "fem_bp30_apply_f16g",
     "Batch", "fem_batch_create", "FEM_OP_BP35", "FEM_OP_BP30", "Server",
@@ -123,6 +123,7 @@ def lib():
             L.fem_bp35_apply_f32.argtypes = [vp, i64, dp, dbl, dp, dp, vp]
             L.fem_bp30_apply_f32.argtypes = [vp, i64, dp, dbl, dp, dp, vp]
             L.fem_bp30_apply_tc.argtypes = [vp, i64, dp, dbl, dp, dp, vp]
+            L.fem_bp35_apply_tc.argtypes = [vp, i64, dp, dbl, dp, dp, vp]
             L.fem_bp30_apply_f32_layout.argtypes = [vp, i64, dp, dbl, dp, dp, i32, vp]
             L.fem_bp35_apply_layout.argtypes = [vp, i64, dp, dbl, dp, dp, i32, vp]
             L.fem_stream_sum.argtypes = [i32, i64, dp, dp, i32, vp]
@@ -183,7 +184,7 @@ def lib():
                       "fem_basis_degree", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_bp30_apply_layout", "fem_fma_probe",
                       "fem_bp35_apply_f16g", "fem_bp30_apply_f16g", "fem_bp35_apply_ex", "fem_bp30_apply_ex",
                       "fem_bp1_bp30_apply",
-                      "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_bp30_apply_tc", "fem_bp30_apply_f32_layout", "fem_bp35_apply_layout", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot",
+                      "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_bp30_apply_tc", "fem_bp35_apply_tc", "fem_bp30_apply_f32_layout", "fem_bp35_apply_layout", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot",
                       "fem_pcg_create", "fem_pcg_solve"):
                 getattr(L, f).restype = i32
             _lib = L
@@ -547,6 +548,21 @@ def fem_bp30_apply_f32_layout(b: Basis, G, lam: float, q, layout: int, out=None,
     _dev32(out, "out", E * b.n ** 3)
     _check(lib().fem_bp30_apply_f32_layout(b.handle, E, G.data_ptr(), float(lam), q.data_ptr(), out.data_ptr(),
                                            int(layout), _stream(stream, q.device)), "fem_bp30_apply_f32_layout")
+    return out
+
+
+def fem_bp35_apply_tc(b: Basis, G, lam: float, q, out=None, stream=None):
+    """BP3.5 matvec with the derivative contractions on the tensor cores
+    (FP32 factors and field, split f16 operands, FP32 accumulation)."""
+    import torch
+    E = q.shape[0]
+    _dev32(q, "q", E * b.n ** 3)
+    _dev32(G, "G", E * 7 * b.n ** 3)
+    if out is None:
+        out = torch.empty_like(q)
+    _dev32(out, "out", E * b.n ** 3)
+    _check(lib().fem_bp35_apply_tc(b.handle, E, G.data_ptr(), float(lam), q.data_ptr(), out.data_ptr(),
+                                   _stream(stream, q.device)), "fem_bp35_apply_tc")
     return out
 
 

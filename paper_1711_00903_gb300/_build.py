@@ -15,7 +15,7 @@ LIB = os.path.join(OUT, "libfem.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["abi.cu", "basis.cpp", "geofacs.cu", "bp1.cu", "bp35.cu", "bp30.cu", "pcg.cu", "noalloc.cu", "batch.cu", "serve.cu", "stream.cu", "bp30_point.cu",
-           "bp35_f16.cu", "bp30_f16.cu", "bp30_tc.cu", "tc_tables.cpp", "bp30_warp.cu", "bp30_stream.cu"]
+           "bp35_f16.cu", "bp30_f16.cu", "bp30_tc.cu", "tc_tables.cpp", "bp30_warp.cu", "bp30_stream.cu", "bp35_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I" + INCLUDE]

@@ -129,6 +129,7 @@ int fem_basis_setup(int N, fem_basis **out) {
     if (e == cudaSuccess) e = fem::prepare_bp35_f16(N, fem::fold_table());
     if (e == cudaSuccess) e = fem::prepare_bp30_f16(N, fem::fold_table());
     if (e == cudaSuccess) e = fem::prepare_bp30_tc(N);
+    if (e == cudaSuccess) e = fem::prepare_bp35_tc(N);
     if (e == cudaSuccess) e = fem::prepare_bp30_warp(N, fem::fold_table());
     if (e != cudaSuccess) {
         cudaFree(b->d_ops);
@@ -348,6 +349,16 @@ int fem_bp30_apply_f32_layout(const fem_basis *b, int64_t E, const float *G, dou
     return e == cudaSuccess ? FEM_OK : cuda_fail(e);
 }
 
+int fem_bp35_apply_tc(const fem_basis *b, int64_t E, const float *G, double lambda, const float *q, float *Aq,
+                      void *stream) {
+    if (!b || E < 0) return FEM_EINVAL;
+    if (E == 0) return FEM_OK;
+    if (!G || !q || !Aq || !aligned16(G) || !aligned16(q) || !aligned16(Aq)) return FEM_EINVAL;
+    if ((const void *)Aq == (const void *)q || E > (int64_t)0x7fffffff) return FEM_EINVAL;
+    cudaError_t e = fem::launch_bp35_tc(b, E, G, lambda, q, Aq, (cudaStream_t)stream);
+    return e == cudaSuccess ? FEM_OK : cuda_fail(e);
+}
+
 int fem_bp30_apply_tc(const fem_basis *b, int64_t E, const float *G, double lambda, const float *q, float *Aq,
                       void *stream) {
     if (!b || E < 0) return FEM_EINVAL;
@@ -386,6 +397,8 @@ int fem_bp35_apply_ex(const fem_basis *b, int64_t E, int prec, const void *G, co
             return fem_bp35_apply_f32(b, E, (const float *)G, lambda, (const float *)q, (float *)Aq, stream);
         case FEM_PREC_F16G:
             return fem_bp35_apply_f16g(b, E, G, ginv, lambda, (const float *)q, (float *)Aq, stream);
+        case FEM_PREC_F16TC:
+            return fem_bp35_apply_tc(b, E, (const float *)G, lambda, (const float *)q, (float *)Aq, stream);
         default:
             return FEM_EINVAL;
     }

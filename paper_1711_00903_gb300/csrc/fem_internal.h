@@ -135,7 +135,11 @@ cudaError_t launch_bp30_tc(const fem_basis *b, int64_t E, const float *G, double
                            cudaStream_t s);
 cudaError_t launch_bp30_pcg_tc(const fem_basis *b, int64_t E, const float *G, double lambda, const float *z,
                                float *p, const double *beta, float *Ap, double *partials, cudaStream_t s);
-int64_t bp30_tc_blocks(int64_t E);
+cudaError_t prepare_bp35_tc(int N);
+cudaError_t launch_bp35_tc(const fem_basis *b, int64_t E, const float *G, double lambda, const float *q, float *Aq,
+                           cudaStream_t s);
+cudaError_t launch_bp35_pcg_tc(const fem_basis *b, int64_t E, const float *G, double lambda, const float *z,
+                               float *p, const double *beta, float *Ap, double *partials, cudaStream_t s);
 // FP32 BP3.0 with one warp per element (bp30_warp.cu)
 cudaError_t prepare_bp30_warp(int N, const double *fold_table);
 cudaError_t launch_bp30_warp(const fem_basis *b, int64_t E, const float *G, double lambda, const float *q, float *Aq,

@@ -9,7 +9,7 @@
 //          loose tolerance by an FP32 PCG whose matvec reads FP32 geometric
 //          factors (FEM_PCG_MIXED), FP16 factors (FEM_PCG_MIXED16), or FP32
 //          factors with the contractions on the tensor cores
-//          (FEM_PCG_MIXED_TC, BP3.0).
+//          (FEM_PCG_MIXED_TC).
 //
 // Device-resident state: every scalar of the recurrence (rho, p.Ap, alpha,
 // beta, ||r||^2, convergence and breakdown flags, the iteration count) lives
@@ -512,7 +512,7 @@ cudaError_t op_apply64(fem_pcg *s, const double *x, double *out, cudaStream_t st
                                 : launch_bp35(s->basis, s->E, s->G, s->lambda, x, out, st);
 }
 int64_t op_blocks(const fem_pcg *s, bool f32) {
-    if (f32 && s->mode == FEM_PCG_MIXED_TC) return bp30_tc_blocks(s->E);
+    if (f32 && s->mode == FEM_PCG_MIXED_TC) return s->E;  // one block per element
     if (f32 && s->mode == FEM_PCG_MIXED16)
         return s->op == FEM_OP_BP30 ? bp30_f16_blocks(s->basis->host.N, s->E) : bp35_f16_blocks(s->basis->host.N, s->E);
     return s->op == FEM_OP_BP30 ? bp30_blocks(s->basis->host.N, s->E, f32) : bp35_blocks(s->basis->host.N, s->E, f32);
@@ -523,8 +523,10 @@ cudaError_t op_pcg(fem_pcg *s, const double *G, const double *z, double *p, doub
                : launch_bp35_pcg(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, s->part, st);
 }
 cudaError_t op_pcg(fem_pcg *s, const float *G, const float *z, float *p, float *Ap, cudaStream_t st) {
-    if (s->mode == FEM_PCG_MIXED_TC)  // BP3.0 only (checked at creation)
-        return launch_bp30_pcg_tc(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, s->part, st);
+    if (s->mode == FEM_PCG_MIXED_TC)
+        return s->op == FEM_OP_BP30
+                   ? launch_bp30_pcg_tc(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, s->part, st)
+                   : launch_bp35_pcg_tc(s->basis, s->E, G, s->lambda, z, p, s->scal + S_BETA, Ap, s->part, st);
     if (s->mode == FEM_PCG_MIXED16)
         return s->op == FEM_OP_BP30 ? launch_bp30_pcg_f16g(s->basis, s->E, s->G16, s->scal + S_GINV, s->lambda, z, p,
                                                            s->scal + S_BETA, Ap, s->part, st, s->scal + S_WAITFAIL)
@@ -1001,7 +1003,7 @@ int pcg_new(const fem_basis *b, int op, int64_t E, const double *G, double lambd
         (mode != FEM_PCG_FP64 && mode != FEM_PCG_MIXED && mode != FEM_PCG_MIXED16 && mode != FEM_PCG_MIXED_TC))
         return FEM_EINVAL;
     if (op != FEM_OP_BP35 && op != FEM_OP_BP30) return FEM_EINVAL;
-    if (mode == FEM_PCG_MIXED_TC && (op != FEM_OP_BP30 || E > (int64_t)0x7fffffff)) return FEM_EINVAL;
+    if (mode == FEM_PCG_MIXED_TC && E > (int64_t)0x7fffffff) return FEM_EINVAL;  // one block per element
     if (!(lambda >= 0.0)) return FEM_EINVAL;
     *out = nullptr;
     fem_pcg *s = new (std::nothrow) fem_pcg();

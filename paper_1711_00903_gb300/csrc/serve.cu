@@ -191,7 +191,7 @@ int fem_serve_submit(fem_server *s, const fem_serve_request *req, int64_t *id) {
     const fem_serve_request &q = *req;
     if ((q.op != FEM_OP_BP35 && q.op != FEM_OP_BP30) || q.N < 1 || q.N > FEM_MAX_N || q.E < 1) return FEM_EINVAL;
     if (!q.verts || !q.rhs || !q.x || (q.mode != FEM_PCG_FP64 && q.mode != FEM_PCG_MIXED && q.mode != FEM_PCG_MIXED16 &&
-                                     !(q.mode == FEM_PCG_MIXED_TC && q.op == FEM_OP_BP30)))
+                                     q.mode != FEM_PCG_MIXED_TC))
         return FEM_EINVAL;
     if (!(q.lambda >= 0.0) || !(q.tol > 0.0)) return FEM_EINVAL;
     Request R;

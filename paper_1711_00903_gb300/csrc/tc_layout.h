@@ -1,6 +1,6 @@
-// Operand layout of the tensor-core BP3.0 operator (bp30_tc.cu): the 1D
-// operators of Algorithm 5 as B fragments of mma.sync m16n8k16 (f16
-// operands, FP32 accumulate), and the position map of the split K axis.
+// Operand layout of the tensor-core operators (bp30_tc.cu, bp35_tc.cu): the
+// 1D operators of Algorithms 4 and 5 as B fragments of mma.sync m16n8k16
+// (f16 operands, FP32 accumulate), and the position map of the split K axis.
 //
 // Each contraction y[o] = sum_k Op[o][k] x[k] (k < Q, o < P) runs in one
 // pass over a K axis of 3Q positions that carries three products,
@@ -21,12 +21,15 @@
 
 namespace fem {
 
-enum { TC_I = 0, TC_DT = 1, TC_DTT = 2, TC_IT = 3, TC_OPS = 4 };
+// BP3.0: interpolation I (m x n), Gauss-point derivative Dt (m x m), its
+// transpose, projection I^T (n x m); BP3.5: GLL derivative D (n x n) and its
+// transpose.
+enum { TC_I = 0, TC_DT = 1, TC_DTT = 2, TC_IT = 3, TC_D = 4, TC_DTR = 5, TC_OPS = 6 };
 
 __host__ __device__ constexpr int tc_nt(int P) { return (P + 7) / 8; }         // 8-wide output tiles
 __host__ __device__ constexpr int tc_ks(int Q) { return (3 * Q + 15) / 16; }   // 16-wide K steps
-__host__ __device__ constexpr int tc_P(int N, int op) { return op == TC_IT ? N + 1 : N + 2; }
-__host__ __device__ constexpr int tc_Q(int N, int op) { return op == TC_I ? N + 1 : N + 2; }
+__host__ __device__ constexpr int tc_P(int N, int op) { return (op == TC_IT || op >= TC_D) ? N + 1 : N + 2; }
+__host__ __device__ constexpr int tc_Q(int N, int op) { return (op == TC_I || op >= TC_D) ? N + 1 : N + 2; }
 __host__ __device__ constexpr int tc_tiles(int N, int op) { return tc_nt(tc_P(N, op)) * tc_ks(tc_Q(N, op)); }
 // Offset of an operator's tiles in the degree's table (in tiles of 32 lanes x 2 words).
 __host__ __device__ constexpr int tc_offset(int N, int op) {
@@ -61,6 +64,16 @@ __host__ __device__ constexpr int tc_sj(int N) {
 }
 __host__ __device__ constexpr int tc_sk(int N) {
     constexpr int t[16] = {0, 9, 26, 37, 38, 76, 116, 92, 108, 140, 164, 180, 268, 300, 332, 340};
+    return t[N];
+}
+// The same for the n x n x n boxes of the BP3.5 operator (sj >= n,
+// sk >= sj n), counted over its own phases.
+__host__ __device__ constexpr int tc35_sj(int N) {
+    constexpr int t[16] = {0, 2, 3, 5, 6, 6, 7, 12, 9, 10, 11, 12, 13, 19, 23, 20};
+    return t[N];
+}
+__host__ __device__ constexpr int tc35_sk(int N) {
+    constexpr int t[16] = {0, 4, 9, 26, 37, 38, 52, 100, 92, 108, 140, 148, 180, 268, 348, 324};
     return t[N];
 }
 

@@ -46,7 +46,9 @@ double op_entry(const HostBasis &h, int op, int o, int k) {
         case TC_I: return h.I[o * h.n + k];    // interpolation (m x n)
         case TC_DT: return h.Dt[o * h.m + k];  // Gauss-point derivative (m x m)
         case TC_DTT: return h.Dt[k * h.m + o]; // its transpose
-        default: return h.I[k * h.n + o];      // projection I^T (n x m)
+        case TC_IT: return h.I[k * h.n + o];   // projection I^T (n x m)
+        case TC_D: return h.D[o * h.n + k];    // GLL derivative (n x n)
+        default: return h.D[k * h.n + o];      // its transpose
     }
 }
 

@@ -33,8 +33,9 @@ def _system(op, N, nx=2):
     return G, b
 
 
-@pytest.mark.parametrize("op,mode", [(2, 0), (2, 1), (2, 2), (3, 1), (3, 3)],
-                         ids=["bp35-fp64", "bp35-mixed", "bp35-mixed16", "bp30-mixed", "bp30-mixed_tc"])
+@pytest.mark.parametrize("op,mode", [(2, 0), (2, 1), (2, 2), (2, 3), (3, 1), (3, 3)],
+                         ids=["bp35-fp64", "bp35-mixed", "bp35-mixed16", "bp35-mixed_tc", "bp30-mixed",
+                              "bp30-mixed_tc"])
 def test_wait_failure_surfaces_as_etimedout(op, mode):
     """The injected report (the status word a stream kernel writes when its
     bounded wait gives up) ends the solve with FEM_ETIMEDOUT; the next solve

@@ -192,11 +192,8 @@ def test_apply_ex_selects_the_precision_entry_points(op, N):
     G16, ginv = _f16_factors(G)
     G16d, gi = torch.from_numpy(G16).to("cuda"), torch.tensor([ginv], dtype=torch.float64, device="cuda")
     assert torch.equal(ex(b, fem.FEM_PREC_F16G, G16d, 1.0, q32, ginv=gi), f16(b, G16d, gi, 1.0, q32))
-    if op == "bp30":
-        assert torch.equal(ex(b, fem.FEM_PREC_F16TC, G32, 1.0, q32), fem.fem_bp30_apply_tc(b, G32, 1.0, q32))
-    else:  # no tensor-core BP3.5 operator
-        with pytest.raises(fem.FemError):
-            ex(b, fem.FEM_PREC_F16TC, G32, 1.0, q32)
+    tc = fem.fem_bp30_apply_tc if op == "bp30" else fem.fem_bp35_apply_tc
+    assert torch.equal(ex(b, fem.FEM_PREC_F16TC, G32, 1.0, q32), tc(b, G32, 1.0, q32))
     with pytest.raises(ValueError):
         ex(b, 4, Gd, 1.0, qd)
     with pytest.raises(TypeError):
@@ -338,7 +335,7 @@ def test_full_size_tight_tolerance():
     x_ref = x64.clone()
     x, info, code = s64.solve(bd, tol=1e-16, maxit=3000, raise_on_error=False)
     assert code == fem.FEM_ENOCONV and bool(torch.isfinite(x).all()) and info["relres"] <= 1e-11
-    for mode in (fem.FEM_PCG_MIXED, fem.FEM_PCG_MIXED16):
+    for mode in (fem.FEM_PCG_MIXED, fem.FEM_PCG_MIXED16, fem.FEM_PCG_MIXED_TC):
         s = fem.fem_pcg_create(basis, G, 1.0, mode)
         x, info, code = s.solve(bd, tol=1e-13, inner_tol=1e-3)
         assert code == 0 and info["relres"] <= 1e-13
@@ -425,14 +422,20 @@ def test_solve_on_a_side_stream_replays_graphs_with_the_same_bits():
             assert i1["iters"] == j1["iters"] and i2["iters"] == j2["iters"]
 
 
-def test_mixed_tc_is_bp30_only():
+@pytest.mark.parametrize("N", [2, 4, 7])
+def test_bp35_mixed_tc_manufactured(N):
+    """BP3.5 defect correction with the tensor-core inner operator reaches
+    the manufactured solution and the oracle's solve, as the FP32 mode does."""
     fem = _fem()
-    N = 3
-    v = fem_synth.box_mesh(2)
-    G, _ = oracle.geofacs(N, oracle.KIND_BP35, v)
+    v, G, u, b = _manufactured(N, 3)
     basis = fem.fem_basis_setup(N)
-    with pytest.raises(fem.FemError):
-        fem.fem_pcg_create(basis, _dev(G), 1.0, fem.FEM_PCG_MIXED_TC, op=fem.FEM_OP_BP35)
+    s = fem.fem_pcg_create(basis, _dev(G), 1.0, fem.FEM_PCG_MIXED_TC)
+    x, info, code = s.solve(_dev(b), tol=1e-11)
+    x = x.cpu().numpy()
+    assert code == 0 and info["relres"] <= 1e-11
+    assert np.linalg.norm(x - u) / np.linalg.norm(u) <= 1e-7
+    xo, _, _ = oracle.pcg_bp35(N, G, 1.0, b, tol=1e-12)
+    assert np.linalg.norm(x - xo) / np.linalg.norm(xo) <= 1e-7
 
 
 def test_full_size_bp30_solves_all_modes():

@@ -1,7 +1,7 @@
-"""GPU parity of the tensor-core BP3.0 operator (fem_bp30_apply_tc: split f16
-mma.sync contractions with FP32 accumulation, FP32 factors and field)
-through the C ABI, against the FP64 oracle applied to the same FP32-rounded
-factors and field.
+"""GPU parity of the tensor-core BP3.0 and BP3.5 operators
+(fem_bp30_apply_tc, fem_bp35_apply_tc: split f16 mma.sync contractions with
+FP32 accumulation, FP32 factors and field) through the C ABI, against the
+FP64 oracle applied to the same FP32-rounded factors and field.
 
 Tolerance.  Each contraction carries x_hi Op_hi + x_lo Op_hi + x_hi Op_lo,
 which leaves about 3 * 2^-22 of the line's largest term per contraction,
@@ -129,4 +129,57 @@ def test_bp30_tc_full_size_sampled(bases):
     ref = oracle.bp30(N, g32[tp].cpu().numpy().astype(np.float64), 1.0, q32[tp].cpu().numpy().astype(np.float64))
     assert _rel(out[tp].cpu().numpy(), ref) <= _tol(N)
     f32 = fem.fem_bp30_apply_f32(b, g32, 1.0, q32)
+    assert ((out - f32).abs().max() / f32.abs().max()).item() <= 2 * _tol(N)
+
+
+def _case35(fem, b, N, E, seed=fem_synth.SEED_MESH):
+    import torch
+    v = fem_synth.box_mesh(4, 4, 4, jitter=0.1, seed=seed)[:E].copy()
+    g32 = fem.fem_mesh_geofacs(b, fem.FEM_GEO_BP35, torch.from_numpy(v).cuda()).float()
+    q32 = torch.from_numpy(fem_synth.field(fem_synth.SEED_Q, E, (N + 1) ** 3)).cuda().float()
+    return g32, q32
+
+
+@pytest.mark.parametrize("N", range(1, 16))
+@pytest.mark.parametrize("lam", [0.0, 1.0])
+def test_bp35_tc_parity(bases, N, lam):
+    """BP3.5 on the tensor cores, N = 1..15 on a ragged 37-element mesh,
+    against the oracle and the FP32 CUDA-core operator."""
+    import paper_1711_00903_gb300 as fem
+    b = bases[N]
+    g32, q32 = _case35(fem, b, N, 37)
+    got = fem.fem_bp35_apply_tc(b, g32, lam, q32).cpu().numpy()
+    ref = oracle.bp35(N, g32.cpu().numpy().astype(np.float64), lam, q32.cpu().numpy().astype(np.float64))
+    assert _rel(got, ref) <= _tol(N)
+    f32 = fem.fem_bp35_apply_f32(b, g32, lam, q32).cpu().numpy()
+    assert _rel(got, f32) <= 2 * _tol(N)
+
+
+@pytest.mark.parametrize("N", [2, 7, 13])
+def test_bp35_tc_power_of_two_scaling_is_exact(bases, N):
+    import paper_1711_00903_gb300 as fem
+    b = bases[N]
+    g32, q32 = _case35(fem, b, N, 20)
+    base = fem.fem_bp35_apply_tc(b, g32, 1.0, q32)
+    for k in (-100, -9, 30, 100):
+        assert bool((fem.fem_bp35_apply_tc(b, g32, 1.0, q32 * 2.0 ** k) == base * 2.0 ** k).all()), k
+
+
+def test_bp35_tc_full_size_sampled(bases):
+    """N = 7 on the 32^3 benchmark mesh, 48 sampled elements against the
+    oracle and every element against the FP32 operator."""
+    import torch
+    import paper_1711_00903_gb300 as fem
+    N, b = 7, bases[7]
+    v = fem_synth.box_mesh(32)
+    E = v.shape[0]
+    g32 = fem.fem_mesh_geofacs(b, fem.FEM_GEO_BP35, torch.from_numpy(v).cuda()).float()
+    q32 = torch.from_numpy(fem_synth.field(fem_synth.SEED_Q, E, (N + 1) ** 3)).cuda().float()
+    out = fem.fem_bp35_apply_tc(b, g32, 1.0, q32)
+    rng = np.random.default_rng(4)
+    pick = np.unique(np.concatenate([rng.choice(E, 46, replace=False), [0, E - 1]]))
+    tp = torch.from_numpy(pick).cuda()
+    ref = oracle.bp35(N, g32[tp].cpu().numpy().astype(np.float64), 1.0, q32[tp].cpu().numpy().astype(np.float64))
+    assert _rel(out[tp].cpu().numpy(), ref) <= _tol(N)
+    f32 = fem.fem_bp35_apply_f32(b, g32, 1.0, q32)
     assert ((out - f32).abs().max() / f32.abs().max()).item() <= 2 * _tol(N)
