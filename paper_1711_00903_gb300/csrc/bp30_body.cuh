@@ -10,6 +10,49 @@
 namespace fem {
 namespace {
 
+
+// Strides (sj, sk) of the four FP32 boxes n^3, m n^2, m^2 n, m^3 of degree
+// N (box b = 0..3), chosen by counting the shared-memory bank conflicts of
+// every access of bp30_core, in the stream launch (one element per group)
+// and the block launch (EPB elements per block), a conflicting store
+// weighted twice (as measured), among the strides whose box fits in the
+// m^3 box of the FP64 layout (shared memory per element unchanged).  On a
+// 32-bank memory no linear m^3 layout serves the r-, s- and t-direction
+// lines all without conflicts; the FP64 layout's odd row stride leaves
+// conflicts in the other boxes and, for even m, in the columns.
+__host__ __device__ constexpr int bp30f_stride(int N, int b, int which) {
+    constexpr short t[16][4][2] = {{{0, 0}, {0, 0}, {0, 0}, {0, 0}},
+                                   {{2, 16}, {3, 6}, {3, 9}, {3, 9}},
+                                   {{3, 9}, {4, 21}, {4, 20}, {4, 19}},
+                                   {{4, 16}, {5, 20}, {5, 25}, {5, 25}},
+                                   {{5, 25}, {9, 45}, {6, 38}, {6, 41}},
+                                   {{6, 36}, {7, 42}, {7, 52}, {7, 49}},
+                                   {{7, 49}, {9, 72}, {8, 72}, {9, 72}},
+                                   {{8, 65}, {9, 88}, {9, 85}, {9, 81}},
+                                   {{9, 81}, {13, 117}, {10, 106}, {10, 101}},
+                                   {{10, 100}, {11, 110}, {11, 121}, {11, 121}},
+                                   {{11, 121}, {13, 143}, {12, 172}, {12, 145}},
+                                   {{12, 145}, {14, 173}, {13, 173}, {13, 169}},
+                                   {{13, 169}, {15, 206}, {14, 206}, {14, 199}},
+                                   {{14, 196}, {15, 210}, {15, 239}, {15, 225}},
+                                   {{15, 225}, {17, 255}, {16, 272}, {17, 272}},
+                                   {{17, 272}, {18, 305}, {17, 305}, {17, 289}}};
+    return t[N][b][which];
+}
+
+template <int N, typename T, int b, int q1, int q2, int q3>
+struct Bp30Box {
+    using type = Box<q1, q2, q3>;
+};
+template <int N, int b, int q1, int q2, int q3>
+struct Bp30Box<N, float, b, q1, q2, q3> {
+    using type = StridedBox<q1, q2, q3, bp30f_stride(N, b, 0), bp30f_stride(N, b, 1)>;
+};
+
+constexpr int max4(int a, int b, int c, int d) {
+    return (a > b ? a : b) > (c > d ? c : d) ? (a > b ? a : b) : (c > d ? c : d);
+}
+
 // Layout of one block of EPB elements (three m^3 shared boxes each), data
 // type T (double for the paper's FP64 operator, float for the inner operator
 // of the mixed-precision solver).
@@ -17,11 +60,14 @@ template <int N, int EPB_, typename T = double, int BOXES = 3>
 struct Bp30Layout {
     static constexpr int n = N + 1, m = N + 2;
     static constexpr int NP = n * n * n, MP = m * m * m, mm = m * m;
-    using B0 = Box<n, n, n>;
-    using B1 = Box<m, n, n>;
-    using B2 = Box<m, m, n>;
-    using B3 = Box<m, m, m>;
-    static constexpr int S = B3::size;  // every buffer holds one m^3 box
+    using B0 = typename Bp30Box<N, T, 0, n, n, n>::type;
+    using B1 = typename Bp30Box<N, T, 1, m, n, n>::type;
+    using B2 = typename Bp30Box<N, T, 2, m, m, n>::type;
+    using B3 = typename Bp30Box<N, T, 3, m, m, m>::type;
+    // every buffer holds any box; the FP64 m^3 box size, so that elements
+    // sit as far apart as the strides above were chosen for
+    static constexpr int S = Box<m, m, m>::size;
+    static_assert(max4(B0::size, B1::size, B2::size, B3::size) <= S, "an FP32 box outgrows the m^3 box");
     static constexpr int per = BOXES * S;
     static constexpr int EPB = EPB_;
     static constexpr int threads = ((mm * EPB + 31) / 32) * 32;  // the block needs at least this many

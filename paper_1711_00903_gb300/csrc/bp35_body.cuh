@@ -10,11 +10,42 @@
 namespace fem {
 namespace {
 
-// Layout of one block of EPB elements (three padded n^3 boxes each).
-template <typename T, int N, int EPB_>
+// The n^3 box of the FP32 stream kernels (TMA-staged, bp35_stream.cuh) of
+// degree N: at N = 7 and 15 the swizzled box (conflict-free in every
+// direction); at N = 1, 3, 5, 9, 11 and 13 strides chosen by counting the
+// bank conflicts of every access of bp35_core in the stream and block
+// launches (a conflicting store weighted twice, as measured), among boxes
+// no larger than the FP64 one; elsewhere the FP64 box, which no linear
+// layout beat.  The block kernels keep the FP64 box: the swizzle's per-line
+// address offsets cost registers, and there (at N = 13 and 15) they measured
+// slower, spilling at N = 15.
+template <int N, typename T>
+struct Bp35Box {
+    using type = Box<N + 1, N + 1, N + 1>;
+};
+template <int N>
+struct Bp35Box<N, float> {
+    static constexpr int n = N + 1;
+    static constexpr int sj = N == 1 ? 2 : N == 3 ? 4 : N == 5 ? 6 : N == 9 ? 10 : N == 11 ? 12 : N == 13 ? 14 : 0;
+    static constexpr int sk = N == 1 ? 5 : N == 3 ? 19 : N == 5 ? 41 : N == 9 ? 101 : N == 11 ? 145 : N == 13 ? 199 : 0;
+    using type = typename std::conditional<
+        (N == 7 || N == 15), SwizzledBox<n>,
+        typename std::conditional<(sj > 0), StridedBox<n, n, n, (sj > 0 ? sj : n), (sk > 0 ? sk : n * n)>,
+                                  Box<n, n, n>>::type>::type;
+};
+
+// Layout of one block of EPB elements (three padded n^3 boxes each);
+// TUNED: the stream kernels' box (Bp35Box), else the FP64 box.
+template <typename T, int N, int EPB_, bool TUNED = false>
 struct Bp35Layout {
     static constexpr int n = N + 1, nn = n * n, NP = n * n * n;
-    using B = Box<n, n, n>;
+    using BX = typename std::conditional<TUNED, typename Bp35Box<N, T>::type, Box<n, n, n>>::type;
+    static_assert(BX::size <= Box<n, n, n>::size, "an FP32 box outgrows the FP64 one");
+    // elements sit as far apart as with the FP64 box (the strides above
+    // were chosen for that spacing)
+    struct B : BX {
+        static constexpr int size = Box<n, n, n>::size;
+    };
     // FP32 is bound by HBM: at kernel start one thread asks the TMA engine
     // to prefetch the block's factor planes (one contiguous range) into L2,
     // so that the chain-rule phase finds them there.  FP64 is bound by FP64
@@ -45,10 +76,11 @@ struct Bp35Cfg
 // TG (T, or FP16 scaled by a power of two that gscale undoes on the output).
 // Returns the thread's share of q . Aq (PCG; 0 otherwise).  Ends without a
 // barrier.
-template <typename T, int N, int EPB_, bool PCG, bool G_SMEM, typename TG = T, typename H = NoFactorHooks>
+template <typename T, int N, int EPB_, bool PCG, bool G_SMEM, typename TG = T, typename H = NoFactorHooks,
+          bool TUNED = false>
 __device__ __forceinline__ T bp35_core(T *smem, int64_t e0, int nel, const TG *__restrict__ Gsrc, double lambda,
                                        T *__restrict__ Aq, T gscale = T(1), const H &hooks = H()) {
-    using C = Bp35Layout<T, N, EPB_>;
+    using C = Bp35Layout<T, N, EPB_, TUNED>;
     using B = typename C::B;
     constexpr int n = C::n, nn = C::nn, NP = C::NP;
     const int el = threadIdx.x / nn, r = threadIdx.x - el * nn;

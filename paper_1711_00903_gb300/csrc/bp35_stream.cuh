@@ -30,7 +30,7 @@ template <int N, bool PCG, typename TG = float>
 struct Bp35Stream {
     static constexpr int n = N + 1, nn = n * n, NP = n * n * n;
     static constexpr int EPS = (kStreamThreads35 / nn) > 1 ? kStreamThreads35 / nn : 1;  // elements per group
-    using L = Bp35Layout<float, N, EPS>;
+    using L = Bp35Layout<float, N, EPS, true>;
     static constexpr int threads = L::threads;
     static constexpr int gElem = 7 * NP * (int)sizeof(TG);      // factor bytes per element
     static constexpr int vElem = NP * 4;                        // field bytes per element
@@ -149,7 +149,8 @@ bp35_stream_kernel(int64_t E, const TG *__restrict__ G, double lambda, const flo
             boxes[el * 3 * B::size + B::at(s % n, (s / n) % n, s / nn)] = v;
         }
         __syncthreads();
-        dot += (double)bp35_core<float, N, EPS, PCG, true, TG>(boxes, e0, nel, sG, lambda, Aq, gscale);
+        dot += (double)bp35_core<float, N, EPS, PCG, true, TG, NoFactorHooks, true>(boxes, e0, nel, sG, lambda, Aq,
+                                                                                      gscale);
         __syncthreads();  // the stage and the boxes are free again
     }
     if (failed) {
@@ -236,7 +237,7 @@ cudaError_t prepare_stream35() {
 template <int N, bool PCG, typename TG = float>
 struct Bp35Stream1 {
     static constexpr int n = N + 1, nn = n * n, NP = n * n * n;
-    using L = Bp35Layout<float, N, 1>;
+    using L = Bp35Layout<float, N, 1, true>;
     static constexpr int threads = L::threads;
     static constexpr int gElem = 7 * NP * (int)sizeof(TG);
     static constexpr int vElem = NP * 4;
@@ -367,7 +368,8 @@ bp35_stream1_kernel(int64_t E, const TG *__restrict__ G, double lambda, const fl
                 if (next && threadIdx.x == 0) (*iss)(next_e);
             }
         } hooks{&bar[0], (unsigned)(it & 1), &failed, &pend_g, has_next, &issue_g, e + gridDim.x};
-        dot += (double)bp35_core<float, N, 1, PCG, true, TG, Hooks>(boxes, e, 1, sG, lambda, Aq, gscale, hooks);
+        dot += (double)bp35_core<float, N, 1, PCG, true, TG, Hooks, true>(boxes, e, 1, sG, lambda, Aq, gscale,
+                                                                           hooks);
         if (failed) break;
         __syncthreads();  // the boxes and the field stage are free again
     }

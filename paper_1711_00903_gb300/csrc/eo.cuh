@@ -17,7 +17,17 @@
 // The folded matrices of every degree live in one __constant__ table; each
 // kernel reads them at compile-time offsets, so every operator entry is a
 // uniform constant-bank operand of the FMA (no load instruction).
+//
+// FP32: the FP32 kernels are bound by instruction issue, not by the FMA
+// lanes, so their contractions pair the two sums of each output row,
+// (E_a, O_a) += (S[a][i], T[a][i]) * (e_i, o_i), in one packed two-lane FMA
+// (__ffma2_rn, sm_100 and later) whose 64-bit coefficient is again a
+// constant-bank operand: half the FMA instructions.  Each lane rounds like
+// fmaf and the summation order is unchanged, so the results are the bits
+// of the scalar form.
 #pragma once
+
+#include <type_traits>
 
 #include "fold_layout.h"
 #include "kernels_common.cuh"
@@ -30,20 +40,42 @@ namespace fem {
 // device code); every TU that uses them uploads the same contents at basis
 // setup.
 static __constant__ double c_fold[kFoldTotal];
-static __constant__ float c_fold32[kFoldTotal];
+static __constant__ float2 c_fold32p[kFoldPairTotal];
 
-template <typename T>
-__device__ __forceinline__ T fold_at(int i);
-template <>
-__device__ __forceinline__ double fold_at<double>(int i) { return c_fold[i]; }
-template <>
-__device__ __forceinline__ float fold_at<float>(int i) { return c_fold32[i]; }
+// FP32 form of eo_apply below (the pair table, OFF its folded offset).
+template <int P, int Q, int SIG, int OFF>
+__device__ __forceinline__ void eo_apply_f32(const float (&x)[Q], float (&y)[P]) {
+    constexpr int hp = P / 2, hq = Q / 2;
+    constexpr int oP = fold_pair_offset_of(OFF);
+    static_assert(oP >= 0, "no folded operator block starts at this offset");
+    constexpr int oC = oP + hp * hq, oR = oC + ((Q % 2) ? hp : 0);
+    float2 eo[hq > 0 ? hq : 1];
+#pragma unroll
+    for (int i = 0; i < hq; i++) eo[i] = make_float2(x[i] + x[Q - 1 - i], x[i] - x[Q - 1 - i]);
+#pragma unroll
+    for (int a = 0; a < hp; a++) {
+        float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int i = 0; i < hq; i++) acc = __ffma2_rn(c_fold32p[oP + a * hq + i], eo[i], acc);
+        float E = acc.x;
+        const float O = acc.y;
+        if (Q % 2) E = fmaf(c_fold32p[oC + a].x, x[hq], E);
+        y[a] = E + O;
+        y[P - 1 - a] = (SIG > 0) ? (E - O) : (O - E);
+    }
+    if (P % 2) {
+        float M = 0.0f;
+#pragma unroll
+        for (int i = 0; i < hq; i++) M = fmaf(c_fold32p[oR + i].x, (SIG > 0) ? eo[i].x : eo[i].y, M);
+        if ((Q % 2) && SIG > 0) M = fmaf(c_fold32p[oR + hq].x, x[hq], M);
+        y[hp] = M;
+    }
+}
 
 
-// y (P) = A x (Q) along one line, A folded at table offset OFF, parity SIG,
-// in the precision T of the data.
+// FP64 form of eo_apply below.
 template <int P, int Q, int SIG, int OFF, typename T>
-__device__ __forceinline__ void eo_apply(const T (&x)[Q], T (&y)[P]) {
+__device__ __forceinline__ void eo_apply_f64(const T (&x)[Q], T (&y)[P]) {
     constexpr int hp = P / 2, hq = Q / 2;
     constexpr int oS = OFF, oT = OFF + hp * hq, oC = OFF + 2 * hp * hq;
     constexpr int oR = oC + ((Q % 2) ? hp : 0);
@@ -58,20 +90,31 @@ __device__ __forceinline__ void eo_apply(const T (&x)[Q], T (&y)[P]) {
         T E = T(0), O = T(0);
 #pragma unroll
         for (int i = 0; i < hq; i++) {
-            E = fmx(fold_at<T>(oS + a * hq + i), e[i], E);
-            O = fmx(fold_at<T>(oT + a * hq + i), o[i], O);
+            E = fmx(c_fold[oS + a * hq + i], e[i], E);
+            O = fmx(c_fold[oT + a * hq + i], o[i], O);
         }
-        if (Q % 2) E = fmx(fold_at<T>(oC + a), x[hq], E);
+        if (Q % 2) E = fmx(c_fold[oC + a], x[hq], E);
         y[a] = E + O;
         y[P - 1 - a] = (SIG > 0) ? (E - O) : (O - E);
     }
     if (P % 2) {
         T M = T(0);
 #pragma unroll
-        for (int i = 0; i < hq; i++) M = fmx(fold_at<T>(oR + i), (SIG > 0) ? e[i] : o[i], M);
-        if ((Q % 2) && SIG > 0) M = fmx(fold_at<T>(oR + hq), x[hq], M);
+        for (int i = 0; i < hq; i++) M = fmx(c_fold[oR + i], (SIG > 0) ? e[i] : o[i], M);
+        if ((Q % 2) && SIG > 0) M = fmx(c_fold[oR + hq], x[hq], M);
         y[hp] = M;
     }
+}
+
+// y (P) = A x (Q) along one line, A folded at table offset OFF, parity SIG,
+// in the precision T of the data.
+template <int P, int Q, int SIG, int OFF, typename T>
+__device__ __forceinline__ void eo_apply(const T (&x)[Q], T (&y)[P]) {
+    static_assert(std::is_same<T, float>::value || std::is_same<T, double>::value, "FP32 or FP64 lines");
+    if constexpr (std::is_same<T, float>::value)
+        eo_apply_f32<P, Q, SIG, OFF>(x, y);
+    else
+        eo_apply_f64<P, Q, SIG, OFF>(x, y);
 }
 
 // Padded element box q1 x q2 x q3 (i fastest); an odd row stride keeps the
@@ -84,6 +127,37 @@ struct Box {
     __device__ __forceinline__ static int at(int i, int j, int k) { return i + sj * j + sk * k; }
 };
 
+// Box with explicit strides (1, SJ, SK) (the FP32 operators choose theirs
+// against shared-memory bank conflicts).
+template <int q1, int q2, int q3, int SJ, int SK>
+struct StridedBox {
+    static_assert(SJ >= q1 && SK >= SJ * q2, "strides too small for the box");
+    static constexpr int sj = SJ, sk = SK;
+    static constexpr int size = pad2(SK * (q3 - 1) + SJ * (q2 - 1) + q1);
+    __device__ __forceinline__ static int at(int i, int j, int k) { return i + SJ * j + SK * k; }
+};
+
+// n^3 box (n = 8 or 16, a power of two dividing 32 with n >= 8) whose lines
+// along every direction are free of bank conflicts on 32 banks of 4 bytes
+// when the lanes of a warp take consecutive lines: rows of n words, planes
+// n^2 + n words apart, and the row's words permuted by
+//   (i, j, k) -> n^2 k + n k + n j + (i XOR g),  g = j / R + (n / R) (k mod R),
+// R = 32 / n the rows a warp covers.  A warp's lanes on lines along i
+// (fixed i, lanes over (j, k)) land in n-word groups indexed by j + k mod R
+// and, inside a group, at distinct i XOR g; along j (lanes over (i, k)) and
+// along k (lanes over (i, j)) the groups differ by k or j and i XOR g is a
+// permutation of i.  A linear layout cannot serve all three at n = 8 or 16.
+template <int n>
+struct SwizzledBox {
+    static_assert(n == 8 || n == 16, "swizzled boxes are for n = 8 and 16");
+    static constexpr int R = 32 / n;
+    static constexpr int sj = n, sk = n * n + n;
+    static constexpr int size = pad2(sk * (n - 1) + sj * (n - 1) + n);
+    __device__ __forceinline__ static int at(int i, int j, int k) {
+        return sk * k + sj * j + (i ^ (j / R + (n / R) * (k % R)));
+    }
+};
+
 // Runs f(el, r) for every task r < COUNT of every element el < EPB of the
 // block, densely over the block's threads (whole warps stay busy).
 template <int COUNT, int EPB, class F>
@@ -94,17 +168,25 @@ __device__ __forceinline__ void for_tasks(int nel, F &&f) {
     }
 }
 
-// Host: uploads the folded table (kFoldTotal doubles) to this TU's copies
-// (the FP32 copy rounded from it).
-#define FEM_DEFINE_FOLD_UPLOAD(NAME)                                                     \
-    cudaError_t NAME(const double *table) {                                              \
-        static float t32[kFoldTotal];                                                    \
-        for (int i = 0; i < kFoldTotal; i++) t32[i] = (float)table[i];                   \
-        cudaError_t e = cudaMemcpyToSymbol(c_fold, table, sizeof(double) * kFoldTotal, 0, \
-                                           cudaMemcpyHostToDevice);                      \
-        if (e != cudaSuccess) return e;                                                  \
-        return cudaMemcpyToSymbol(c_fold32, t32, sizeof(float) * kFoldTotal, 0,         \
-                                  cudaMemcpyHostToDevice);                               \
+// Host: uploads the folded table (kFoldTotal doubles) to this TU's copies:
+// the FP64 table as it is, the FP32 pair table rounded from it.
+#define FEM_DEFINE_FOLD_UPLOAD(NAME)                                                      \
+    cudaError_t NAME(const double *table) {                                               \
+        static float2 tp[kFoldPairTotal];                                                 \
+        for (int N = 1; N <= kMaxN; N++)                                                  \
+            for (int op = 0; op < kFoldCount; op++) {                                     \
+                const int P = fold_rows(op, N + 1, N + 2), Q = fold_cols(op, N + 1, N + 2);  \
+                const int hh = (P / 2) * (Q / 2), rest = fold_size(P, Q) - 2 * hh;        \
+                const double *f = table + fold_offset(N, op);                             \
+                float2 *o = tp + fold_pair_offset(N, op);                                 \
+                for (int k = 0; k < hh; k++) o[k] = make_float2((float)f[k], (float)f[hh + k]); \
+                for (int k = 0; k < rest; k++) o[hh + k] = make_float2((float)f[2 * hh + k], 0.0f); \
+            }                                                                             \
+        cudaError_t e = cudaMemcpyToSymbol(c_fold, table, sizeof(double) * kFoldTotal, 0,  \
+                                           cudaMemcpyHostToDevice);                       \
+        if (e != cudaSuccess) return e;                                                   \
+        return cudaMemcpyToSymbol(c_fold32p, tp, sizeof(float2) * kFoldPairTotal, 0,     \
+                                  cudaMemcpyHostToDevice);                                \
     }
 
 }  // namespace fem

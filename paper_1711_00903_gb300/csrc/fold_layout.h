@@ -37,6 +37,28 @@ __host__ __device__ constexpr int fold_offset(int N, int op) {
 }
 constexpr int kFoldTotal = fold_degree_offset(kMaxN + 1);
 
+// The same table in pairs for the FP32 kernels, whose contractions issue one
+// packed two-lane FMA per (S, T) entry: per operator, the hp x hq pairs
+// (S[a][i], T[a][i]), then every remaining folded entry (middle column,
+// middle row, centre) as (value, 0), in the order of the folded block.
+__host__ __device__ constexpr int fold_pair_size(int P, int Q) { return fold_size(P, Q) - (P / 2) * (Q / 2); }
+__host__ __device__ constexpr int fold_pair_offset(int N, int op) {
+    int s = 0;
+    for (int k = 1; k < N; k++)
+        for (int o = 0; o < kFoldCount; o++) s += fold_pair_size(fold_rows(o, k + 1, k + 2), fold_cols(o, k + 1, k + 2));
+    for (int o = 0; o < op; o++) s += fold_pair_size(fold_rows(o, N + 1, N + 2), fold_cols(o, N + 1, N + 2));
+    return s;
+}
+constexpr int kFoldPairTotal = fold_pair_offset(kMaxN + 1, 0);
+// Pair offset of the operator block that starts at folded offset off (-1 if
+// no block starts there).
+__host__ __device__ constexpr int fold_pair_offset_of(int off) {
+    for (int N = 1; N <= kMaxN; N++)
+        for (int op = 0; op < kFoldCount; op++)
+            if (fold_offset(N, op) == off) return fold_pair_offset(N, op);
+    return -1;
+}
+
 // Host: writes the folded form of A (P x Q row-major, parity sigma) to out
 // (fold_size(P, Q) doubles): S, T (P/2 x Q/2 each), the middle column
 // A[a][Q/2] (Q odd), the middle row A[P/2][i] (P odd), the centre entry.
