@@ -80,7 +80,7 @@ template <int N>
 struct Bp35F32Launch {
     static cudaError_t run(int64_t E, const float *G, double lambda, const float *q, float *Aq,
                            cudaStream_t s) {
-        if constexpr (bp35_streamed(N)) {
+        if constexpr (bp35_streamed<N, false, float>()) {
             return launch_stream35<N, false>(E, G, lambda, q, Aq, nullptr, nullptr, nullptr, nullptr, s);
         } else if constexpr (bp35_streamed1<N, false, float>()) {
             return launch_stream35_1<N, false>(E, G, lambda, q, Aq, nullptr, nullptr, nullptr, nullptr, s);
@@ -100,7 +100,7 @@ struct Bp35PcgLaunchT {
     struct L {
         static cudaError_t run(int64_t E, const T *G, double lambda, const T *z, T *p, const double *beta,
                                T *Ap, double *partials, cudaStream_t s, double *status) {
-            if constexpr (sizeof(T) == 4 && bp35_streamed(N)) {
+            if constexpr (sizeof(T) == 4 && bp35_streamed<N, true, float>()) {
                 return launch_stream35<N, true>(E, G, lambda, nullptr, Ap, z, p, beta, partials, s, nullptr,
                                                 status);
             } else if constexpr (sizeof(T) == 4 && bp35_streamed1<N, true, float>()) {
@@ -124,7 +124,7 @@ struct Bp35Blocks {
         using F = Bp35Cfg<float, N>;
         const int64_t a = (E + C::EPB - 1) / C::EPB;
         int64_t b = (E + F::EPB - 1) / F::EPB;
-        if constexpr (bp35_streamed(N)) {
+        if constexpr (bp35_streamed<N, true, float>()) {
             using S = Bp35Stream<N, true>;
             b = stream_grid35((E + S::EPS - 1) / S::EPS, S::blocks_per_sm);
         } else if constexpr (bp35_streamed1<N, true, float>()) {
@@ -145,14 +145,13 @@ struct Bp35Prepare {
     static cudaError_t run() {
         cudaError_t e = one<double, false>();
         if (e == cudaSuccess) e = one<double, true>();
-        if constexpr (bp35_streamed(N)) {
-            // all operands live in shared memory: ask for the largest carveout
+        if (e == cudaSuccess) e = one<float, false>();
+        if (e == cudaSuccess) e = one<float, true>();
+        // the stream kernels keep all operands in shared memory: they ask
+        // for the largest carveout
+        if constexpr (bp35_two_stage_fits(N))
             if (e == cudaSuccess) e = prepare_stream35<N, float>();
-        } else {
-            if (e == cudaSuccess) e = one<float, false>();
-            if (e == cudaSuccess) e = one<float, true>();
-            if (e == cudaSuccess) e = prepare_stream35_1<N, float>();
-        }
+        if (e == cudaSuccess) e = prepare_stream35_1<N, float>();
         return e;
     }
 };

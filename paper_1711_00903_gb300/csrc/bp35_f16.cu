@@ -58,7 +58,7 @@ struct F16Launch {
         static cudaError_t run(int64_t E, const __half *G, const double *ginv, double lambda, const float *q,
                                float *Aq, const float *z, float *p, const double *beta, double *partials,
                                cudaStream_t s, double *status) {
-            if constexpr (bp35_streamed(N)) {
+            if constexpr (bp35_streamed<N, PCG, __half>()) {
                 return launch_stream35<N, PCG, __half>(E, G, lambda, q, Aq, z, p, beta, partials, s, ginv, status);
             } else if constexpr (bp35_streamed1<N, PCG, __half>()) {
                 return launch_stream35_1<N, PCG, __half>(E, G, lambda, q, Aq, z, p, beta, partials, s, ginv,
@@ -77,7 +77,7 @@ struct F16Launch {
 template <int N>
 struct F16Blocks {
     static cudaError_t run(int64_t E, int64_t *out) {
-        if constexpr (bp35_streamed(N)) {
+        if constexpr (bp35_streamed<N, true, __half>()) {
             using S = Bp35Stream<N, true, __half>;
             *out = stream_grid35((E + S::EPS - 1) / S::EPS, S::blocks_per_sm);
         } else if constexpr (bp35_streamed1<N, true, __half>()) {
@@ -93,17 +93,15 @@ struct F16Blocks {
 template <int N>
 struct F16Prepare {
     static cudaError_t run() {
-        if constexpr (bp35_streamed(N)) {
-            return prepare_stream35<N, __half>();
-        } else {
-            cudaError_t e = cudaFuncSetAttribute(f16g_fn<N, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 Bp35Cfg<float, N>::smem);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute(f16g_fn<N, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Bp35Cfg<float, N>::smem);
-            if (e == cudaSuccess) e = prepare_stream35_1<N, __half>();
-            return e;
-        }
+        cudaError_t e = cudaFuncSetAttribute(f16g_fn<N, false>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             Bp35Cfg<float, N>::smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(f16g_fn<N, true>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     Bp35Cfg<float, N>::smem);
+        if constexpr (bp35_two_stage_fits(N))
+            if (e == cudaSuccess) e = prepare_stream35<N, __half>();
+        if (e == cudaSuccess) e = prepare_stream35_1<N, __half>();
+        return e;
     }
 };
 

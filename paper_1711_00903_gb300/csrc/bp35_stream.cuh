@@ -23,7 +23,7 @@ namespace {
 // multiples of 16 bytes; each range is then copied as its enclosing
 // 16-byte-aligned range (range_copy_plan) and read at its offset.  Up to
 // N = 9 (two stages must fit in shared memory).
-constexpr bool bp35_streamed(int N) { return N <= 9; }
+constexpr bool bp35_two_stage_fits(int N) { return N <= 9; }
 constexpr int kStreamThreads35 = 128;
 
 template <int N, bool PCG, typename TG = float>
@@ -250,20 +250,40 @@ struct Bp35Stream1 {
     static constexpr int smem = oBox + (L::smem > 256 ? L::smem : 256);
     static constexpr bool fits = smem <= 227 * 1024;
     static constexpr int per_sm_raw = (220 * 1024) / (smem + 1024);
-    static constexpr int blocks_per_sm = per_sm_raw > 8 ? 8 : (per_sm_raw < 1 ? 1 : per_sm_raw);
+    // up to 16 resident blocks: at middle degrees a block is small (one
+    // element, 64-100 threads), and more of them keep more copies in flight
+    static constexpr int blocks_per_sm = per_sm_raw > 16 ? 16 : (per_sm_raw < 1 ? 1 : per_sm_raw);
 };
 
-// The kernel choice above N = 9: the one-factor-stage stream kernel where
-// it fits in shared memory and measured faster than the block kernel on the
-// 32^3 mesh (GB300, fraction of the copy rate).  FP32 factors: 0.97, 0.78,
-// 0.97, 0.78 and 0.79 at N = 10, 11, 12, 14 and 15, against 0.57-0.70 for
-// the block kernel; at N = 13 one block per SM fits and it measured 0.62
-// against 0.65.  FP16 factors: 0.46-0.72 against 0.39-0.56 at N = 10-14,
-// 0.48 against 0.50 at N = 15.
+// The kernel form per degree and factor type, from the operator sweep on the
+// 32^3 mesh (GB300, fraction of the copy rate at the operator's bytes):
+//   - the one-factor-stage kernel from N = 6 where it fits and measured
+//     faster: FP32 factors 0.87-0.91 at N = 6-9 against 0.80-0.85 for the
+//     two-stage kernel, 0.78-0.97 at N = 10-12, 14, 15 against 0.57-0.70
+//     for the block kernel; FP16 factors at N = 6-8 (0.60-0.82 against
+//     0.56-0.73) and 10-14 (0.46-0.72 against 0.39-0.56);
+//   - the two-stage kernel up to N = 5 (at N = 3-5 the one-stage kernel
+//     measured 0.69-0.78 against 0.79-0.89), and with FP16 factors at N = 9;
+//   - the block kernel at N = 13 with FP32 factors (one one-stage block per
+//     SM fits; 0.62 against 0.65) and at N = 15 with FP16 factors (0.48
+//     against 0.50);
+//   - the PCG variants (p <- z + beta p fused in) keep the two-stage kernel
+//     up to N = 9, which stages the old p by TMA: the mixed solves at N = 7
+//     measured 207 us per inner iteration with it, 258 with the one-stage
+//     kernel reading p in its staging loop, and 211 with a TMA stage for p
+//     added to the one-stage kernel.
+template <int N, bool PCG, typename TG>
+constexpr bool bp35_one_stage_pick() {
+    if (PCG && bp35_two_stage_fits(N)) return false;
+    return sizeof(TG) == 4 ? (N >= 6 && N != 13) : ((N >= 6 && N <= 8) || (N >= 10 && N <= 14));
+}
+template <int N, bool PCG, typename TG>
+constexpr bool bp35_streamed() {
+    return bp35_two_stage_fits(N) && !bp35_one_stage_pick<N, PCG, TG>();
+}
 template <int N, bool PCG, typename TG>
 constexpr bool bp35_streamed1() {
-    constexpr bool faster = sizeof(TG) == 4 ? (N != 13) : (N != 15);
-    return !bp35_streamed(N) && faster && Bp35Stream1<N, PCG, TG>::fits;
+    return bp35_one_stage_pick<N, PCG, TG>() && Bp35Stream1<N, PCG, TG>::fits;
 }
 
 template <int N, bool PCG, typename TG>
