@@ -250,10 +250,11 @@ int fem_bp35_apply_f32(const fem_basis *b, int64_t E, const float *G, double lam
 
 int fem_wait_timeouts(unsigned long long *count, int reset) {
     if (!count) return FEM_EINVAL;
-    unsigned long long a = 0, b = 0;
+    unsigned long long a = 0, b = 0, c = 0;
     cudaError_t e = fem::wait_timeouts_bp35(&a, reset != 0);
     if (e == cudaSuccess) e = fem::wait_timeouts_bp35_f16(&b, reset != 0);
-    *count = a + b;
+    if (e == cudaSuccess) e = fem::wait_timeouts_bp30_stream(&c, reset != 0);
+    *count = a + b + c;
     return e == cudaSuccess ? FEM_OK : cuda_fail(e);
 }
 

@@ -60,6 +60,8 @@ FEM_DEFINE_FOLD_UPLOAD(upload_fold_bp30_stream_tu)
 
 }  // namespace
 
+FEM_DEFINE_WAIT_COUNTER(wait_timeouts_bp30_stream)
+
 cudaError_t launch_bp30_stream(int N, bool pcg, int64_t E, const float *G, double lambda, const float *q, float *Aq,
                                const float *z, float *p, const double *beta, double *partials, cudaStream_t s,
                                double *status) {
