@@ -184,6 +184,17 @@ int fem_wait_timeouts(unsigned long long *count, int reset);
  * Errors: FEM_EINVAL, FEM_ECUDA. */
 int fem_wait_selftest(unsigned long long *gave_up);
 
+/* Host-side check of the element boxes the operator kernels lay out in
+ * shared memory, for every degree: each point of each box (BP3.0's four
+ * boxes, BP3.5's n^3 box, in the FP64 and FP32 layouts) must map to a
+ * distinct word inside its share of the per-element buffer, and the
+ * swizzled FP32 BP3.5 boxes (N = 7 and 15) must serve the lines of every
+ * direction, taken by the 32 lanes of a warp, without a shared-memory bank
+ * conflict.  Writes the number of violations to *violations (0 when every
+ * layout holds).  Runs on the host only: no GPU needed.
+ * Errors: FEM_EINVAL (violations NULL). */
+int fem_layout_check(int64_t *violations);
+
 /* Roofline calibration stream with a chosen read:write ratio (Section 5
  * calibrates the bandwidth roofline by a copy; the operators read several
  * planes per plane written): dst[i] = sum over p = 0..planes-1, in that

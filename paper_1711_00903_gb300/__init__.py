@@ -20,7 +20,7 @@ __all__ = [
     "FemError", "lib", "Basis", "fem_version", "fem_basis_setup", "fem_basis_free",
     "fem_basis_tables", "fem_basis_host_tables", "fem_mesh_geofacs", "fem_bp1_apply",
     "fem_bp35_apply", "fem_bp30_apply", "FEM_GEO_BP1", "FEM_GEO_BP35", "FEM_GEO_BP30",
-    "geo_shape", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_wait_selftest", "fem_bp30_apply_layout", "fem_fma_probe",
+    "geo_shape", "fem_mesh_geofacs_set", "fem_wait_timeouts", "fem_wait_selftest", "fem_layout_check", "fem_bp30_apply_layout", "fem_fma_probe",
     "FEM_LAYOUT_LINES", "FEM_LAYOUT_POINTS", "FEM_LAYOUT_WARP", "FEM_LAYOUT_STREAM", "fem_bp30_apply_f32_layout", "fem_bp35_apply_layout", "FEM_BATCH_POINTS30",
     "FEM_BATCH_POINTS35", "fem_bp35_apply_f32", "fem_bp30_apply_f32", "fem_bp30_apply_tc", "fem_bp35_apply_tc", "FEM_PREC_F16TC", "fem_stream_sum", "fem_bp35_jacobi", "fem_bp30_jacobi", "fem_dot", "fem_dot_scratch_size", "Pcg",
     "fem_bp35_apply_ex", "fem_bp30_apply_ex", "fem_bp1_bp30_apply", "FEM_PREC_F64", "FEM_PREC_F32", "FEM_PREC_F16G",
@@ -131,6 +131,7 @@ def lib():
             L.fem_wait_timeouts.argtypes = [C.POINTER(C.c_ulonglong), i32]
             L.fem_fma_probe_threads.restype = i64
             L.fem_wait_selftest.argtypes = [C.POINTER(C.c_ulonglong)]
+            L.fem_layout_check.argtypes = [C.POINTER(C.c_int64)]
             L.fem_fma_probe.argtypes = [i64, dp, vp]
             L.fem_bp30_apply_layout.argtypes = [vp, i64, dp, dbl, dp, dp, i32, vp]
             L.fem_bp35_apply_f16g.argtypes = [vp, i64, dp, dp, dbl, dp, dp, vp]
@@ -485,6 +486,14 @@ def fem_wait_selftest():
     if code not in (FEM_OK, FEM_ETIMEDOUT):
         _check(code, "fem_wait_selftest")
     return int(c.value), code
+
+
+def fem_layout_check() -> int:
+    """Host-side check of the kernels' shared-memory element boxes; returns
+    the number of violations (0 when every layout holds)."""
+    v = C.c_int64(-1)
+    _check(lib().fem_layout_check(C.byref(v)), "fem_layout_check")
+    return int(v.value)
 
 
 def fem_fma_probe(iters: int, out=None, stream=None):

@@ -258,6 +258,12 @@ int fem_wait_timeouts(unsigned long long *count, int reset) {
     return e == cudaSuccess ? FEM_OK : cuda_fail(e);
 }
 
+int fem_layout_check(int64_t *violations) {
+    if (!violations) return FEM_EINVAL;
+    *violations = (int64_t)fem::layout_violations_bp30() + (int64_t)fem::layout_violations_bp35();
+    return FEM_OK;
+}
+
 int fem_wait_selftest(unsigned long long *gave_up) {
     if (!gave_up) return FEM_EINVAL;
     bool reported = false;

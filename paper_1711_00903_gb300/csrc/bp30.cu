@@ -221,4 +221,30 @@ cudaError_t prepare_bp30(int N, const double *fold_table) {
     return e;
 }
 
+namespace {
+// Layout check of degree N: the four FP32 boxes (the stream and block
+// kernels' layout) and the four FP64 boxes, each point of each box mapped
+// to a distinct word inside the per-element buffer.
+template <int N>
+int bp30_layout_violations_of() {
+    constexpr int n = N + 1, m = N + 2;
+    using F = Bp30Layout<N, 1, float>;
+    using D = Bp30Layout<N, 1, double>;
+    return box_layout_violations<typename F::B0, n, n, n>(F::S) +
+           box_layout_violations<typename F::B1, m, n, n>(F::S) +
+           box_layout_violations<typename F::B2, m, m, n>(F::S) +
+           box_layout_violations<typename F::B3, m, m, m>(F::S) +
+           box_layout_violations<typename D::B0, n, n, n>(D::S) +
+           box_layout_violations<typename D::B1, m, n, n>(D::S) +
+           box_layout_violations<typename D::B2, m, m, n>(D::S) +
+           box_layout_violations<typename D::B3, m, m, m>(D::S);
+}
+template <int... Ns>
+int bp30_layout_violations_all(std::integer_sequence<int, Ns...>) {
+    return (0 + ... + bp30_layout_violations_of<Ns + 1>());
+}
+}  // namespace
+
+int layout_violations_bp30() { return bp30_layout_violations_all(std::make_integer_sequence<int, kMaxN>{}); }
+
 }  // namespace fem

@@ -202,4 +202,27 @@ cudaError_t prepare_bp35(int N, const double *fold_table) {
     return dispatch_degree<Bp35Prepare>(N);
 }
 
+namespace {
+// Layout check of degree N: the n^3 box of the FP32 stream kernels and of
+// the FP64 and block kernels, each point mapped to a distinct word inside
+// the box's share of the per-element buffer; the swizzled boxes (N = 7,
+// 15) also serve every direction's warp line accesses without a bank
+// conflict.
+template <int N>
+int bp35_layout_violations_of() {
+    constexpr int n = N + 1;
+    using T = typename Bp35Layout<float, N, 1, true>::B;
+    using P = typename Bp35Layout<double, N, 1>::B;
+    int bad = box_layout_violations<T, n, n, n>(T::size) + box_layout_violations<P, n, n, n>(P::size);
+    if constexpr (N == 7 || N == 15) bad += box_line_conflicts<T, n>();
+    return bad;
+}
+template <int... Ns>
+int bp35_layout_violations_all(std::integer_sequence<int, Ns...>) {
+    return (0 + ... + bp35_layout_violations_of<Ns + 1>());
+}
+}  // namespace
+
+int layout_violations_bp35() { return bp35_layout_violations_all(std::make_integer_sequence<int, kMaxN>{}); }
+
 }  // namespace fem

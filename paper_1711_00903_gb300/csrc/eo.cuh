@@ -28,6 +28,8 @@
 #pragma once
 
 #include <type_traits>
+#include <utility>
+#include <vector>
 
 #include "fold_layout.h"
 #include "kernels_common.cuh"
@@ -124,7 +126,7 @@ struct Box {
     static constexpr int sj = (q1 % 2) ? q1 : q1 + 1;
     static constexpr int sk = sj * q2;
     static constexpr int size = pad2(sk * q3);
-    __device__ __forceinline__ static int at(int i, int j, int k) { return i + sj * j + sk * k; }
+    __host__ __device__ __forceinline__ static int at(int i, int j, int k) { return i + sj * j + sk * k; }
 };
 
 // Box with explicit strides (1, SJ, SK) (the FP32 operators choose theirs
@@ -134,7 +136,7 @@ struct StridedBox {
     static_assert(SJ >= q1 && SK >= SJ * q2, "strides too small for the box");
     static constexpr int sj = SJ, sk = SK;
     static constexpr int size = pad2(SK * (q3 - 1) + SJ * (q2 - 1) + q1);
-    __device__ __forceinline__ static int at(int i, int j, int k) { return i + SJ * j + SK * k; }
+    __host__ __device__ __forceinline__ static int at(int i, int j, int k) { return i + SJ * j + SK * k; }
 };
 
 // n^3 box (n = 8 or 16, a power of two dividing 32 with n >= 8) whose lines
@@ -153,10 +155,53 @@ struct SwizzledBox {
     static constexpr int R = 32 / n;
     static constexpr int sj = n, sk = n * n + n;
     static constexpr int size = pad2(sk * (n - 1) + sj * (n - 1) + n);
-    __device__ __forceinline__ static int at(int i, int j, int k) {
+    __host__ __device__ __forceinline__ static int at(int i, int j, int k) {
         return sk * k + sj * j + (i ^ (j / R + (n / R) * (k % R)));
     }
 };
+
+// Host checks of a box layout (the library's layout self-check): the
+// number of points (i, j, k) of the q1 x q2 x q3 box B that map outside
+// [0, size) or onto a word that another point maps to.
+template <class B, int q1, int q2, int q3>
+int box_layout_violations(int size) {
+    std::vector<unsigned char> seen((size_t)(size > 0 ? size : 0), 0);
+    int bad = 0;
+    for (int k = 0; k < q3; k++)
+        for (int j = 0; j < q2; j++)
+            for (int i = 0; i < q1; i++) {
+                const int a = B::at(i, j, k);
+                if (a < 0 || a >= size || seen[(size_t)a]++) bad++;
+            }
+    return bad;
+}
+
+// The bank conflicts (extra words served by one of 32 banks of 4 bytes) of
+// the lines of an n^3 box B along each direction, the lanes of a warp
+// taking 32 consecutive lines (line r at the other two indices (r mod n,
+// r / n)), summed over every position along the line.
+template <class B, int n>
+int box_line_conflicts() {
+    int extra = 0;
+    for (int dir = 0; dir < 3; dir++)
+        for (int l = 0; l < n; l++)
+            for (int w = 0; w * 32 < n * n; w++) {
+                int words[32][32];
+                int count[32] = {0};
+                for (int lane = 0; lane < 32 && w * 32 + lane < n * n; lane++) {
+                    const int r = w * 32 + lane, u = r % n, v = r / n;
+                    const int a = dir == 0 ? B::at(l, u, v) : dir == 1 ? B::at(u, l, v) : B::at(u, v, l);
+                    const int bank = a % 32;
+                    bool dup = false;
+                    for (int c = 0; c < count[bank]; c++) dup = dup || words[bank][c] == a;
+                    if (!dup) words[bank][count[bank]++] = a;
+                }
+                int most = 0;
+                for (int b = 0; b < 32; b++) most = count[b] > most ? count[b] : most;
+                extra += most > 1 ? most - 1 : 0;
+            }
+    return extra;
+}
 
 // Runs f(el, r) for every task r < COUNT of every element el < EPB of the
 // block, densely over the block's threads (whole warps stay busy).

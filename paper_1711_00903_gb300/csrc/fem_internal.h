@@ -150,6 +150,11 @@ int64_t bp30_blocks(int N, int64_t E, bool f32);
 
 // FP32 BP3.5 matvec (the inner operator of the mixed-precision solver).
 cudaError_t wait_timeouts_bp35(unsigned long long *count, bool reset);
+// Host checks of the element-box layouts in shared memory: the number of
+// violations (points mapped outside their buffer or onto another point's
+// word; bank conflicts of the swizzled boxes), 0 when the layouts hold.
+int layout_violations_bp30();
+int layout_violations_bp35();
 // The same count for the BP3.0 stream kernels (FP32 and FP16 factors).
 cudaError_t wait_timeouts_bp30_stream(unsigned long long *count, bool reset);
 cudaError_t launch_stream_sum(int planes, int64_t n, const void *src, void *dst, int word, cudaStream_t s);

@@ -32,6 +32,18 @@ def test_library_exports_symbol(name):
     assert hasattr(fem.lib(), name), name
 
 
+def test_shared_memory_box_layouts_hold():
+    """The element boxes the operator kernels lay out in shared memory
+    (FP64 and the FP32 layouts chosen against bank conflicts, every degree)
+    map each point to a distinct word inside its buffer, and the swizzled
+    FP32 BP3.5 boxes (N = 7, 15) serve the lines of every direction, taken
+    by the 32 lanes of a warp, without a bank conflict.  A host-side check
+    in the library: no GPU."""
+    assert fem.fem_layout_check() == 0
+    with pytest.raises(TypeError):
+        fem.fem_layout_check(1)
+
+
 def test_version_and_strerror():
     L = fem.lib()
     assert fem.fem_version() >= 10000
