@@ -133,7 +133,7 @@ struct Bp30LaunchT {
                                const double *beta, double *partials, cudaStream_t s, double *status = nullptr,
                                int which = 0) {
             if constexpr (sizeof(T) == 4) {
-                if (which == 2 || (which == 0 && bp30_stream_default(N)))
+                if (which == 2 || (which == 0 && bp30_stream_default(N, false, PCG)))
                     return launch_bp30_stream(N, PCG, E, G, lambda, q, Aq, z, p, beta, partials, s, status);
             }
             using C = Bp30Cfg<N, T>;
@@ -150,7 +150,7 @@ struct Bp30Blocks {
     static cudaError_t run(int64_t E, bool f32, int64_t *out) {
         const int epb = f32 ? Bp30Cfg<N, float>::EPB : Bp30Cfg<N, double>::EPB;
         *out = (E + epb - 1) / epb;
-        if (f32 && bp30_stream_default(N)) *out = bp30_stream_grid(N, E);
+        if (f32 && bp30_stream_default(N, false, true)) *out = bp30_stream_grid(N, E);
         return cudaSuccess;
     }
 };

@@ -59,7 +59,7 @@ struct F16Launch30 {
         static cudaError_t run(int64_t E, const __half *G, const double *ginv, double lambda, const float *q,
                                float *Aq, const float *z, float *p, const double *beta, double *partials,
                                cudaStream_t s, double *status) {
-            if (bp30_stream_default(N, true))
+            if (bp30_stream_default(N, true, PCG))
                 return launch_bp30_stream_f16g(N, PCG, E, G, ginv, lambda, q, Aq, z, p, beta, partials, s, status);
             using C = Bp30Cfg<N, float>;
             const int64_t blocks = (E + C::EPB - 1) / C::EPB;
@@ -85,7 +85,7 @@ struct F16Prepare30 {
 template <int N>
 struct F16Blocks30 {
     static cudaError_t run(int64_t E, int64_t *out) {
-        *out = bp30_stream_default(N, true) ? bp30_stream_grid(N, E, true)
+        *out = bp30_stream_default(N, true, true) ? bp30_stream_grid(N, E, true)
                                             : (E + Bp30Cfg<N, float>::EPB - 1) / Bp30Cfg<N, float>::EPB;
         return cudaSuccess;
     }

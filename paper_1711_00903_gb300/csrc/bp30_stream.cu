@@ -11,15 +11,18 @@ namespace {
 // block kernel).  FP32 factors: 0.63 / 0.57 at N = 3, 0.72 / 0.67 at 6,
 // 0.66 / 0.64 at 7, 0.38 / 0.37 at 14 and 0.39 / 0.35 at 15; at the other
 // degrees the block kernel was as fast or faster (0.62 / 0.34 at N = 1).
-// FP16 factors (GDOF/s): 92 / 85 at N = 7, 88 / 81 at 8, 95 / 81 at 9,
-// 87 / 74 at 10, 76 / 70 at 12, 75 / 68 at 13; ties or losses elsewhere
-// (50 / 64 at N = 4).
-template <int N, typename TG>
+// With the packed FMA and the searched box strides the plain operator
+// (not the PCG variant, which reads the old p in its staging loop) also
+// gains at N = 8, 10 and 11 (GDOF/s: 94 / 90, 77 / 76, 89 / 87; 59 / 87 at
+// N = 12 and 69 / 78 at 13 stay with the block kernel).  FP16 factors
+// (GDOF/s): 92 / 85 at N = 7, 88 / 81 at 8, 95 / 81 at 9, 87 / 74 at 10,
+// 76 / 70 at 12, 75 / 68 at 13; ties or losses elsewhere (50 / 64 at N = 4).
+template <int N, typename TG, bool PCG>
 constexpr bool stream30_default() {
     if constexpr (!Bp30Stream<N, true, TG>::fits) {
         return false;
     } else if constexpr (sizeof(TG) == 4) {
-        return N == 3 || N == 6 || N == 7 || N == 14 || N == 15;
+        return N == 3 || N == 6 || N == 7 || N == 14 || N == 15 || (!PCG && (N == 8 || N == 10 || N == 11));
     } else {
         return (N >= 7 && N <= 10) || N == 12 || N == 13;
     }
@@ -44,8 +47,8 @@ struct Stream30 {
     };
     template <int N>
     struct Info {
-        static cudaError_t run(int64_t E, int64_t *grid, bool *def) {
-            *def = stream30_default<N, TG>();
+        static cudaError_t run(int64_t E, bool pcg, int64_t *grid, bool *def) {
+            *def = pcg ? stream30_default<N, TG, true>() : stream30_default<N, TG, false>();
             *grid = stream_grid30(E, Bp30Stream<N, true, TG>::blocks_per_sm);
             return cudaSuccess;
         }
@@ -78,13 +81,13 @@ cudaError_t launch_bp30_stream_f16g(int N, bool pcg, int64_t E, const __half *G,
                                                      status);
 }
 
-bool bp30_stream_default(int N, bool f16) {
+bool bp30_stream_default(int N, bool f16, bool pcg) {
     int64_t g = 0;
     bool d = false;
     if (f16)
-        dispatch_degree<Stream30<__half>::Info>(N, (int64_t)1, &g, &d);
+        dispatch_degree<Stream30<__half>::Info>(N, (int64_t)1, pcg, &g, &d);
     else
-        dispatch_degree<Stream30<float>::Info>(N, (int64_t)1, &g, &d);
+        dispatch_degree<Stream30<float>::Info>(N, (int64_t)1, pcg, &g, &d);
     return d;
 }
 
@@ -92,9 +95,9 @@ int64_t bp30_stream_grid(int N, int64_t E, bool f16) {
     int64_t g = 0;
     bool d = false;
     if (f16)
-        dispatch_degree<Stream30<__half>::Info>(N, E, &g, &d);
+        dispatch_degree<Stream30<__half>::Info>(N, E, true, &g, &d);
     else
-        dispatch_degree<Stream30<float>::Info>(N, E, &g, &d);
+        dispatch_degree<Stream30<float>::Info>(N, E, true, &g, &d);
     return g;
 }
 

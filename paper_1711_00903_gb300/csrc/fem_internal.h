@@ -96,7 +96,7 @@ cudaError_t launch_bp30_stream(int N, bool pcg, int64_t E, const float *G, doubl
 cudaError_t launch_bp30_stream_f16g(int N, bool pcg, int64_t E, const __half *G, const double *ginv, double lambda,
                                     const float *q, float *Aq, const float *z, float *p, const double *beta,
                                     double *partials, cudaStream_t s, double *status);
-bool bp30_stream_default(int N, bool f16 = false);
+bool bp30_stream_default(int N, bool f16, bool pcg);  // pcg: the PCG variant's choice
 int64_t bp30_stream_grid(int N, int64_t E, bool f16 = false);
 cudaError_t prepare_bp30_stream(int N, const double *fold_table);
 // which: 0 the default kernel for the degree, 1 the block kernel, 2 the TMA
