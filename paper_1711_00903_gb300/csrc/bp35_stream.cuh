@@ -1,6 +1,8 @@
-// The persistent, double-buffered TMA stream form of the FP32 BP3.5 operator
-// (degree up to 9), shared by the FP32-factor kernels (bp35.cu) and the
-// FP16-factor kernels of the half-precision inner operator (bp35_f16.cu).
+// The persistent TMA stream forms of the FP32 BP3.5 operator (two stages up
+// to degree 9, one factor stage at any degree where it fits), shared by the
+// FP32-factor kernels (bp35.cu) and the FP16-factor kernels of the
+// half-precision inner operator (bp35_f16.cu); bp35_one_stage_pick chooses
+// per degree, factor type and variant.
 #pragma once
 
 #include <atomic>
@@ -14,7 +16,8 @@ namespace {
 // FP32 stream kernel.  In FP32 the operator is bound by HBM, and a kernel
 // that loads each element's factors with per-thread loads in the middle of
 // its phases leaves the memory system idle while its blocks compute.  Here a
-// fixed grid of persistent blocks (two per SM) walks groups of EPS elements;
+// fixed grid of persistent blocks (as many per SM as the shared memory
+// holds) walks groups of EPS elements;
 // for every group one thread issues TMA bulk copies of the group's factor
 // planes and input field(s) (contiguous ranges) into one of two shared
 // stages, completing on that stage's mbarrier, one group ahead of the
@@ -222,9 +225,11 @@ cudaError_t prepare_stream35() {
 }
 
 // ---------------------------------------------------------------------------
-// Single-factor-stage stream kernel, for the degrees above 9 where two
-// stages of an element's factors (37-115 KB in FP32) do not fit in shared
-// memory.  One element per group; the input field is double-buffered (TMA
+// Single-factor-stage stream kernel: above degree 9 two stages of an
+// element's factors (37-115 KB in FP32) do not fit in shared memory, and
+// at degrees 6-9 one element per block with one factor stage lets more
+// blocks share an SM than the two-stage kernel.  One element per group;
+// the input field is double-buffered (TMA
 // bulk copies, one group ahead) and the factors have one stage: the copy of
 // the next group's factors is issued as soon as this group's factor phase
 // has passed its barrier (bp35_core's hooks), so it lands while this group
